@@ -1,0 +1,14 @@
+"""Seeded synthetic inputs for the non-isothermal single-phase flow problem.
+
+This package only draws random fields and lays out wells and physical
+constants. It holds none of the discretisation, linear algebra or
+preconditioning arithmetic; both the CUDA path and the CPU oracle consume
+what it produces.
+"""
+from .fields import gaussian_random_field, iid_log_normal, channelised, layered
+from .configs import make_problem, CONFIG_SHAPES, default_fluid
+
+__all__ = [
+    "gaussian_random_field", "iid_log_normal", "channelised", "layered",
+    "make_problem", "CONFIG_SHAPES", "default_fluid",
+]

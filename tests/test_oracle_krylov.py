@@ -1,0 +1,119 @@
+"""Pins of the oracle's block preconditioner and FGMRES.
+
+With exact inner solves the five-step preconditioner of Sec. 3.2 is A^{-1}
+(Eq. Afact / Eq. Ainv), so preconditioned GMRES converges in one iteration;
+the block lower-triangular variant has a preconditioned operator with
+minimal polynomial of degree 2, so two iterations suffice. FGMRES is pinned
+to a least-squares minimisation over an explicit Krylov basis and to a
+dense direct solve."""
+import numpy as np
+import pytest
+
+from oracle import amg, krylov, physics
+from synthetic import make_problem
+from synthetic.configs import perturbed_state
+
+
+def small_system(shape=(5, 4, 3), seed=1):
+    prob = make_problem("tiny", shape=shape, seed=seed)
+    p, T = perturbed_state(prob, seed=seed + 10)
+    sys, bp, bT, S = krylov.assemble(prob, p, T)
+    return prob, sys, bp, bT, S
+
+
+def dense(A):
+    return amg.to_dense(A)
+
+
+def exact_parts(sys):
+    App, ApT, ATp, ATT = (dense(m) for m in (sys.App, sys.ApT, sys.ATp, sys.ATT))
+    Sx = ATT - ATp @ np.linalg.solve(App, ApT)
+    return App, Sx
+
+
+def run(sys, bp, bT, inv_pp, inv_S, variant, rtol=1e-12, maxit=20):
+    M = krylov.block_preconditioner(sys, inv_pp, inv_S, variant)
+    sm, se = sys.s_m, sys.s_e
+    mv = lambda xp, xT: tuple(s * y for s, y in zip((sm, se), sys.matvec(xp, xT)))
+    pc = lambda vp, vT: M(vp / sm, vT / se)
+    return krylov.fgmres(mv, pc, sm * bp, se * bT, rtol, maxit, 30)
+
+
+def test_exact_block_factorisation_converges_in_one_iteration():
+    prob, sys, bp, bT, S = small_system()
+    App, Sx = exact_parts(sys)
+    out = run(sys, bp, bT, lambda r: np.linalg.solve(App, r), lambda r: np.linalg.solve(Sx, r), "full")
+    assert out["iters"] == 1
+    assert out["rel_res"] < 1e-10
+
+
+def test_exact_lower_triangular_converges_in_two_iterations():
+    prob, sys, bp, bT, S = small_system((4, 4, 3), seed=2)
+    App, Sx = exact_parts(sys)
+    out = run(sys, bp, bT, lambda r: np.linalg.solve(App, r), lambda r: np.linalg.solve(Sx, r), "lower")
+    assert out["iters"] <= 2
+    assert out["rel_res"] < 1e-9
+
+
+def test_preconditioner_equals_inverse_with_exact_solves():
+    prob, sys, bp, bT, S = small_system((3, 3, 3), seed=3)
+    App, Sx = exact_parts(sys)
+    M = krylov.block_preconditioner(sys, lambda r: np.linalg.solve(App, r),
+                                    lambda r: np.linalg.solve(Sx, r), "full")
+    rng = np.random.default_rng(0)
+    vp, vT = rng.standard_normal(sys.N), rng.standard_normal(sys.N)
+    zp, zT = M(vp, vT)
+    yp, yT = sys.matvec(zp, zT)
+    assert np.max(np.abs(yp - vp)) <= 1e-6 * np.max(np.abs(vp))
+    assert np.max(np.abs(yT - vT)) <= 1e-6 * np.max(np.abs(vT))
+
+
+def test_fgmres_residuals_are_krylov_least_squares_minima():
+    """Without preconditioning, |g_{m}| after m steps equals
+    min_y ||b - A K_m y|| over the Krylov space K_m(A, b)."""
+    rng = np.random.default_rng(4)
+    n = 40
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.5
+    b = rng.standard_normal(n)
+    h = n // 2
+    mv = lambda xp, xT: ((A @ np.concatenate([xp, xT]))[:h], (A @ np.concatenate([xp, xT]))[h:])
+    pc = lambda vp, vT: (vp, vT)
+    out = krylov.fgmres(mv, pc, b[:h], b[h:], rtol=1e-14, maxit=12, restart=30)
+    K = np.zeros((n, 12))
+    v = b.copy()
+    for m in range(12):
+        K[:, m] = v / np.linalg.norm(v)
+        v = A @ K[:, m]
+    for m in range(1, 13):
+        Q, _ = np.linalg.qr(A @ K[:, :m])
+        r = b - Q @ (Q.T @ b)
+        assert abs(out["hist"][m - 1] - np.linalg.norm(r) / np.linalg.norm(b)) <= 1e-9
+
+
+def test_amg_preconditioned_solve_matches_direct_solve():
+    prob = make_problem(1)
+    out = krylov.solve(prob, rtol=1e-10)
+    assert out["status"] == "converged"
+    xp, xT = krylov.direct_solution(out["sys"], out["bp"], out["bT"])
+    N = out["sys"].N
+    x = out["x"]
+    assert np.linalg.norm(x[:N] - xp) <= 1e-7 * np.linalg.norm(xp)
+    assert np.linalg.norm(x[N:] - xT) <= 1e-6 * np.linalg.norm(xT)
+    assert out["iters"] < 40
+
+
+@pytest.mark.parametrize("variant", ["full", "lower"])
+def test_schur_approximation_beats_ATT_in_condition_number(variant):
+    """Trend of Table 4: on a heterogeneous grid with wells, S~_T^{-1} S is
+    better conditioned than A_TT^{-1} S (the paper's SPE10 numbers are not
+    reproduced, only the ordering)."""
+    prob = make_problem("tiny", shape=(6, 6, 2), seed=8, dt_days=100.0)
+    prob["wells"][0]["value"] = 1e-2
+    p, T = perturbed_state(prob, seed=3, dp=1e5, dT=20.0)
+    sys, bp, bT, S = krylov.assemble(prob, p, T)
+    App, Sx = exact_parts(sys)
+    St = dense(S)
+    ATT = dense(sys.ATT)
+    k_t = np.linalg.cond(np.linalg.solve(St, Sx))
+    k_a = np.linalg.cond(np.linalg.solve(ATT, Sx))
+    assert k_t < k_a
