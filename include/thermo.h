@@ -1,0 +1,206 @@
+/*
+ * thermo.h -- C-ABI of the GB300 solver for the linearised non-isothermal
+ * single-phase pressure/temperature system of Roy, Jonsthovel, Lemon and
+ * Wathen, "A block preconditioner for non-isothermal flow in porous media"
+ * (arXiv 1902.00095).
+ *
+ * The library assembles the TPFA Newton system (Sec. 2.2, Eq. Fm / Eq. Fe,
+ * Eq. AXR), builds the block factorisation preconditioner of Sec. 3.2 with
+ * the Schur approximation S~_T of Eq. Se, inverts A_pp and S~_T with one
+ * algebraic-multigrid V-cycle each, and solves with right-preconditioned
+ * flexible GMRES (Sec. 4 solver settings). All arithmetic runs in CUDA
+ * kernels on the device of the stream given to tp_create.
+ *
+ * Conventions for every call
+ *   - Return value: TP_OK (0), a negative error, or a positive warning.
+ *     No call aborts, throws across the ABI, or traps the GPU.
+ *   - Ownership: the caller owns every pointer it passes. Inputs are copied
+ *     (or read during the call); outputs are written into caller buffers.
+ *     The library owns all device memory it allocates and frees it in
+ *     tp_destroy / tp_amg_destroy.
+ *   - Pointers flagged by ptr_is_device = 1 are device pointers on the
+ *     context's device; with 0 they are host pointers (pageable or pinned).
+ *   - Streams: all work is enqueued on the context stream; calls return
+ *     after their results are ready (the stream is synchronised).
+ *   - Cell index i = x + nx*(y + ny*z), z up (layer 0 at the bottom).
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef THERMO_H
+#define THERMO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TP_OK              0
+#define TP_EINVAL         -1  /* bad argument (NULL, size, range)           */
+#define TP_ENOMEM         -2  /* device or host allocation failed           */
+#define TP_ECUDA          -3  /* a CUDA runtime call failed                 */
+#define TP_ENONFINITE     -4  /* NaN/Inf found in an input or a result      */
+#define TP_SETUP_FAILED   -5  /* AMG setup could not finish (round cap,     */
+                              /* coarsest level too large, zero pivot)      */
+#define TP_ESTATE         -6  /* call order violated (e.g. solve before     */
+                              /* assemble / build)                          */
+#define TP_NOT_CONVERGED   1  /* FGMRES reached maxit above rtol            */
+#define TP_BREAKDOWN       2  /* zero or non-finite Arnoldi norm            */
+
+typedef struct tp_ctx tp_ctx;
+typedef struct tp_amg tp_amg;
+
+/* Cartesian grid: nx*ny*nz cells of dx*dy*dz metres, gravity g (m/s^2). */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz, g;
+} tp_grid;
+
+/* Fluid and rock constants (SI). Density rho0 exp(c (p-p0)) exp(beta (T-T0))
+ * (Sec. 2.1.4); viscosity mu0 exp(-mu_coef (T - T_mu0)); c_v and rock
+ * rho_r, c_r of Eq. energy1; k_T = phi kTr + (1-phi) kTf as printed in
+ * Sec. 2.1.2 when kT_mix = 0, or (1-phi) kTr + phi kTf when kT_mix = 1. */
+typedef struct {
+  double rho0, c, beta, p0, T0;
+  double mu0, T_mu0, mu_coef;
+  double cv, rho_r, cr, kTf;
+  int kT_mix;
+} tp_fluid;
+
+/* A well or heater completed in cells (i, j, k0..k1) (Sec. 2.1.5).
+ * kind 0: rate injector, value = total volume rate (m^3/s) split equally
+ *         over the completed layers, injected at T_inj (Eq. f, Eq. fT);
+ * kind 1: producer at bottom-hole pressure value (Pa), Peaceman index per
+ *         completed cell with Dx = Dy = h = 5 m, r_w = 0.1 m, no cross-flow;
+ * kind 2: heater with coefficient U (W/K) per completed cell towards T_inj;
+ * kind 3: rate producer, value = total volume rate (m^3/s). */
+typedef struct {
+  int i, j, k0, k1, kind;
+  double value, T_inj, U;
+} tp_well;
+
+/* Preconditioner options (defaults from tp_default_opts). */
+typedef struct {
+  int schur;        /* 0: S~_T of Eq. Se; 2: S~_ATT = A_TT (Sec. 3.3)          */
+  int variant;      /* 0: full five-step apply (Sec. 3.2); 1: block lower     */
+                    /*    triangular (steps 1-3, delta_p = x_p)               */
+  int precision;    /* 0: FP64 hierarchy; 1: FP32 hierarchy values, smoothers */
+                    /*    and V-cycles inside FP64 FGMRES (coarsest LU FP64)  */
+  int interp;       /* 0: classical (Ruge-Stueben, modified); 1: extended+i   */
+  int smoother;     /* 0: l1-Jacobi; 1: Chebyshev on D^-1 A                   */
+  int nu_pre, nu_post, cheb_degree;
+  double theta;     /* strength threshold                                     */
+  int max_levels, coarse_size;
+  unsigned long long seed;  /* PMIS tie-break seed                            */
+  int use_graphs;   /* 1: replay each V-cycle / preconditioner as a CUDA graph */
+} tp_precond_opts;
+
+typedef struct {
+  int iters, restarts, status;
+  int levels_pp, levels_S;
+  double rel_res;           /* ||D (b - A x)|| / ||D b|| (stopping measure)  */
+  double rel_res_unscaled;  /* ||b - A x|| / ||b||                           */
+  double rel_res_p, rel_res_T; /* per-block unscaled relative residuals      */
+  double opc_pp, opc_S;     /* operator complexities                         */
+  double t_solve_ms;
+} tp_solve_info;
+
+void        tp_default_opts(tp_precond_opts* opts);
+const char* tp_status_string(int status);
+/* Message of the last failed call on this host thread ("" if none). */
+const char* tp_last_error(void);
+/* Number of CUDA kernels this library has launched in this process (a CUDA
+ * graph replay counts its kernel nodes). Host-side counter, no device work. */
+long long   tp_kernel_launches(void);
+
+/* --- context ------------------------------------------------------------
+ * tp_create: one context per grid. `cuda_stream` is a cudaStream_t (NULL =
+ * the legacy default stream). Fluid constants are copied. */
+int  tp_create(tp_ctx** ctx, const tp_grid* grid, const tp_fluid* fluid,
+               void* cuda_stream);
+void tp_destroy(tp_ctx* ctx);
+int  tp_get_sizes(const tp_ctx* ctx, int* N, int* nnzb);
+
+/* Cell fields, each [N] float64: permeabilities (m^2) along x, y, z,
+ * porosity, rock conductivity (W/m/K). Copied. Non-positive K or
+ * non-finite values give TP_EINVAL / TP_ENONFINITE. */
+int tp_set_fields(tp_ctx* ctx, const double* Kx, const double* Ky,
+                  const double* Kz, const double* phi, const double* kTr,
+                  int ptr_is_device);
+
+/* Wells (host array of n entries, copied). Cells outside the grid or an
+ * unknown kind give TP_EINVAL. */
+int tp_set_wells(tp_ctx* ctx, const tp_well* wells, int n);
+
+/* Newton linearisation at (p_k, T_k) with previous time level (p_n, T_n)
+ * and step dt (Sec. 3, Eq. AXR): writes the block-CSR Jacobian (pattern
+ * 7-point, columns ascending, 2x2 blocks [[dRm/dp, dRm/dT],[dRe/dp, dRe/dT]]),
+ * the residual G(x_k) and S~_T (Eq. Se) into the context; optionally copies
+ * the residual to R_m, R_e ([N] each, may be NULL). Inputs [N] each. */
+int tp_assemble(tp_ctx* ctx, const double* p_k, const double* T_k,
+                const double* p_n, const double* T_n, double dt,
+                double* R_m, double* R_e, int ptr_is_device);
+
+/* Split the Jacobian into A_pp, A_pT, A_Tp, A_TT (Eq. AXR), build one AMG
+ * hierarchy for A_pp and one for the Schur approximation chosen in opts.
+ * Requires a prior tp_assemble. */
+int tp_build_preconditioner(tp_ctx* ctx, const tp_precond_opts* opts);
+
+/* Solve A x = b with FGMRES(restart) preconditioned on the right by the
+ * block preconditioner. b = (b_p, b_T), x = (x_p, x_T), [N] each; if b_p
+ * and b_T are both NULL, b = -G(x_k) from the last tp_assemble. x starts at
+ * zero. Returns TP_OK, TP_NOT_CONVERGED or TP_BREAKDOWN (info filled in all
+ * three cases). */
+int tp_solve(tp_ctx* ctx, const double* b_p, const double* b_T,
+             double* x_p, double* x_T, double rtol, int maxit, int restart,
+             tp_solve_info* info, int ptr_is_device);
+
+/* y = A x with the assembled Jacobian (Eq. AXR), no scaling. [N] each. */
+int tp_spmv(tp_ctx* ctx, const double* x_p, const double* x_T,
+            double* y_p, double* y_T, int ptr_is_device);
+
+/* z = M^{-1} v: one application of the block preconditioner of Sec. 3.2
+ * (unscaled system). [N] each. Requires tp_build_preconditioner. */
+int tp_apply_preconditioner(tp_ctx* ctx, const double* v_p, const double* v_T,
+                            double* z_p, double* z_T, int ptr_is_device);
+
+/* Copies of the assembled operators to host buffers: the block matrix
+ * (rowptr [N+1], col [nnzb], val [4*nnzb] row-major blocks) and the Schur
+ * approximation values on the same pattern ([nnzb]). Any pointer may be
+ * NULL. Also the equation scales (s_m, s_e) used by tp_solve. */
+int tp_export_system(tp_ctx* ctx, int* rowptr, int* col, double* val,
+                     double* schur_val, double* scales);
+
+/* Hierarchy introspection: which = 0 (A_pp) or 1 (Schur). n/nnz receive
+ * up to max_levels entries. */
+int tp_hierarchy_info(tp_ctx* ctx, int which, int* nlevels, int* n, int* nnz,
+                      int max_levels);
+
+/* --- standalone AMG on a caller CSR matrix --------------------------------
+ * tp_amg_create builds the hierarchy of an n x n CSR matrix (rowptr [n+1],
+ * col [nnz] ascending per row with the diagonal present, val [nnz]); the
+ * pattern must be structurally symmetric. Inputs are copied. */
+int  tp_amg_create(tp_amg** amg, int n, int nnz, const int* rowptr,
+                   const int* col, const double* val,
+                   const tp_precond_opts* opts, void* cuda_stream,
+                   int ptr_is_device);
+void tp_amg_destroy(tp_amg* amg);
+/* One V-cycle from a zero initial guess: x = V(b), [n] each. */
+int  tp_amg_vcycle(tp_amg* amg, const double* b, double* x, int ptr_is_device);
+int  tp_amg_info(tp_amg* amg, int* nlevels, int* n, int* nnz, int max_levels);
+/* Host copies of level `level`: operator A_l (rowptr [n_l+1], col/val
+ * [nnz_l]), C/F split cf [n_l] (+1 C, -1 F; only for non-coarsest levels),
+ * strength mask [nnz_l] (1 strong), interpolation P_l (rowptr [n_l+1],
+ * col/val sized by P_nnz). Any pointer may be NULL. */
+int  tp_amg_export_level(tp_amg* amg, int level, int* rowptr, int* col,
+                         double* val, signed char* cf, signed char* strong,
+                         int* P_nnz, int* P_rowptr, int* P_col, double* P_val);
+/* Same introspection for a context hierarchy (which = 0 A_pp, 1 Schur). */
+int  tp_export_level(tp_ctx* ctx, int which, int level, int* rowptr, int* col,
+                     double* val, signed char* cf, signed char* strong,
+                     int* P_nnz, int* P_rowptr, int* P_col, double* P_val);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THERMO_H */

@@ -1,0 +1,78 @@
+// Algebraic multigrid hierarchy (internal header).
+//
+// Setup: strength of connection, PMIS C/F splitting with seeded tie-breaks,
+// classical or extended+i interpolation, R = P^T, Galerkin R (A P), l1-Jacobi
+// scaling, and an explicit inverse of the coarsest operator from LU with
+// partial pivoting. Everything that decides structure is evaluated in one
+// fixed order with correctly rounded IEEE multiply/add/divide (no FMA
+// contraction), so the hierarchy is reproducible bit for bit.
+//
+// Solve: one V-cycle from a zero guess, FP64 or FP32 values/vectors, replayable
+// as a CUDA graph.
+#pragma once
+#include "common.cuh"
+
+namespace tp {
+
+struct AmgOpts {
+  int interp = 1;        // 0 classical, 1 extended+i
+  int smoother = 0;      // 0 l1-Jacobi, 1 Chebyshev
+  int nu_pre = 2, nu_post = 2, cheb_degree = 2;
+  double theta = 0.25;
+  int max_levels = 25, coarse_size = 64, max_coarse_dense = 2048;
+  unsigned long long seed = 0;
+  int precision = 0;     // 0 FP64, 1 FP32 hierarchy
+  int max_pmis_rounds = 64;
+};
+
+struct Level {
+  DevCSR A;
+  int* dpos = nullptr;
+  int* tpos = nullptr;
+  unsigned char* strong = nullptr;
+  signed char* cf = nullptr;
+  int pmis_rounds = 0;
+  DevCSR P, R;       // P: n x nc, R: nc x n
+  double* dinv = nullptr;   // smoother scaling (l1 or plain diagonal), FP64
+  float* dinvf = nullptr;
+  double cheb_lo = 0.0, cheb_hi = 0.0;
+  // V-cycle work vectors, in the hierarchy precision (double* or float*)
+  void* b = nullptr;
+  void* x = nullptr;
+  void* t = nullptr;
+  void* r = nullptr;
+  int lanes_A = 1, lanes_R = 1, lanes_P = 1;
+};
+
+class Hierarchy {
+ public:
+  Hierarchy() = default;
+  Hierarchy(const Hierarchy&) = delete;
+  Hierarchy& operator=(const Hierarchy&) = delete;
+  ~Hierarchy();
+
+  // Build from a CSR matrix whose arrays stay owned by the caller and must
+  // outlive the hierarchy (level 0 borrows them).
+  void setup(const DevCSR& A0, const AmgOpts& opts, cudaStream_t s);
+  // One V-cycle: out = V(in). in/out are the hierarchy's own FP64 buffers.
+  void vcycle(cudaStream_t s);
+  double operator_complexity() const;
+
+  AmgOpts opts;
+  std::vector<Level> L;
+  int n0 = 0;
+  double* in = nullptr;    // [n0] FP64 right-hand side
+  double* out = nullptr;   // [n0] FP64 result
+  double* coarse_inv = nullptr;   // [nc*nc] row-major inverse of the coarsest A
+  int nc = 0;
+  Pool pool;
+
+ private:
+  void vcycle_fp64(cudaStream_t s);
+  void vcycle_fp32(cudaStream_t s);
+};
+
+// Standalone sparse helpers reused by the solver.
+void csr_transpose_positions(const DevCSR& A, int* tpos, int* err, cudaStream_t s);
+
+}  // namespace tp

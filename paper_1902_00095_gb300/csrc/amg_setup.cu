@@ -1,0 +1,806 @@
+// AMG setup kernels: strength, PMIS, interpolation, transpose, Galerkin
+// product, smoother scaling and the coarsest-level inverse.
+//
+// The paper inverts A_pp and S~_T approximately with an AMG V-cycle
+// (Sec. 3.2) built with classical Ruge-Stueben interpolation and Gaussian
+// elimination on the coarsest grid (Sec. 4 solver settings). Here the C/F
+// split is PMIS with seeded tie-breaks and the interpolation is classical or
+// its distance-two extended+i form; all structure-deciding arithmetic uses
+// __dmul_rn / __dadd_rn / __ddiv_rn in a fixed ascending-column order.
+#include "amg.cuh"
+#include <cmath>
+#include <algorithm>
+
+namespace tp {
+
+namespace {
+
+constexpr signed char kC = 1, kF = -1, kU = 0;
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  // splitmix64 output for state x (Steele, Lea, Flood 2014)
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned int pmis_hash(unsigned long long seed, int i) {
+  return (unsigned int)(splitmix64(seed ^ (unsigned long long)(long long)i) >> 32);
+}
+
+// index of key in a[lo, hi) (ascending), or -1
+__device__ __forceinline__ int find_in(const int* __restrict__ a, int lo, int hi, int key) {
+  int h = hi;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < h && a[lo] == key) ? lo : -1;
+}
+
+__device__ __forceinline__ bool opposite(double a, double d) {
+  return (d > 0.0 && a < 0.0) || (d < 0.0 && a > 0.0);
+}
+
+__global__ void k_diag_pos(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           int* __restrict__ dpos, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int p = find_in(col, rp[i], rp[i + 1], i);
+  dpos[i] = p;
+  if (p < 0) atomicOr(err, 1);
+}
+
+__global__ void k_transpose_pos(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                int* __restrict__ tpos, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int k = col[e];
+    int p = (k >= 0 && k < n) ? find_in(col, rp[k], rp[k + 1], i) : -1;
+    tpos[e] = p;
+    if (p < 0) atomicOr(err, 2);
+  }
+}
+
+// strong[e] = 1 iff col != i and -a_e >= theta * max_{k != i}(-a_ik) > 0
+__global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const double* __restrict__ val, double theta,
+                           unsigned char* __restrict__ strong) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double mx = -INFINITY;
+  for (int e = rp[i]; e < rp[i + 1]; ++e)
+    if (col[e] != i && -val[e] > mx) mx = -val[e];
+  if (!(mx > 0.0)) {
+    for (int e = rp[i]; e < rp[i + 1]; ++e) strong[e] = 0;
+    return;
+  }
+  const double thr = __dmul_rn(theta, mx);
+  for (int e = rp[i]; e < rp[i + 1]; ++e) strong[e] = (col[e] != i && -val[e] >= thr) ? 1 : 0;
+}
+
+__global__ void k_pmis_init(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                            const unsigned char* __restrict__ strong,
+                            const int* __restrict__ tpos, int* __restrict__ lam,
+                            signed char* __restrict__ state) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int l = 0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e)
+    if (col[e] != i && strong[tpos[e]]) ++l;
+  lam[i] = l;
+  state[i] = (l == 0) ? kF : kU;
+}
+
+__global__ void k_pmis_select(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                              const unsigned char* __restrict__ strong,
+                              const int* __restrict__ tpos, const int* __restrict__ lam,
+                              const signed char* __restrict__ state, unsigned long long seed,
+                              unsigned char* __restrict__ newc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] != kU) {
+    newc[i] = 0;
+    return;
+  }
+  const int li = lam[i];
+  const unsigned int hi = pmis_hash(seed, i);
+  unsigned char is_max = 1;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int k = col[e];
+    if (k == i || state[k] != kU) continue;
+    if (!(strong[e] || strong[tpos[e]])) continue;
+    int lk = lam[k];
+    unsigned int hk = pmis_hash(seed, k);
+    bool bigger = (lk > li) || (lk == li && (hk > hi || (hk == hi && k > i)));
+    if (bigger) {
+      is_max = 0;
+      break;
+    }
+  }
+  newc[i] = is_max;
+}
+
+__global__ void k_pmis_update(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                              const unsigned char* __restrict__ strong,
+                              signed char* __restrict__ state,
+                              const unsigned char* __restrict__ newc,
+                              int* __restrict__ undecided) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (newc[i]) {
+    state[i] = kC;
+    return;
+  }
+  if (state[i] != kU) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int k = col[e];
+    if (strong[e] && (newc[k] || state[k] == kC)) {
+      state[i] = kF;
+      return;
+    }
+  }
+  atomicAdd(undecided, 1);
+}
+
+__global__ void k_cflag(int n, const signed char* __restrict__ state, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = state[i] == kC ? 1 : 0;
+}
+
+// ---------------------------------------------------- classical interpolation
+__device__ __forceinline__ bool is_strong_c(const int* __restrict__ rp,
+                                            const int* __restrict__ col,
+                                            const unsigned char* __restrict__ strong,
+                                            const signed char* __restrict__ state, int i, int m) {
+  int p = find_in(col, rp[i], rp[i + 1], m);
+  return p >= 0 && strong[p] && state[m] == kC;
+}
+
+__global__ void k_classical_count(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                  const unsigned char* __restrict__ strong,
+                                  const signed char* __restrict__ state, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] == kC) {
+    cnt[i] = 1;
+    return;
+  }
+  int c = 0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e)
+    if (strong[e] && state[col[e]] == kC) ++c;
+  cnt[i] = c;
+}
+
+__global__ void k_classical_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const double* __restrict__ val, const int* __restrict__ dpos,
+                                 const unsigned char* __restrict__ strong,
+                                 const signed char* __restrict__ state,
+                                 const int* __restrict__ cidx, const int* __restrict__ Prp,
+                                 int* __restrict__ Pcol, double* __restrict__ Pval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p0 = Prp[i], p1 = Prp[i + 1];
+  if (state[i] == kC) {
+    Pcol[p0] = cidx[i];
+    Pval[p0] = 1.0;
+    return;
+  }
+  if (p0 == p1) return;
+  // columns (coarse numbering keeps the fine order) and numerator start a_ij
+  int q = p0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e)
+    if (strong[e] && state[col[e]] == kC) {
+      Pcol[q] = cidx[col[e]];
+      Pval[q] = val[e];
+      ++q;
+    }
+  double denom = val[dpos[i]];
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int k = col[e];
+    if (k == i) continue;
+    if (!strong[e]) {
+      denom = __dadd_rn(denom, val[e]);
+      continue;
+    }
+    if (state[k] == kC) continue;
+    const double akk = val[dpos[k]];
+    double s = 0.0;
+    for (int f = rp[k]; f < rp[k + 1]; ++f) {
+      const int m = col[f];
+      if (opposite(val[f], akk) && is_strong_c(rp, col, strong, state, i, m))
+        s = __dadd_rn(s, val[f]);
+    }
+    if (s == 0.0) {
+      denom = __dadd_rn(denom, val[e]);
+      continue;
+    }
+    const double t = __ddiv_rn(val[e], s);
+    for (int f = rp[k]; f < rp[k + 1]; ++f) {
+      const int m = col[f];
+      if (opposite(val[f], akk) && is_strong_c(rp, col, strong, state, i, m)) {
+        int slot = find_in(Pcol, p0, p1, cidx[m]);
+        Pval[slot] = __dadd_rn(Pval[slot], __dmul_rn(t, val[f]));
+      }
+    }
+  }
+  for (int s = p0; s < p1; ++s) Pval[s] = __ddiv_rn(-Pval[s], denom);
+}
+
+// ---------------------------------------------------- extended+i interpolation
+__global__ void k_extpi_ub(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const unsigned char* __restrict__ strong,
+                           const signed char* __restrict__ state, int* __restrict__ ub) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] == kC) {
+    ub[i] = 1;
+    return;
+  }
+  int u = rp[i + 1] - rp[i];
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int k = col[e];
+    if (k != i && strong[e] && state[k] != kC) u += rp[k + 1] - rp[k];
+  }
+  ub[i] = u;
+}
+
+__device__ __forceinline__ void insert_unique(int* __restrict__ buf, int& u, int key) {
+  int lo = 0, hi = u;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (buf[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < u && buf[lo] == key) return;
+  for (int q = u; q > lo; --q) buf[q] = buf[q - 1];
+  buf[lo] = key;
+  ++u;
+}
+
+// interpolatory set C^_i (sorted fine indices) of every F row
+__global__ void k_extpi_sets(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                             const unsigned char* __restrict__ strong,
+                             const signed char* __restrict__ state, const int* __restrict__ off,
+                             int* __restrict__ buf, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] == kC) {
+    cnt[i] = 1;
+    return;
+  }
+  int* b = buf + off[i];
+  int u = 0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int k = col[e];
+    if (k == i || !strong[e]) continue;
+    if (state[k] == kC) {
+      insert_unique(b, u, k);
+    } else {
+      for (int f = rp[k]; f < rp[k + 1]; ++f) {
+        const int m = col[f];
+        if (strong[f] && state[m] == kC && m != k) insert_unique(b, u, m);
+      }
+    }
+  }
+  cnt[i] = u;
+}
+
+__global__ void k_extpi_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                             const double* __restrict__ val, const int* __restrict__ dpos,
+                             const unsigned char* __restrict__ strong,
+                             const signed char* __restrict__ state, const int* __restrict__ cidx,
+                             const int* __restrict__ off, const int* __restrict__ buf,
+                             const int* __restrict__ Prp, int* __restrict__ Pcol,
+                             double* __restrict__ Pval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p0 = Prp[i], p1 = Prp[i + 1];
+  if (state[i] == kC) {
+    Pcol[p0] = cidx[i];
+    Pval[p0] = 1.0;
+    return;
+  }
+  if (p0 == p1) return;
+  const int* set = buf + off[i];
+  const int ns = p1 - p0;
+  for (int s = 0; s < ns; ++s) {
+    Pcol[p0 + s] = cidx[set[s]];
+    Pval[p0 + s] = 0.0;
+  }
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int s = find_in(set, 0, ns, col[e]);
+    if (s >= 0) Pval[p0 + s] = val[e];
+  }
+  double denom = val[dpos[i]];
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int k = col[e];
+    if (k == i) continue;
+    if (strong[e] && state[k] != kC) {
+      const double akk = val[dpos[k]];
+      double s = 0.0;
+      double aki = 0.0;
+      bool has_ki = false;
+      for (int f = rp[k]; f < rp[k + 1]; ++f) {
+        const int m = col[f];
+        if ((m == i || find_in(set, 0, ns, m) >= 0) && opposite(val[f], akk))
+          s = __dadd_rn(s, val[f]);
+        if (m == i) {
+          aki = val[f];
+          has_ki = true;
+        }
+      }
+      if (s == 0.0) {
+        denom = __dadd_rn(denom, val[e]);
+      } else {
+        const double t = __ddiv_rn(val[e], s);
+        if (has_ki && opposite(aki, akk)) denom = __dadd_rn(denom, __dmul_rn(t, aki));
+        for (int f = rp[k]; f < rp[k + 1]; ++f) {
+          const int m = col[f];
+          if (!opposite(val[f], akk)) continue;
+          int slot = find_in(set, 0, ns, m);
+          if (slot >= 0) Pval[p0 + slot] = __dadd_rn(Pval[p0 + slot], __dmul_rn(t, val[f]));
+        }
+      }
+    } else if (find_in(set, 0, ns, k) >= 0) {
+      // interpolated directly
+    } else {
+      denom = __dadd_rn(denom, val[e]);
+    }
+  }
+  for (int s = p0; s < p1; ++s) Pval[s] = __ddiv_rn(-Pval[s], denom);
+}
+
+// ------------------------------------------------------------- transpose
+__global__ void k_count_cols(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                             int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) atomicAdd(&cnt[col[e]], 1);
+}
+
+__global__ void k_fill_transpose(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const double* __restrict__ val, const int* __restrict__ Trp,
+                                 int* __restrict__ cursor, int* __restrict__ Tcol,
+                                 double* __restrict__ Tval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int c = col[e];
+    int q = Trp[c] + atomicAdd(&cursor[c], 1);
+    Tcol[q] = i;
+    Tval[q] = val[e];
+  }
+}
+
+// sort every row by column (insertion sort; rows are short)
+__global__ void k_sort_rows(int n, const int* __restrict__ rp, int* __restrict__ col,
+                            double* __restrict__ val) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = rp[i] + 1; e < rp[i + 1]; ++e) {
+    int c = col[e];
+    double v = val[e];
+    int q = e - 1;
+    while (q >= rp[i] && col[q] > c) {
+      col[q + 1] = col[q];
+      val[q + 1] = val[q];
+      --q;
+    }
+    col[q + 1] = c;
+    val[q + 1] = v;
+  }
+}
+
+// ------------------------------------------------------------- SpGEMM C = A B
+__global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
+                            const int* __restrict__ Brp, int* __restrict__ ub) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int u = 0;
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
+    int k = Acol[e];
+    u += Brp[k + 1] - Brp[k];
+  }
+  ub[i] = u;
+}
+
+// Row i of C: products a_ik * b_kj in ascending k (row i of A) then ascending
+// j (row k of B); each column's sum starts at 0.0 and adds them in that
+// order. Columns kept sorted by insertion.
+__global__ void k_spgemm_rows(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
+                              const double* __restrict__ Aval, const int* __restrict__ Brp,
+                              const int* __restrict__ Bcol, const double* __restrict__ Bval,
+                              const int* __restrict__ off, int* __restrict__ ccol,
+                              double* __restrict__ cval, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int* cc = ccol + off[i];
+  double* cv = cval + off[i];
+  int u = 0;
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
+    const int k = Acol[e];
+    const double a = Aval[e];
+    for (int f = Brp[k]; f < Brp[k + 1]; ++f) {
+      const int j = Bcol[f];
+      const double prod = __dmul_rn(a, Bval[f]);
+      int lo = 0, hi = u;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cc[mid] < j) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < u && cc[lo] == j) {
+        cv[lo] = __dadd_rn(cv[lo], prod);
+      } else {
+        for (int q = u; q > lo; --q) {
+          cc[q] = cc[q - 1];
+          cv[q] = cv[q - 1];
+        }
+        cc[lo] = j;
+        cv[lo] = __dadd_rn(0.0, prod);
+        ++u;
+      }
+    }
+  }
+  cnt[i] = u;
+}
+
+__global__ void k_spgemm_compact(int n, const int* __restrict__ off,
+                                 const int* __restrict__ ccol, const double* __restrict__ cval,
+                                 const int* __restrict__ Crp, int* __restrict__ Ccol,
+                                 double* __restrict__ Cval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = off[i];
+  for (int e = Crp[i]; e < Crp[i + 1]; ++e) {
+    Ccol[e] = ccol[o + (e - Crp[i])];
+    Cval[e] = cval[o + (e - Crp[i])];
+  }
+}
+
+// ------------------------------------------------------------ smoother scaling
+__global__ void k_l1_dinv(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                          const double* __restrict__ val, double* __restrict__ dinv,
+                          float* __restrict__ dinvf, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) s += (col[e] == i) ? val[e] : fabs(val[e]);
+  if (!(s > 0.0)) {
+    atomicOr(err, 4);
+    s = 1.0;
+  }
+  dinv[i] = 1.0 / s;
+  if (dinvf) dinvf[i] = (float)(1.0 / s);
+}
+
+__global__ void k_to_float(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------ coarsest level
+__global__ void k_to_dense(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const double* __restrict__ val, double* __restrict__ D) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = 0; j < n; ++j) D[(long long)i * n + j] = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) D[(long long)i * n + col[e]] += val[e];
+}
+
+// Gauss-Jordan elimination with partial pivoting on [A | I] (one block):
+// leaves A^{-1} in inv. Pivot: largest |a_ik| over rows >= k, lowest row on
+// ties. A zero pivot sets err.
+__global__ void k_gauss_jordan(int n, double* __restrict__ A, double* __restrict__ inv,
+                               int* __restrict__ err) {
+  __shared__ double s_val[1024];
+  __shared__ int s_idx[1024];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (long long q = tid; q < (long long)n * n; q += nt) inv[q] = ((q / n) == (q % n)) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += nt) {
+      double a = fabs(A[(long long)i * n + k]);
+      if (a > best || (a == best && i < bi)) {
+        best = a;
+        bi = i;
+      }
+    }
+    s_val[tid] = best;
+    s_idx[tid] = bi;
+    __syncthreads();
+    for (int o = nt / 2; o > 0; o >>= 1) {
+      if (tid < o) {
+        double a = s_val[tid + o];
+        int ai = s_idx[tid + o];
+        if (a > s_val[tid] || (a == s_val[tid] && ai < s_idx[tid])) {
+          s_val[tid] = a;
+          s_idx[tid] = ai;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      s_piv = s_idx[0];
+      if (!(s_val[0] > 0.0)) *err = 1;
+    }
+    __syncthreads();
+    if (*err) return;
+    const int p = s_piv;
+    if (p != k) {
+      for (int j = tid; j < n; j += nt) {
+        double t = A[(long long)k * n + j];
+        A[(long long)k * n + j] = A[(long long)p * n + j];
+        A[(long long)p * n + j] = t;
+        t = inv[(long long)k * n + j];
+        inv[(long long)k * n + j] = inv[(long long)p * n + j];
+        inv[(long long)p * n + j] = t;
+      }
+    }
+    __syncthreads();
+    const double piv = A[(long long)k * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      A[(long long)k * n + j] /= piv;
+      inv[(long long)k * n + j] /= piv;
+    }
+    __syncthreads();
+    for (long long q = tid; q < (long long)n * n; q += nt) {
+      int i = (int)(q / n), j = (int)(q % n);
+      if (i == k) continue;
+      double f = A[(long long)i * n + k];
+      if (j == k) continue;  // column k of A is cleared below
+      A[(long long)i * n + j] -= f * A[(long long)k * n + j];
+      inv[(long long)i * n + j] -= f * inv[(long long)k * n + j];
+    }
+    __syncthreads();
+    // inv column k and A column k for rows != k
+    for (int i = tid; i < n; i += nt) {
+      if (i == k) continue;
+      double f = A[(long long)i * n + k];
+      inv[(long long)i * n + k] -= f * inv[(long long)k * n + k];
+      A[(long long)i * n + k] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+int pick_lanes(const DevCSR& A) {
+  double avg = A.n > 0 ? (double)A.nnz / A.n : 1.0;
+  int l = 1;
+  while (l * 2 <= avg && l < 32) l *= 2;
+  return l;
+}
+
+int read_int(const int* d, cudaStream_t s) {
+  int h = 0;
+  TP_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return h;
+}
+
+// C = A B with the canonical summation order; C arrays allocated from `pool`.
+DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaStream_t s) {
+  const int n = A.n;
+  int* ub = scratch.alloc<int>(n + 1);
+  int* off = scratch.alloc<int>(n + 1);
+  k_spgemm_ub<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, B.rowptr, ub);
+  TP_LAUNCH_CHECK();
+  long long tot = scan_exclusive(ub, off, n, scratch, s);
+  int* ccol = scratch.alloc<int>(tot + 1);
+  double* cval = scratch.alloc<double>(tot + 1);
+  int* cnt = scratch.alloc<int>(n + 1);
+  k_spgemm_rows<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                 B.val, off, ccol, cval, cnt);
+  TP_LAUNCH_CHECK();
+  DevCSR C;
+  C.n = n;
+  C.m = B.m;
+  C.rowptr = pool.alloc<int>(n + 1);
+  long long nnz = scan_exclusive(cnt, C.rowptr, n, scratch, s);
+  C.nnz = (int)nnz;
+  C.col = pool.alloc<int>(nnz + 1);
+  C.val = pool.alloc<double>(nnz + 1);
+  k_spgemm_compact<<<grid_for(n), kBlock, 0, s>>>(n, off, ccol, cval, C.rowptr, C.col, C.val);
+  TP_LAUNCH_CHECK();
+  return C;
+}
+
+DevCSR transpose(const DevCSR& P, Pool& pool, Pool& scratch, cudaStream_t s) {
+  DevCSR R;
+  R.n = P.m;
+  R.m = P.n;
+  R.nnz = P.nnz;
+  int* cnt = scratch.alloc<int>(R.n + 1);
+  int* cursor = scratch.alloc<int>(R.n + 1);
+  TP_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * (R.n + 1), s));
+  TP_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * (R.n + 1), s));
+  k_count_cols<<<grid_for(P.n), kBlock, 0, s>>>(P.n, P.rowptr, P.col, cnt);
+  TP_LAUNCH_CHECK();
+  R.rowptr = pool.alloc<int>(R.n + 1);
+  scan_exclusive(cnt, R.rowptr, R.n, scratch, s);
+  R.col = pool.alloc<int>(R.nnz + 1);
+  R.val = pool.alloc<double>(R.nnz + 1);
+  k_fill_transpose<<<grid_for(P.n), kBlock, 0, s>>>(P.n, P.rowptr, P.col, P.val, R.rowptr,
+                                                    cursor, R.col, R.val);
+  TP_LAUNCH_CHECK();
+  k_sort_rows<<<grid_for(R.n), kBlock, 0, s>>>(R.n, R.rowptr, R.col, R.val);
+  TP_LAUNCH_CHECK();
+  return R;
+}
+
+}  // namespace
+
+void csr_transpose_positions(const DevCSR& A, int* tpos, int* err, cudaStream_t s) {
+  k_transpose_pos<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, tpos, err);
+  TP_LAUNCH_CHECK();
+}
+
+Hierarchy::~Hierarchy() = default;
+
+double Hierarchy::operator_complexity() const {
+  if (L.empty() || L[0].A.nnz == 0) return 0.0;
+  double s = 0.0;
+  for (const Level& l : L) s += l.A.nnz;
+  return s / L[0].A.nnz;
+}
+
+void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
+  opts = o;
+  pool.release();
+  L.clear();
+  coarse_inv = nullptr;
+  Pool scratch;
+  int* err = pool.alloc<int>(1);
+  TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  L.emplace_back();
+  L[0].A = A0;
+  n0 = A0.n;
+  while (true) {
+    Level& cur = L.back();
+    const DevCSR& A = cur.A;
+    const int n = A.n;
+    cur.dpos = pool.alloc<int>(n);
+    k_diag_pos<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.dpos, err);
+    TP_LAUNCH_CHECK();
+    if (read_int(err, s) != 0) fail(TP_EINVAL, "AMG: a row has no diagonal entry");
+    if (n <= opts.coarse_size || (int)L.size() >= opts.max_levels) break;
+    cur.tpos = pool.alloc<int>(A.nnz);
+    k_transpose_pos<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.tpos, err);
+    TP_LAUNCH_CHECK();
+    if (read_int(err, s) != 0) fail(TP_EINVAL, "AMG: pattern is not structurally symmetric");
+    cur.strong = pool.alloc<unsigned char>(A.nnz);
+    k_strength<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, A.val, opts.theta, cur.strong);
+    TP_LAUNCH_CHECK();
+    // PMIS
+    int* lam = scratch.alloc<int>(n);
+    unsigned char* newc = scratch.alloc<unsigned char>(n);
+    int* undecided = scratch.alloc<int>(1);
+    cur.cf = pool.alloc<signed char>(n);
+    k_pmis_init<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos, lam,
+                                               cur.cf);
+    TP_LAUNCH_CHECK();
+    int rounds = 0;
+    while (true) {
+      if (rounds >= opts.max_pmis_rounds) fail(TP_SETUP_FAILED, "PMIS round cap reached");
+      ++rounds;
+      k_pmis_select<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos,
+                                                   lam, cur.cf, opts.seed, newc);
+      TP_LAUNCH_CHECK();
+      TP_CUDA_TRY(cudaMemsetAsync(undecided, 0, sizeof(int), s));
+      k_pmis_update<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf, newc,
+                                                   undecided);
+      TP_LAUNCH_CHECK();
+      if (read_int(undecided, s) == 0) break;
+    }
+    cur.pmis_rounds = rounds;
+    int* flag = scratch.alloc<int>(n + 1);
+    int* cidx = scratch.alloc<int>(n + 1);
+    k_cflag<<<grid_for(n), kBlock, 0, s>>>(n, cur.cf, flag);
+    TP_LAUNCH_CHECK();
+    const int nc = (int)scan_exclusive(flag, cidx, n, scratch, s);
+    if (nc == 0 || (double)nc > 0.9 * (double)n) {
+      cur.cf = nullptr;  // this level becomes the coarsest
+      break;
+    }
+    // interpolation
+    DevCSR P;
+    P.n = n;
+    P.m = nc;
+    P.rowptr = pool.alloc<int>(n + 1);
+    int* cnt = scratch.alloc<int>(n + 1);
+    if (opts.interp == 0) {
+      k_classical_count<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf,
+                                                       cnt);
+      TP_LAUNCH_CHECK();
+      P.nnz = (int)scan_exclusive(cnt, P.rowptr, n, scratch, s);
+      P.col = pool.alloc<int>(P.nnz);
+      P.val = pool.alloc<double>(P.nnz);
+      k_classical_fill<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, cur.dpos,
+                                                        cur.strong, cur.cf, cidx, P.rowptr,
+                                                        P.col, P.val);
+      TP_LAUNCH_CHECK();
+    } else {
+      int* ub = scratch.alloc<int>(n + 1);
+      int* off = scratch.alloc<int>(n + 1);
+      k_extpi_ub<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf, ub);
+      TP_LAUNCH_CHECK();
+      long long tot = scan_exclusive(ub, off, n, scratch, s);
+      int* buf = scratch.alloc<int>(tot + 1);
+      k_extpi_sets<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf, off,
+                                                    buf, cnt);
+      TP_LAUNCH_CHECK();
+      P.nnz = (int)scan_exclusive(cnt, P.rowptr, n, scratch, s);
+      P.col = pool.alloc<int>(P.nnz);
+      P.val = pool.alloc<double>(P.nnz);
+      k_extpi_fill<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, cur.dpos,
+                                                    cur.strong, cur.cf, cidx, off, buf,
+                                                    P.rowptr, P.col, P.val);
+      TP_LAUNCH_CHECK();
+    }
+    cur.P = P;
+    cur.R = transpose(P, pool, scratch, s);
+    DevCSR AP = spgemm(A, P, scratch, scratch, s);
+    DevCSR Ac = spgemm(cur.R, AP, pool, scratch, s);
+    TP_CUDA_TRY(cudaStreamSynchronize(s));
+    scratch.release();
+    L.emplace_back();
+    L.back().A = Ac;
+  }
+  // smoother scaling, FP32 copies, work vectors
+  const bool f32 = opts.precision == 1;
+  for (size_t l = 0; l < L.size(); ++l) {
+    Level& v = L[l];
+    const int n = v.A.n;
+    v.dinv = pool.alloc<double>(n);
+    v.dinvf = f32 ? pool.alloc<float>(n) : nullptr;
+    k_l1_dinv<<<grid_for(n), kBlock, 0, s>>>(n, v.A.rowptr, v.A.col, v.A.val, v.dinv, v.dinvf,
+                                             err);
+    TP_LAUNCH_CHECK();
+    if (f32) {
+      v.A.valf = pool.alloc<float>(v.A.nnz);
+      k_to_float<<<grid_for(v.A.nnz), kBlock, 0, s>>>(v.A.nnz, v.A.val, v.A.valf);
+      TP_LAUNCH_CHECK();
+      if (v.P.nnz) {
+        v.P.valf = pool.alloc<float>(v.P.nnz);
+        k_to_float<<<grid_for(v.P.nnz), kBlock, 0, s>>>(v.P.nnz, v.P.val, v.P.valf);
+        v.R.valf = pool.alloc<float>(v.R.nnz);
+        k_to_float<<<grid_for(v.R.nnz), kBlock, 0, s>>>(v.R.nnz, v.R.val, v.R.valf);
+        TP_LAUNCH_CHECK();
+      }
+    }
+    const size_t es = f32 ? sizeof(float) : sizeof(double);
+    v.b = pool.alloc<char>(es * (n + 1));
+    v.x = pool.alloc<char>(es * (n + 1));
+    v.t = pool.alloc<char>(es * (n + 1));
+    v.r = pool.alloc<char>(es * (n + 1));
+    v.lanes_A = pick_lanes(v.A);
+    v.lanes_P = v.P.nnz ? pick_lanes(v.P) : 1;
+    v.lanes_R = v.R.nnz ? pick_lanes(v.R) : 1;
+  }
+  if (read_int(err, s) & 4) fail(TP_SETUP_FAILED, "AMG: non-positive l1 row norm");
+  // coarsest level: explicit inverse by Gauss-Jordan with partial pivoting
+  Level& cl = L.back();
+  nc = cl.A.n;
+  if (nc > opts.max_coarse_dense) fail(TP_SETUP_FAILED, "AMG: coarsest level too large");
+  double* D = scratch.alloc<double>((size_t)nc * nc);
+  coarse_inv = pool.alloc<double>((size_t)nc * nc);
+  k_to_dense<<<grid_for(nc), kBlock, 0, s>>>(nc, cl.A.rowptr, cl.A.col, cl.A.val, D);
+  TP_LAUNCH_CHECK();
+  TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  k_gauss_jordan<<<1, 1024, 0, s>>>(nc, D, coarse_inv, err);
+  TP_LAUNCH_CHECK();
+  if (read_int(err, s) != 0) fail(TP_SETUP_FAILED, "AMG: singular coarsest operator");
+  in = pool.alloc<double>(n0 + 1);
+  out = pool.alloc<double>(n0 + 1);
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+}  // namespace tp

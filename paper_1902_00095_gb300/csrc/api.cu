@@ -1,0 +1,691 @@
+// C-ABI entry points of the thermo library (declared in include/thermo.h).
+// Every entry point converts internal errors into status codes; nothing is
+// thrown across the ABI.
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include "solver.cuh"
+
+using tp::Error;
+using tp::fail;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+#define TP_API_BEGIN try {
+#define TP_API_END                                   \
+  }                                                  \
+  catch (const Error& e) {                           \
+    g_last_error = e.what;                           \
+    cudaGetLastError();                              \
+    return e.code;                          \
+  }                                                  \
+  catch (const std::bad_alloc&) {                    \
+    g_last_error = "host allocation failed";         \
+    return TP_ENOMEM;                                \
+  }                                                  \
+  catch (...) {                                      \
+    g_last_error = "unexpected exception";           \
+    return TP_ECUDA;                                 \
+  }
+
+void to_device(double* dst, const double* src, size_t n, int ptr_is_device, cudaStream_t s) {
+  TP_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                              ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+void from_device(double* dst, const double* src, size_t n, int ptr_is_device, cudaStream_t s) {
+  TP_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                              ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+__global__ void k_check_fields(int N, const double* Kx, const double* Ky, const double* Kz,
+                               const double* phi, const double* kTr, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double v[5] = {Kx[i], Ky[i], Kz[i], phi[i], kTr[i]};
+  for (int q = 0; q < 5; ++q)
+    if (!isfinite(v[q])) atomicOr(flags, 1);
+  if (!(Kx[i] > 0.0) || !(Ky[i] > 0.0) || !(Kz[i] > 0.0) || !(phi[i] > 0.0) || !(phi[i] < 1.0) ||
+      !(kTr[i] >= 0.0))
+    atomicOr(flags, 2);
+}
+
+__global__ void k_check_finite(long long n, const double* a, int* flags) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(a[i])) atomicOr(flags, 1);
+}
+
+__global__ void k_negate(double* a, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = -a[i];
+}
+
+void negate(double* a, long long n, cudaStream_t s) {
+  k_negate<<<tp::grid_for(n), tp::kBlock, 0, s>>>(a, n);
+  TP_LAUNCH_CHECK();
+}
+
+int read_flags(int* d, cudaStream_t s) {
+  int h = 0;
+  TP_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return h;
+}
+
+tp::AmgOpts amg_opts(const tp_precond_opts& o) {
+  tp::AmgOpts a;
+  a.interp = o.interp;
+  a.smoother = o.smoother;
+  a.nu_pre = o.nu_pre;
+  a.nu_post = o.nu_post;
+  a.cheb_degree = o.cheb_degree;
+  a.theta = o.theta;
+  a.max_levels = o.max_levels;
+  a.coarse_size = o.coarse_size;
+  a.seed = o.seed;
+  a.precision = o.precision;
+  return a;
+}
+
+void check_opts(const tp_precond_opts& o) {
+  if (o.schur != 0 && o.schur != 2) fail(TP_EINVAL, "schur must be 0 (S~_T) or 2 (A_TT)");
+  if (o.variant != 0 && o.variant != 1) fail(TP_EINVAL, "variant must be 0 or 1");
+  if (o.precision != 0 && o.precision != 1) fail(TP_EINVAL, "precision must be 0 or 1");
+  if (o.interp != 0 && o.interp != 1) fail(TP_EINVAL, "interp must be 0 or 1");
+  if (o.smoother != 0) fail(TP_EINVAL, "smoother must be 0 (l1-Jacobi)");
+  if (o.nu_pre < 1 || o.nu_post < 1 || o.nu_pre > 8 || o.nu_post > 8)
+    fail(TP_EINVAL, "nu_pre and nu_post must be in 1..8");
+  if (!(o.theta > 0.0 && o.theta < 1.0)) fail(TP_EINVAL, "theta must be in (0, 1)");
+  if (o.max_levels < 1 || o.coarse_size < 1) fail(TP_EINVAL, "max_levels, coarse_size >= 1");
+}
+
+}  // namespace
+
+tp_ctx::~tp_ctx() {
+  if (pc_graph) cudaGraphExecDestroy(pc_graph);
+  hpp.reset();
+  hS.reset();
+  if (host_est) cudaFreeHost(host_est);
+}
+
+struct tp_amg {
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  tp::Pool pool;
+  tp::DevCSR A;
+  std::unique_ptr<tp::Hierarchy> h;
+  ~tp_amg() {
+    h.reset();
+    pool.release();
+    if (own_stream && s) cudaStreamDestroy(s);
+  }
+};
+
+namespace {
+std::vector<std::pair<tp_ctx*, cudaStream_t>>& owned_streams() {
+  static std::vector<std::pair<tp_ctx*, cudaStream_t>> v;
+  return v;
+}
+}  // namespace
+
+extern "C" {
+
+void tp_default_opts(tp_precond_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->schur = 0;
+  o->variant = 0;
+  o->precision = 0;
+  o->interp = 1;
+  o->smoother = 0;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->cheb_degree = 2;
+  o->theta = 0.25;
+  o->max_levels = 25;
+  o->coarse_size = 64;
+  o->seed = 0;
+  o->use_graphs = 1;
+}
+
+const char* tp_status_string(int st) {
+  switch (st) {
+    case TP_OK: return "ok";
+    case TP_EINVAL: return "invalid argument";
+    case TP_ENOMEM: return "out of memory";
+    case TP_ECUDA: return "CUDA error";
+    case TP_ENONFINITE: return "non-finite value";
+    case TP_SETUP_FAILED: return "AMG setup failed";
+    case TP_ESTATE: return "call order violated";
+    case TP_NOT_CONVERGED: return "not converged";
+    case TP_BREAKDOWN: return "Krylov breakdown";
+    default: return "unknown status";
+  }
+}
+
+const char* tp_last_error(void) { return g_last_error.c_str(); }
+
+long long tp_kernel_launches(void) { return tp::launches_total(); }
+
+int tp_create(tp_ctx** out, const tp_grid* grid, const tp_fluid* fluid, void* cuda_stream) {
+  if (!out || !grid || !fluid) return TP_EINVAL;
+  *out = nullptr;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return TP_EINVAL;
+  long long N = (long long)grid->nx * grid->ny * grid->nz;
+  if (N > 200000000LL) return TP_EINVAL;
+  if (!(grid->dx > 0 && grid->dy > 0 && grid->dz > 0)) return TP_EINVAL;
+  tp_ctx* c = nullptr;
+  TP_API_BEGIN
+  c = new tp_ctx();
+  TP_CUDA_TRY(cudaGetDevice(&c->device));
+  TP_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  if (cuda_stream) {
+    c->s = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    // a blocking stream (ordered with the legacy default stream) owned here
+    TP_CUDA_TRY(cudaStreamCreate(&c->s));
+    owned_streams().push_back({c, c->s});
+  }
+  cudaStream_t s = c->s;
+  c->grid = {grid->nx, grid->ny, grid->nz, grid->dx, grid->dy, grid->dz, grid->g};
+  c->fluid = {fluid->rho0, fluid->c,     fluid->beta,    fluid->p0, fluid->T0,
+              fluid->mu0,  fluid->T_mu0, fluid->mu_coef, fluid->cv, fluid->rho_r,
+              fluid->cr,   fluid->kTf,   fluid->kT_mix};
+  const int n = (int)N;
+  c->N = n;
+  long long nnzb = N + 2LL * ((long long)(grid->nx - 1) * grid->ny * grid->nz +
+                              (long long)grid->nx * (grid->ny - 1) * grid->nz +
+                              (long long)grid->nx * grid->ny * (grid->nz - 1));
+  c->nnzb = (int)nnzb;
+  tp::Pool& P = c->pool;
+  c->rowptr = P.alloc<int>(n + 1);
+  c->col = P.alloc<int>(nnzb);
+  c->dpos = P.alloc<int>(n);
+  tp::launch_pattern(c->grid, c->rowptr, c->col, c->dpos, s);
+  for (double** f : {&c->Kx, &c->Ky, &c->Kz, &c->phi, &c->kTr, &c->kT, &c->p, &c->T, &c->pn,
+                     &c->Tn, &c->rho, &c->lam, &c->lam_p, &c->lam_T, &c->Rm, &c->Re, &c->bp_s,
+                     &c->bT_s, &c->tmpN, &c->io0, &c->io1, &c->io2, &c->io3})
+    *f = P.alloc<double>(n);
+  c->bval = P.alloc<double>(4 * nnzb);
+  c->Sval = P.alloc<double>(nnzb);
+  c->App = P.alloc<double>(nnzb);
+  c->ApT = P.alloc<double>(nnzb);
+  c->ATp = P.alloc<double>(nnzb);
+  c->ATT = P.alloc<double>(nnzb);
+  c->scales = P.alloc<double>(2);
+  c->ones = P.alloc<double>(2);
+  const double one2[2] = {1.0, 1.0};
+  TP_CUDA_TRY(cudaMemcpyAsync(c->ones, one2, sizeof(one2), cudaMemcpyHostToDevice, s));
+  c->nparts = std::max(1, std::min(2 * c->num_sms, (n + 255) / 256));
+  c->partials = P.alloc<double>(c->nparts + 1);
+  TP_CUDA_TRY(cudaMallocHost(&c->host_est, 16 * sizeof(double)));
+  tp_default_opts(&c->opts);
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = c;
+  return TP_OK;
+  }
+  catch (const Error& e) {
+    g_last_error = e.what;
+    cudaGetLastError();
+    if (c) tp_destroy(c);
+    return e.code;
+  }
+  catch (...) {
+    if (c) tp_destroy(c);
+    return TP_ENOMEM;
+  }
+}
+
+void tp_destroy(tp_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->s);
+  cudaStream_t own = nullptr;
+  auto& v = owned_streams();
+  for (size_t i = 0; i < v.size(); ++i)
+    if (v[i].first == c) {
+      own = v[i].second;
+      v.erase(v.begin() + i);
+      break;
+    }
+  delete c;
+  if (own) cudaStreamDestroy(own);
+}
+
+int tp_get_sizes(const tp_ctx* c, int* N, int* nnzb) {
+  if (!c) return TP_EINVAL;
+  if (N) *N = c->N;
+  if (nnzb) *nnzb = c->nnzb;
+  return TP_OK;
+}
+
+int tp_set_fields(tp_ctx* c, const double* Kx, const double* Ky, const double* Kz,
+                  const double* phi, const double* kTr, int ptr_is_device) {
+  if (!c || !Kx || !Ky || !Kz || !phi || !kTr) return TP_EINVAL;
+  TP_API_BEGIN
+  cudaStream_t s = c->s;
+  const size_t n = c->N;
+  to_device(c->Kx, Kx, n, ptr_is_device, s);
+  to_device(c->Ky, Ky, n, ptr_is_device, s);
+  to_device(c->Kz, Kz, n, ptr_is_device, s);
+  to_device(c->phi, phi, n, ptr_is_device, s);
+  to_device(c->kTr, kTr, n, ptr_is_device, s);
+  int* flags = reinterpret_cast<int*>(c->partials);
+  TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  k_check_fields<<<tp::grid_for(c->N), tp::kBlock, 0, s>>>(c->N, c->Kx, c->Ky, c->Kz, c->phi,
+                                                           c->kTr, flags);
+  TP_LAUNCH_CHECK();
+  int f = read_flags(flags, s);
+  if (f & 1) return TP_ENONFINITE;
+  if (f & 2) return TP_EINVAL;
+  tp::launch_mix_conductivity(c->N, c->phi, c->kTr, c->fluid, c->kT, s);
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  c->fields_set = true;
+  c->assembled = false;
+  c->built = false;
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_set_wells(tp_ctx* c, const tp_well* w, int n) {
+  if (!c || n < 0 || (n > 0 && !w)) return TP_EINVAL;
+  TP_API_BEGIN
+  // expand into completions grouped by cell (input order kept within a cell)
+  struct Comp { int cell, kind, nl; double value, Tinj, U; int order; };
+  std::vector<Comp> comps;
+  for (int q = 0; q < n; ++q) {
+    const tp_well& x = w[q];
+    if (x.kind < 0 || x.kind > 3) return TP_EINVAL;
+    if (x.i < 0 || x.i >= c->grid.nx || x.j < 0 || x.j >= c->grid.ny || x.k0 < 0 ||
+        x.k1 < x.k0 || x.k1 >= c->grid.nz)
+      return TP_EINVAL;
+    if (!std::isfinite(x.value) || !std::isfinite(x.T_inj) || !std::isfinite(x.U))
+      return TP_ENONFINITE;
+    const int nl = x.k1 - x.k0 + 1;
+    for (int k = x.k0; k <= x.k1; ++k) {
+      int cell = x.i + c->grid.nx * (x.j + c->grid.ny * k);
+      comps.push_back({cell, x.kind, nl, x.value, x.T_inj, x.U, (int)comps.size()});
+    }
+  }
+  std::stable_sort(comps.begin(), comps.end(),
+                   [](const Comp& a, const Comp& b) { return a.cell < b.cell; });
+  std::vector<int> cells, off, kind, nl;
+  std::vector<double> value, Tinj, U;
+  for (size_t q = 0; q < comps.size(); ++q) {
+    if (q == 0 || comps[q].cell != comps[q - 1].cell) {
+      cells.push_back(comps[q].cell);
+      off.push_back((int)q);
+    }
+    kind.push_back(comps[q].kind);
+    nl.push_back(comps[q].nl);
+    value.push_back(comps[q].value);
+    Tinj.push_back(comps[q].Tinj);
+    U.push_back(comps[q].U);
+  }
+  off.push_back((int)comps.size());
+  cudaStream_t s = c->s;
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  c->wpool.release();
+  tp::WellsDev d;
+  d.ncells = (int)cells.size();
+  if (d.ncells > 0) {
+    const size_t nc = comps.size();
+    d.cell = c->wpool.alloc<int>(cells.size());
+    d.off = c->wpool.alloc<int>(off.size());
+    d.kind = c->wpool.alloc<int>(nc);
+    d.nlayers = c->wpool.alloc<int>(nc);
+    d.value = c->wpool.alloc<double>(nc);
+    d.T_inj = c->wpool.alloc<double>(nc);
+    d.U = c->wpool.alloc<double>(nc);
+    TP_CUDA_TRY(cudaMemcpy(d.cell, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TP_CUDA_TRY(cudaMemcpy(d.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TP_CUDA_TRY(cudaMemcpy(d.kind, kind.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
+    TP_CUDA_TRY(cudaMemcpy(d.nlayers, nl.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
+    TP_CUDA_TRY(cudaMemcpy(d.value, value.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
+    TP_CUDA_TRY(cudaMemcpy(d.T_inj, Tinj.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
+    TP_CUDA_TRY(cudaMemcpy(d.U, U.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  c->wells = d;
+  c->assembled = false;
+  c->built = false;
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_assemble(tp_ctx* c, const double* p_k, const double* T_k, const double* p_n,
+                const double* T_n, double dt, double* R_m, double* R_e, int ptr_is_device) {
+  if (!c || !p_k || !T_k || !p_n || !T_n) return TP_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return TP_EINVAL;
+  if (!c->fields_set) return TP_ESTATE;
+  TP_API_BEGIN
+  cudaStream_t s = c->s;
+  const size_t n = c->N;
+  to_device(c->p, p_k, n, ptr_is_device, s);
+  to_device(c->T, T_k, n, ptr_is_device, s);
+  to_device(c->pn, p_n, n, ptr_is_device, s);
+  to_device(c->Tn, T_n, n, ptr_is_device, s);
+  int* flags = reinterpret_cast<int*>(c->partials);
+  TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  for (const double* a : {c->p, c->T, c->pn, c->Tn}) {
+    k_check_finite<<<tp::grid_for(n), tp::kBlock, 0, s>>>(n, a, flags);
+    TP_LAUNCH_CHECK();
+  }
+  if (read_flags(flags, s)) return TP_ENONFINITE;
+  tp::launch_cell_props(c->N, c->p, c->T, c->fluid, c->rho, c->lam, c->lam_p, c->lam_T, s);
+  tp::launch_assemble(c->grid, c->fluid, c->rowptr, c->dpos, c->Kx, c->Ky, c->Kz, c->phi, c->kT,
+                      c->p, c->T, c->pn, c->Tn, c->rho, c->lam, c->lam_p, c->lam_T, dt, c->bval,
+                      c->Sval, c->Rm, c->Re, s);
+  tp::launch_wells(c->grid, c->fluid, c->wells, c->dpos, c->Kx, c->Ky, c->p, c->T, c->rho,
+                   c->lam, c->lam_p, c->lam_T, c->bval, c->Sval, c->Rm, c->Re, s);
+  TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  k_check_finite<<<tp::grid_for(4ll * c->nnzb), tp::kBlock, 0, s>>>(4ll * c->nnzb, c->bval, flags);
+  TP_LAUNCH_CHECK();
+  if (R_m) from_device(R_m, c->Rm, n, ptr_is_device, s);
+  if (R_e) from_device(R_e, c->Re, n, ptr_is_device, s);
+  if (read_flags(flags, s)) return TP_ENONFINITE;
+  c->assembled = true;
+  c->built = false;
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_build_preconditioner(tp_ctx* c, const tp_precond_opts* opts) {
+  if (!c) return TP_EINVAL;
+  if (!c->assembled) return TP_ESTATE;
+  TP_API_BEGIN
+  tp_precond_opts o;
+  if (opts) o = *opts;
+  else tp_default_opts(&o);
+  check_opts(o);
+  cudaStream_t s = c->s;
+  if (c->pc_graph) {
+    cudaGraphExecDestroy(c->pc_graph);
+    c->pc_graph = nullptr;
+  }
+  c->built = false;
+  tp::launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+  tp::launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
+                             c->scales, s);
+  c->S_active = (o.schur == 2) ? c->ATT : c->Sval;
+  tp::DevCSR App{c->N, c->N, c->nnzb, c->rowptr, c->col, c->App, nullptr};
+  tp::DevCSR S{c->N, c->N, c->nnzb, c->rowptr, c->col, c->S_active, nullptr};
+  c->opts = o;
+  c->hpp.reset(new tp::Hierarchy());
+  c->hS.reset(new tp::Hierarchy());
+  tp::AmgOpts ao = amg_opts(o);
+  c->hpp->setup(App, ao, s);
+  c->hS->setup(S, ao, s);
+  if (o.use_graphs) {
+    cudaGraph_t graph = nullptr;
+    TP_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    tp::g_capturing = true;
+    try {
+      tp::precond_record(c, s);
+    } catch (...) {
+      tp::g_capturing = false;
+      cudaStreamEndCapture(s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    tp::g_capturing = false;
+    TP_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+    size_t nodes = 0;
+    TP_CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nodes));
+    c->pc_graph_kernels = (long long)nodes;
+    cudaError_t e = cudaGraphInstantiate(&c->pc_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->pc_graph = nullptr;
+      fail(TP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+  }
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  c->built = true;
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_solve(tp_ctx* c, const double* b_p, const double* b_T, double* x_p, double* x_T,
+             double rtol, int maxit, int restart, tp_solve_info* info, int ptr_is_device) {
+  if (!c || !x_p || !x_T) return TP_EINVAL;
+  if ((b_p == nullptr) != (b_T == nullptr)) return TP_EINVAL;
+  if (!(rtol > 0.0) || maxit < 1 || restart < 1 || restart > 200) return TP_EINVAL;
+  if (!c->built) return TP_ESTATE;
+  TP_API_BEGIN
+  cudaStream_t s = c->s;
+  const size_t n = c->N;
+  // right-hand side on the device: caller's, or -G(x_k)
+  const double* bp;
+  const double* bT;
+  if (b_p) {
+    to_device(c->io0, b_p, n, ptr_is_device, s);
+    to_device(c->io1, b_T, n, ptr_is_device, s);
+  } else {
+    // b = -R
+    TP_CUDA_TRY(cudaMemcpyAsync(c->io0, c->Rm, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TP_CUDA_TRY(cudaMemcpyAsync(c->io1, c->Re, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    negate(c->io0, n, s);
+    negate(c->io1, n, s);
+  }
+  bp = c->io0;
+  bT = c->io1;
+  int st = tp::fgmres_solve(c, bp, bT, c->io2, c->io3, rtol, maxit, restart, info);
+  from_device(x_p, c->io2, n, ptr_is_device, s);
+  from_device(x_T, c->io3, n, ptr_is_device, s);
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
+  TP_API_END
+}
+
+int tp_spmv(tp_ctx* c, const double* x_p, const double* x_T, double* y_p, double* y_T,
+            int ptr_is_device) {
+  if (!c || !x_p || !x_T || !y_p || !y_T) return TP_EINVAL;
+  if (!c->assembled) return TP_ESTATE;
+  TP_API_BEGIN
+  cudaStream_t s = c->s;
+  const size_t n = c->N;
+  to_device(c->io0, x_p, n, ptr_is_device, s);
+  to_device(c->io1, x_T, n, ptr_is_device, s);
+  tp::launch_block_spmv(c->N, c->rowptr, c->col, c->bval, c->io0, c->io1, c->io2, c->io3, nullptr,
+                        s);
+  from_device(y_p, c->io2, n, ptr_is_device, s);
+  from_device(y_T, c->io3, n, ptr_is_device, s);
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_apply_preconditioner(tp_ctx* c, const double* v_p, const double* v_T, double* z_p,
+                            double* z_T, int ptr_is_device) {
+  if (!c || !v_p || !v_T || !z_p || !z_T) return TP_EINVAL;
+  if (!c->built) return TP_ESTATE;
+  TP_API_BEGIN
+  cudaStream_t s = c->s;
+  const size_t n = c->N;
+  to_device(c->io0, v_p, n, ptr_is_device, s);
+  to_device(c->io1, v_T, n, ptr_is_device, s);
+  tp::precond_apply(c, c->io0, c->io1, c->ones, s);
+  from_device(z_p, c->hpp->out, n, ptr_is_device, s);
+  from_device(z_T, c->hS->out, n, ptr_is_device, s);
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_export_system(tp_ctx* c, int* rowptr, int* col, double* val, double* schur_val,
+                     double* scales) {
+  if (!c) return TP_EINVAL;
+  if (!c->assembled) return TP_ESTATE;
+  TP_API_BEGIN
+  cudaStream_t s = c->s;
+  if (rowptr)
+    TP_CUDA_TRY(cudaMemcpyAsync(rowptr, c->rowptr, (c->N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (col) TP_CUDA_TRY(cudaMemcpyAsync(col, c->col, c->nnzb * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (val)
+    TP_CUDA_TRY(cudaMemcpyAsync(val, c->bval, 4ll * c->nnzb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (schur_val)
+    TP_CUDA_TRY(cudaMemcpyAsync(schur_val, c->Sval, c->nnzb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (scales) {
+    if (!c->built) {
+      tp::launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+      tp::launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
+                                 c->scales, s);
+    }
+    TP_CUDA_TRY(cudaMemcpyAsync(scales, c->scales, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+  TP_API_END
+}
+
+static int hierarchy_info(tp::Hierarchy* h, int* nlevels, int* n, int* nnz, int max_levels) {
+  if (!h) return TP_ESTATE;
+  if (nlevels) *nlevels = (int)h->L.size();
+  for (int l = 0; l < (int)h->L.size() && l < max_levels; ++l) {
+    if (n) n[l] = h->L[l].A.n;
+    if (nnz) nnz[l] = h->L[l].A.nnz;
+  }
+  return TP_OK;
+}
+
+static int export_level(tp::Hierarchy* h, cudaStream_t s, int level, int* rowptr, int* col,
+                        double* val, signed char* cf, signed char* strong, int* P_nnz,
+                        int* P_rowptr, int* P_col, double* P_val) {
+  if (!h) return TP_ESTATE;
+  if (level < 0 || level >= (int)h->L.size()) return TP_EINVAL;
+  TP_API_BEGIN
+  const tp::Level& v = h->L[level];
+  const tp::DevCSR& A = v.A;
+  if (rowptr) TP_CUDA_TRY(cudaMemcpyAsync(rowptr, A.rowptr, (A.n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (col) TP_CUDA_TRY(cudaMemcpyAsync(col, A.col, A.nnz * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (val) TP_CUDA_TRY(cudaMemcpyAsync(val, A.val, A.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (cf) {
+    if (v.cf) TP_CUDA_TRY(cudaMemcpyAsync(cf, v.cf, A.n, cudaMemcpyDeviceToHost, s));
+    else std::memset(cf, 0, A.n);
+  }
+  if (strong) {
+    if (v.strong) TP_CUDA_TRY(cudaMemcpyAsync(strong, v.strong, A.nnz, cudaMemcpyDeviceToHost, s));
+    else std::memset(strong, 0, A.nnz);
+  }
+  if (P_nnz) *P_nnz = v.P.nnz;
+  if (v.P.nnz > 0) {
+    if (P_rowptr) TP_CUDA_TRY(cudaMemcpyAsync(P_rowptr, v.P.rowptr, (v.P.n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (P_col) TP_CUDA_TRY(cudaMemcpyAsync(P_col, v.P.col, v.P.nnz * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (P_val) TP_CUDA_TRY(cudaMemcpyAsync(P_val, v.P.val, v.P.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_hierarchy_info(tp_ctx* c, int which, int* nlevels, int* n, int* nnz, int max_levels) {
+  if (!c || (which != 0 && which != 1)) return TP_EINVAL;
+  if (!c->built) return TP_ESTATE;
+  return hierarchy_info(which == 0 ? c->hpp.get() : c->hS.get(), nlevels, n, nnz, max_levels);
+}
+
+int tp_export_level(tp_ctx* c, int which, int level, int* rowptr, int* col, double* val,
+                    signed char* cf, signed char* strong, int* P_nnz, int* P_rowptr, int* P_col,
+                    double* P_val) {
+  if (!c || (which != 0 && which != 1)) return TP_EINVAL;
+  if (!c->built) return TP_ESTATE;
+  return export_level(which == 0 ? c->hpp.get() : c->hS.get(), c->s, level, rowptr, col, val, cf,
+                      strong, P_nnz, P_rowptr, P_col, P_val);
+}
+
+int tp_amg_create(tp_amg** out, int n, int nnz, const int* rowptr, const int* col,
+                  const double* val, const tp_precond_opts* opts, void* cuda_stream,
+                  int ptr_is_device) {
+  if (!out || n < 1 || nnz < n || !rowptr || !col || !val) return TP_EINVAL;
+  *out = nullptr;
+  tp_amg* a = nullptr;
+  TP_API_BEGIN
+  tp_precond_opts o;
+  if (opts) o = *opts;
+  else tp_default_opts(&o);
+  check_opts(o);
+  a = new tp_amg();
+  if (cuda_stream) {
+    a->s = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    TP_CUDA_TRY(cudaStreamCreate(&a->s));
+    a->own_stream = true;
+  }
+  cudaStream_t s = a->s;
+  // validate the pattern on the host side when it is host memory
+  if (!ptr_is_device) {
+    if (rowptr[0] != 0 || rowptr[n] != nnz) {
+      delete a;
+      return TP_EINVAL;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (rowptr[i + 1] < rowptr[i]) { delete a; return TP_EINVAL; }
+      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        if (col[e] < 0 || col[e] >= n || (e > rowptr[i] && col[e] <= col[e - 1]) ||
+            !std::isfinite(val[e])) {
+          delete a;
+          return TP_EINVAL;
+        }
+      }
+    }
+  }
+  a->A.n = a->A.m = n;
+  a->A.nnz = nnz;
+  a->A.rowptr = a->pool.alloc<int>(n + 1);
+  a->A.col = a->pool.alloc<int>(nnz);
+  a->A.val = a->pool.alloc<double>(nnz);
+  cudaMemcpyKind k = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  TP_CUDA_TRY(cudaMemcpyAsync(a->A.rowptr, rowptr, (n + 1) * sizeof(int), k, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(a->A.col, col, nnz * sizeof(int), k, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(a->A.val, val, nnz * sizeof(double), k, s));
+  a->h.reset(new tp::Hierarchy());
+  a->h->setup(a->A, amg_opts(o), s);
+  *out = a;
+  return TP_OK;
+  }
+  catch (const Error& e) {
+    g_last_error = e.what;
+    cudaGetLastError();
+    delete a;
+    return e.code;
+  }
+  catch (...) {
+    delete a;
+    return TP_ECUDA;
+  }
+}
+
+void tp_amg_destroy(tp_amg* a) {
+  if (!a) return;
+  cudaStreamSynchronize(a->s);
+  delete a;
+}
+
+int tp_amg_vcycle(tp_amg* a, const double* b, double* x, int ptr_is_device) {
+  if (!a || !b || !x) return TP_EINVAL;
+  TP_API_BEGIN
+  const size_t n = a->A.n;
+  to_device(a->h->in, b, n, ptr_is_device, a->s);
+  a->h->vcycle(a->s);
+  from_device(x, a->h->out, n, ptr_is_device, a->s);
+  TP_CUDA_TRY(cudaStreamSynchronize(a->s));
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_amg_info(tp_amg* a, int* nlevels, int* n, int* nnz, int max_levels) {
+  if (!a) return TP_EINVAL;
+  return hierarchy_info(a->h.get(), nlevels, n, nnz, max_levels);
+}
+
+int tp_amg_export_level(tp_amg* a, int level, int* rowptr, int* col, double* val,
+                        signed char* cf, signed char* strong, int* P_nnz, int* P_rowptr,
+                        int* P_col, double* P_val) {
+  if (!a) return TP_EINVAL;
+  return export_level(a->h.get(), a->s, level, rowptr, col, val, cf, strong, P_nnz, P_rowptr,
+                      P_col, P_val);
+}
+
+}  // extern "C"
+

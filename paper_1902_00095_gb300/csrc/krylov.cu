@@ -1,0 +1,533 @@
+// Block preconditioner (Sec. 3.2) and flexible GMRES (Sec. 4 solver
+// settings: right preconditioning, restart 30).
+//
+// Krylov vectors are split [p (N) | T (N)]. The solve works on the
+// equation-scaled system D A x = D b, D = diag(s_m I, s_e I) (the mass and
+// energy rows differ by ~10 orders of magnitude in SI units); the block
+// preconditioner of D A is M^{-1} D^{-1} because each V-cycle is linear and
+// scale-homogeneous. Orthogonalisation is classical Gram-Schmidt with one
+// re-orthogonalisation (CGS2); all reductions use a fixed block partition and
+// tree order, so results are deterministic.
+#include <cmath>
+#include <chrono>
+#include "solver.cuh"
+
+namespace tp {
+
+namespace {
+
+constexpr int kDotV = 8;  // vectors per multi-dot pass
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void chunk_of(long long n, long long& lo, long long& hi) {
+  long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  lo = chunk * blockIdx.x;
+  hi = lo + chunk;
+  if (hi > n) hi = n;
+}
+
+// block-level sum of one value per thread -> out (thread 0 writes)
+__device__ __forceinline__ void block_sum_store(double v, double* out) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) *out = t;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------ preconditioner pieces
+__global__ void k_precond_in(int N, const double* __restrict__ vp, const double* __restrict__ vT,
+                             const double* __restrict__ scales, double* __restrict__ bp_s,
+                             double* __restrict__ bT_s, double* __restrict__ hin) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double a = vp[i] / scales[0];
+  bp_s[i] = a;
+  hin[i] = a;
+  bT_s[i] = vT[i] / scales[1];
+}
+
+// out = b - A x over the shared 7-point pattern (steps 2 and 4 of Sec. 3.2)
+__global__ void k_rhs_minus(int N, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, const double* __restrict__ b,
+                            const double* __restrict__ x, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double acc = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) acc += val[e] * x[col[e]];
+  out[i] = b[i] - acc;
+}
+
+// w = D A z (block-CSR, Eq. AXR); optionally stores z into Z_j.
+__global__ void __launch_bounds__(256) k_block_spmv(int N, const int* __restrict__ rp,
+                                                    const int* __restrict__ col,
+                                                    const double4_32a* __restrict__ bval,
+                                                    const double* __restrict__ zp,
+                                                    const double* __restrict__ zT,
+                                                    double* __restrict__ Zp,
+                                                    double* __restrict__ ZT,
+                                                    double* __restrict__ wp,
+                                                    double* __restrict__ wT,
+                                                    const double* __restrict__ scales) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double ap = 0.0, aT = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int j = col[e];
+    const double4_32a b = bval[e];
+    const double xp = zp[j], xT = zT[j];
+    ap += b.x * xp + b.y * xT;
+    aT += b.z * xp + b.w * xT;
+  }
+  if (Zp) {
+    Zp[i] = zp[i];
+    ZT[i] = zT[i];
+  }
+  const double s0 = scales ? scales[0] : 1.0, s1 = scales ? scales[1] : 1.0;
+  wp[i] = s0 * ap;
+  wT[i] = s1 * aT;
+}
+
+// ------------------------------------------------------------ Gram-Schmidt
+template <int NV>
+__global__ void __launch_bounds__(256) k_mdot(long long n2, const double* __restrict__ V,
+                                              long long stride, int k0, int nv,
+                                              const double* __restrict__ w,
+                                              double* __restrict__ partials) {
+  long long lo, hi;
+  chunk_of(n2, lo, hi);
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q < nv) acc[q] += wi * V[(long long)(k0 + q) * stride + i];
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    if (q < nv) block_sum_store(acc[q], &partials[(long long)(k0 + q) * gridDim.x + blockIdx.x]);
+  }
+}
+
+// out[k] = sum_b partials[k * B + b], k < count (fixed order)
+__global__ void k_reduce_rows(int count, int B, const double* __restrict__ partials,
+                              double* __restrict__ out) {
+  const int k = blockIdx.x;
+  if (k >= count) return;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) v += partials[(long long)k * B + b];
+  block_sum_store(v, &out[k]);
+}
+
+// w -= sum_k h_k V_k; optionally per-block partial sums of w^2
+__global__ void __launch_bounds__(256) k_orth_update(long long n2, const double* __restrict__ V,
+                                                     long long stride, int count,
+                                                     const double* __restrict__ h,
+                                                     double* __restrict__ w,
+                                                     double* __restrict__ norm_partials) {
+  long long lo, hi;
+  chunk_of(n2, lo, hi);
+  double nrm = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double a = w[i];
+    for (int k = 0; k < count; ++k) a -= h[k] * V[(long long)k * stride + i];
+    w[i] = a;
+    nrm += a * a;
+  }
+  if (norm_partials) block_sum_store(nrm, &norm_partials[blockIdx.x]);
+}
+
+// Arnoldi column j: H(:, j) = h1 + h2, H(j+1, j) = ||w||, Givens update.
+__global__ void k_arnoldi(int j, int ldh, double* __restrict__ H, double* __restrict__ cs,
+                          double* __restrict__ sn, double* __restrict__ g,
+                          const double* __restrict__ h1, const double* __restrict__ h2,
+                          const double* __restrict__ npart, int B, double* __restrict__ hn_out,
+                          double* __restrict__ est) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* Hj = H + (long long)j * ldh;
+  for (int k = 0; k <= j; ++k) Hj[k] = h1[k] + h2[k];
+  double s = 0.0;
+  for (int b = 0; b < B; ++b) s += npart[b];
+  const double hn = sqrt(s);
+  Hj[j + 1] = hn;
+  for (int k = 0; k < j; ++k) {
+    const double t = cs[k] * Hj[k] + sn[k] * Hj[k + 1];
+    Hj[k + 1] = -sn[k] * Hj[k] + cs[k] * Hj[k + 1];
+    Hj[k] = t;
+  }
+  const double den = hypot(Hj[j], Hj[j + 1]);
+  if (den > 0.0) {
+    cs[j] = Hj[j] / den;
+    sn[j] = Hj[j + 1] / den;
+  } else {
+    cs[j] = 1.0;
+    sn[j] = 0.0;
+  }
+  Hj[j] = den;
+  Hj[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  *hn_out = hn;
+  est[0] = fabs(g[j + 1]);
+  est[1] = hn;
+  est[2] = den;
+}
+
+__global__ void k_normalize(long long n2, const double* __restrict__ w,
+                            const double* __restrict__ hn, double* __restrict__ v) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n2) v[i] = w[i] / hn[0];
+}
+
+// first basis vector and Givens right-hand side: v0 = r / beta, g = beta e1
+__global__ void k_start_cycle(long long n2, const double* __restrict__ r,
+                              const double* __restrict__ beta, double* __restrict__ v0,
+                              double* __restrict__ g, int restart) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n2) v0[i] = r[i] / beta[0];
+  if (i <= restart) g[i] = (i == 0) ? beta[0] : 0.0;
+}
+
+// y = H(0:m, 0:m)^{-1} g (upper triangular back substitution)
+__global__ void k_hsolve(int m, int ldh, const double* __restrict__ H,
+                         const double* __restrict__ g, double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = m - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int k = i + 1; k < m; ++k) s -= H[(long long)k * ldh + i] * y[k];
+    y[i] = s / H[(long long)i * ldh + i];
+  }
+}
+
+// x += sum_k y_k Z_k
+__global__ void k_update_x(long long n2, const double* __restrict__ Z, long long stride, int m,
+                           const double* __restrict__ y, double* __restrict__ x) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  double a = x[i];
+  for (int k = 0; k < m; ++k) a += y[k] * Z[(long long)k * stride + i];
+  x[i] = a;
+}
+
+// bs = D b and partial ||bs||^2
+__global__ void __launch_bounds__(256) k_scale_rhs(int N, const double* __restrict__ bp,
+                                                   const double* __restrict__ bT,
+                                                   const double* __restrict__ scales,
+                                                   double* __restrict__ bs,
+                                                   double* __restrict__ partials) {
+  long long lo, hi;
+  chunk_of(2ll * N, lo, hi);
+  double s = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double v = (i < N) ? scales[0] * bp[i] : scales[1] * bT[i - N];
+    bs[i] = v;
+    s += v * v;
+  }
+  block_sum_store(s, &partials[blockIdx.x]);
+}
+
+// r = bs - D A x and partial ||r||^2 (row-parallel over the 2N rows)
+__global__ void __launch_bounds__(256) k_true_residual(int N, const int* __restrict__ rp,
+                                                       const int* __restrict__ col,
+                                                       const double4_32a* __restrict__ bval,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ bs,
+                                                       const double* __restrict__ scales,
+                                                       double* __restrict__ r,
+                                                       double* __restrict__ partials) {
+  long long lo, hi;
+  chunk_of(N, lo, hi);
+  double s = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double ap = 0.0, aT = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = col[e];
+      const double4_32a b = bval[e];
+      const double xp = x[j], xT = x[N + j];
+      ap += b.x * xp + b.y * xT;
+      aT += b.z * xp + b.w * xT;
+    }
+    const double rp_ = bs[i] - scales[0] * ap, rT_ = bs[N + i] - scales[1] * aT;
+    r[i] = rp_;
+    r[N + i] = rT_;
+    s += rp_ * rp_ + rT_ * rT_;
+  }
+  block_sum_store(s, &partials[blockIdx.x]);
+}
+
+// unscaled per-block residual sums: ||r_p||^2, ||r_T||^2, ||b_p||^2, ||b_T||^2
+__global__ void __launch_bounds__(256) k_unscaled_sums(int N, const int* __restrict__ rp,
+                                                       const int* __restrict__ col,
+                                                       const double4_32a* __restrict__ bval,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ bp,
+                                                       const double* __restrict__ bT,
+                                                       double* __restrict__ partials) {
+  long long lo, hi;
+  chunk_of(N, lo, hi);
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double ap = 0.0, aT = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = col[e];
+      const double4_32a b = bval[e];
+      ap += b.x * x[j] + b.y * x[N + j];
+      aT += b.z * x[j] + b.w * x[N + j];
+    }
+    const double a = bp[i] - ap, c = bT[i] - aT;
+    s[0] += a * a;
+    s[1] += c * c;
+    s[2] += bp[i] * bp[i];
+    s[3] += bT[i] * bT[i];
+  }
+  for (int q = 0; q < 4; ++q) block_sum_store(s[q], &partials[(long long)q * gridDim.x + blockIdx.x]);
+}
+
+__global__ void k_sum_to(const double* __restrict__ partials, int B, double* __restrict__ out) {
+  double v = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) v += partials[b];
+  block_sum_store(v, out);
+}
+
+__global__ void k_sqrt_inplace(double* v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) v[0] = sqrt(v[0]);
+}
+
+void mdot_all(long long n2, const double* V, long long stride, int count, const double* w,
+              double* partials, int B, double* out, cudaStream_t s) {
+  for (int k0 = 0; k0 < count; k0 += kDotV) {
+    int nv = count - k0 < kDotV ? count - k0 : kDotV;
+    k_mdot<kDotV><<<B, 256, 0, s>>>(n2, V, stride, k0, nv, w, partials);
+    TP_LAUNCH_CHECK();
+  }
+  k_reduce_rows<<<count, 256, 0, s>>>(count, B, partials, out);
+  TP_LAUNCH_CHECK();
+}
+
+double read_double(const double* d, double* host_pinned, cudaStream_t s) {
+  TP_CUDA_TRY(cudaMemcpyAsync(host_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return *host_pinned;
+}
+
+void ensure_workspace(tp_ctx* c, int restart) {
+  if (c->restart_alloc >= restart && c->Vb) return;
+  c->kpool.release();
+  const long long n2 = 2ll * c->N;
+  c->Vb = c->kpool.alloc<double>((size_t)(restart + 1) * n2);
+  c->Zb = c->kpool.alloc<double>((size_t)restart * n2);
+  c->w = c->kpool.alloc<double>(n2);
+  c->xs = c->kpool.alloc<double>(n2);
+  c->bs = c->kpool.alloc<double>(n2);
+  const int ldh = restart + 1;
+  c->H = c->kpool.alloc<double>((size_t)ldh * (restart + 1));
+  c->cs = c->kpool.alloc<double>(restart + 1);
+  c->sn = c->kpool.alloc<double>(restart + 1);
+  c->g = c->kpool.alloc<double>(restart + 2);
+  c->yv = c->kpool.alloc<double>(restart + 1);
+  c->hn = c->kpool.alloc<double>(4);
+  c->est = c->kpool.alloc<double>(4);
+  c->h2 = c->kpool.alloc<double>(2 * (restart + 2));
+  c->kparts = c->kpool.alloc<double>((size_t)(restart + 2) * 4 * c->nparts + 16);
+  c->restart_alloc = restart;
+}
+
+}  // namespace
+
+void launch_block_spmv(int N, const int* rowptr, const int* col, const double* bval,
+                       const double* xp, const double* xT, double* yp, double* yT,
+                       const double* scales, cudaStream_t s) {
+  k_block_spmv<<<grid_for(N), kBlock, 0, s>>>(N, rowptr, col,
+                                              reinterpret_cast<const double4_32a*>(bval), xp, xT,
+                                              nullptr, nullptr, yp, yT, scales);
+  TP_LAUNCH_CHECK();
+}
+
+void precond_record(tp_ctx* c, cudaStream_t s) {
+  Hierarchy& hp = *c->hpp;
+  Hierarchy& hs = *c->hS;
+  const int N = c->N;
+  hp.vcycle(s);  // step 1: x_p = V_pp(b_p)
+  k_rhs_minus<<<grid_for(N), kBlock, 0, s>>>(N, c->rowptr, c->col, c->ATp, c->bT_s, hp.out,
+                                             hs.in);  // step 2
+  TP_LAUNCH_CHECK();
+  hs.vcycle(s);  // step 3: d_T = V_S(bt_T)
+  if (c->opts.variant == 0) {
+    k_rhs_minus<<<grid_for(N), kBlock, 0, s>>>(N, c->rowptr, c->col, c->ApT, c->bp_s, hs.out,
+                                               hp.in);  // step 4
+    TP_LAUNCH_CHECK();
+    hp.vcycle(s);  // step 5: d_p = V_pp(bt_p)
+  }
+}
+
+void precond_apply(tp_ctx* c, const double* vp, const double* vT, const double* scales,
+                   cudaStream_t s) {
+  const int N = c->N;
+  k_precond_in<<<grid_for(N), kBlock, 0, s>>>(N, vp, vT, scales, c->bp_s, c->bT_s, c->hpp->in);
+  TP_LAUNCH_CHECK();
+  if (c->pc_graph) {
+    TP_CUDA_TRY(cudaGraphLaunch(c->pc_graph, s));
+    count_launch(c->pc_graph_kernels);
+  } else {
+    precond_record(c, s);
+  }
+}
+
+int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, double* xT,
+                 double rtol, int maxit, int restart, tp_solve_info* info) {
+  cudaStream_t s = c->s;
+  ensure_workspace(c, restart);
+  const int N = c->N;
+  const long long n2 = 2ll * N;
+  const int B = c->nparts;
+  const int ldh = restart + 1;
+  double* hp_host = c->host_est;
+  auto t0 = std::chrono::steady_clock::now();
+
+  k_scale_rhs<<<B, 256, 0, s>>>(N, bp, bT, c->scales, c->bs, c->kparts);
+  TP_LAUNCH_CHECK();
+  k_sum_to<<<1, 256, 0, s>>>(c->kparts, B, c->hn + 2);
+  TP_LAUNCH_CHECK();
+  const double bnorm = std::sqrt(read_double(c->hn + 2, hp_host, s));
+  TP_CUDA_TRY(cudaMemsetAsync(c->xs, 0, sizeof(double) * n2, s));
+  int its = 0, restarts = 0, status = TP_NOT_CONVERGED;
+  double beta = bnorm;
+  bool breakdown = false;
+  if (!std::isfinite(bnorm)) fail(TP_ENONFINITE, "right-hand side is not finite");
+  if (bnorm == 0.0) {
+    status = TP_OK;
+  } else {
+    bool first = true;
+    double* r = c->w;  // residual shares the w buffer at cycle start
+    while (true) {
+      if (first) {
+        TP_CUDA_TRY(cudaMemcpyAsync(r, c->bs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+        TP_CUDA_TRY(cudaMemcpyAsync(c->hn, c->hn + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        k_sqrt_inplace<<<1, 32, 0, s>>>(c->hn);
+        TP_LAUNCH_CHECK();
+        first = false;
+      } else {
+        k_true_residual<<<B, 256, 0, s>>>(N, c->rowptr, c->col,
+                                          reinterpret_cast<const double4_32a*>(c->bval), c->xs,
+                                          c->bs, c->scales, r, c->kparts);
+        TP_LAUNCH_CHECK();
+        k_sum_to<<<1, 256, 0, s>>>(c->kparts, B, c->hn);
+        TP_LAUNCH_CHECK();
+        k_sqrt_inplace<<<1, 32, 0, s>>>(c->hn);
+        TP_LAUNCH_CHECK();
+        beta = read_double(c->hn, hp_host, s);
+      }
+      if (!std::isfinite(beta)) {
+        breakdown = true;
+        break;
+      }
+      if (beta <= rtol * bnorm) {
+        status = TP_OK;
+        break;
+      }
+      if (its >= maxit || breakdown) break;
+      k_start_cycle<<<grid_for(n2), kBlock, 0, s>>>(n2, r, c->hn, c->Vb, c->g, restart);
+      TP_LAUNCH_CHECK();
+      int m = 0;
+      for (int j = 0; j < restart; ++j) {
+        double* vj = c->Vb + (long long)j * n2;
+        double* zj = c->Zb + (long long)j * n2;
+        precond_apply(c, vj, vj + N, c->scales, s);
+        k_block_spmv<<<grid_for(N), kBlock, 0, s>>>(
+            N, c->rowptr, c->col, reinterpret_cast<const double4_32a*>(c->bval), c->hpp->out,
+            c->hS->out, zj, zj + N, c->w, c->w + N, c->scales);
+        TP_LAUNCH_CHECK();
+        // CGS2 against V_0..V_j
+        double* h1 = c->h2;
+        double* h2 = c->h2 + (restart + 2);
+        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h1, s);
+        k_orth_update<<<B, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h1, c->w, nullptr);
+        TP_LAUNCH_CHECK();
+        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h2, s);
+        double* npart = c->kparts + (long long)(restart + 2) * B;
+        k_orth_update<<<B, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h2, c->w, npart);
+        TP_LAUNCH_CHECK();
+        k_arnoldi<<<1, 32, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, npart, B, c->hn,
+                                   c->est);
+        TP_LAUNCH_CHECK();
+        TP_CUDA_TRY(cudaMemcpyAsync(hp_host, c->est, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TP_CUDA_TRY(cudaStreamSynchronize(s));
+        const double est = hp_host[0], hnv = hp_host[1], den = hp_host[2];
+        ++its;
+        m = j + 1;
+        if (!std::isfinite(est) || !std::isfinite(hnv) || !(den > 0.0)) {
+          breakdown = true;  // drop the singular or non-finite column j
+          m = j;
+          break;
+        }
+        if (est <= rtol * bnorm || its >= maxit) break;
+        if (hnv == 0.0) break;  // happy breakdown: the solution is in the space
+        k_normalize<<<grid_for(n2), kBlock, 0, s>>>(n2, c->w, c->hn, c->Vb + (long long)(j + 1) * n2);
+        TP_LAUNCH_CHECK();
+      }
+      if (m > 0) {
+        k_hsolve<<<1, 32, 0, s>>>(m, ldh, c->H, c->g, c->yv);
+        TP_LAUNCH_CHECK();
+        k_update_x<<<grid_for(n2), kBlock, 0, s>>>(n2, c->Zb, n2, m, c->yv, c->xs);
+        TP_LAUNCH_CHECK();
+      }
+      ++restarts;
+      if (breakdown) break;
+    }
+  }
+  // final true residual (scaled) and unscaled per-block residuals
+  k_true_residual<<<B, 256, 0, s>>>(N, c->rowptr, c->col,
+                                    reinterpret_cast<const double4_32a*>(c->bval), c->xs, c->bs,
+                                    c->scales, c->w, c->kparts);
+  TP_LAUNCH_CHECK();
+  k_sum_to<<<1, 256, 0, s>>>(c->kparts, B, c->hn);
+  TP_LAUNCH_CHECK();
+  const double rfin = std::sqrt(read_double(c->hn, hp_host, s));
+  k_unscaled_sums<<<B, 256, 0, s>>>(N, c->rowptr, c->col,
+                                    reinterpret_cast<const double4_32a*>(c->bval), c->xs, bp,
+                                    bT, c->kparts);
+  TP_LAUNCH_CHECK();
+  for (int q = 0; q < 4; ++q) {
+    k_sum_to<<<1, 256, 0, s>>>(c->kparts + (long long)q * B, B, c->est + q);
+    TP_LAUNCH_CHECK();
+  }
+  TP_CUDA_TRY(cudaMemcpyAsync(hp_host, c->est, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(xp, c->xs, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(xT, c->xs + N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  auto t1 = std::chrono::steady_clock::now();
+  const double rp2 = hp_host[0], rT2 = hp_host[1], bp2 = hp_host[2], bT2 = hp_host[3];
+  const double rel = bnorm > 0.0 ? rfin / bnorm : 0.0;
+  if (status != TP_OK && bnorm > 0.0 && rel <= rtol) status = TP_OK;
+  if (breakdown && status != TP_OK) status = TP_BREAKDOWN;
+  if (info) {
+    info->iters = its;
+    info->restarts = restarts;
+    info->status = status;
+    info->rel_res = rel;
+    info->rel_res_unscaled = (bp2 + bT2) > 0 ? std::sqrt((rp2 + rT2) / (bp2 + bT2)) : 0.0;
+    info->rel_res_p = bp2 > 0 ? std::sqrt(rp2 / bp2) : std::sqrt(rp2);
+    info->rel_res_T = bT2 > 0 ? std::sqrt(rT2 / bT2) : std::sqrt(rT2);
+    info->t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->levels_pp = (int)c->hpp->L.size();
+    info->levels_S = (int)c->hS->L.size();
+    info->opc_pp = c->hpp->operator_complexity();
+    info->opc_S = c->hS->operator_complexity();
+  }
+  return status;
+}
+
+}  // namespace tp

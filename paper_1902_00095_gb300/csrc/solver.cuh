@@ -1,0 +1,70 @@
+// Solver context behind the C-ABI (internal header).
+#pragma once
+#include <memory>
+#include "amg.cuh"
+#include "kernels.cuh"
+
+struct tp_ctx {
+  cudaStream_t s = nullptr;
+  int device = 0;
+  int num_sms = 152;
+  tp::GridDev grid{};
+  tp::FluidDev fluid{};
+  int N = 0, nnzb = 0;
+  tp::Pool pool;  // persistent buffers
+  // block pattern (7-point, ascending columns)
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  int* dpos = nullptr;
+  // cell fields
+  double *Kx = nullptr, *Ky = nullptr, *Kz = nullptr, *phi = nullptr, *kTr = nullptr,
+         *kT = nullptr;
+  bool fields_set = false;
+  // wells
+  tp::WellsDev wells;
+  tp::Pool wpool;
+  // state and properties
+  double *p = nullptr, *T = nullptr, *pn = nullptr, *Tn = nullptr;
+  double *rho = nullptr, *lam = nullptr, *lam_p = nullptr, *lam_T = nullptr;
+  // assembled system
+  double* bval = nullptr;  // [4 * nnzb]
+  double* Sval = nullptr;  // [nnzb]
+  double *Rm = nullptr, *Re = nullptr;
+  double *App = nullptr, *ApT = nullptr, *ATp = nullptr, *ATT = nullptr;
+  double* scales = nullptr;  // [2] equation scales s_m, s_e
+  double* ones = nullptr;    // [2] = {1, 1}
+  double* partials = nullptr;
+  int nparts = 0;
+  double* tmpN = nullptr;
+  bool assembled = false;
+  // preconditioner
+  tp_precond_opts opts{};
+  std::unique_ptr<tp::Hierarchy> hpp, hS;
+  double* S_active = nullptr;  // values of the Schur approximation used
+  double *bp_s = nullptr, *bT_s = nullptr;
+  bool built = false;
+  cudaGraphExec_t pc_graph = nullptr;
+  long long pc_graph_kernels = 0;
+  // Krylov workspace
+  tp::Pool kpool;
+  int restart_alloc = 0;
+  double *Vb = nullptr, *Zb = nullptr, *w = nullptr, *xs = nullptr, *bs = nullptr;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
+         *hn = nullptr, *est = nullptr, *kparts = nullptr, *h2 = nullptr;
+  double* host_est = nullptr;  // pinned
+  // user-facing scratch for host pointer marshalling
+  double *io0 = nullptr, *io1 = nullptr, *io2 = nullptr, *io3 = nullptr;
+
+  ~tp_ctx();
+};
+
+namespace tp {
+long long launches_total();
+// block preconditioner (Sec. 3.2) applied to (vp, vT) in the scaled system:
+// z = M^{-1} D^{-1} v with D = diag(scales); result left in hpp->out, hS->out.
+void precond_record(tp_ctx* c, cudaStream_t s);
+void precond_apply(tp_ctx* c, const double* vp, const double* vT, const double* scales,
+                   cudaStream_t s);
+int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, double* xT,
+                 double rtol, int maxit, int restart, tp_solve_info* info);
+}  // namespace tp

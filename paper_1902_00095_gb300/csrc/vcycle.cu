@@ -1,0 +1,264 @@
+// AMG V-cycle kernels (l1-Jacobi smoothing, residual, restriction,
+// prolongation, coarsest dense solve) in FP64 or FP32.
+//
+// CSR rows are processed by groups of LANES consecutive threads (LANES a
+// power of two chosen from the mean row length), reduced with warp shuffles.
+// On the finest level of an FP32 hierarchy the right-hand side is read in
+// FP64 and the final post-smoothing sweep writes the FP64 result directly,
+// so no conversion passes are needed at the preconditioner boundary.
+#include "amg.cuh"
+
+namespace tp {
+
+namespace {
+
+template <int LANES, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, LANES);
+  return v;
+}
+
+// row dot sum_j a_ij x_j for the row owned by this thread group
+template <int LANES, class TV, class TX>
+__device__ __forceinline__ TV row_dot(const int* __restrict__ rp, const int* __restrict__ col,
+                                      const TV* __restrict__ val, const TX* __restrict__ x,
+                                      int row, bool valid, int lane) {
+  TV acc = TV(0);
+  if (valid) {
+    const int e1 = rp[row + 1];
+    for (int e = rp[row] + lane; e < e1; e += LANES) acc += val[e] * (TV)x[col[e]];
+  }
+  return group_sum<LANES>(acc);
+}
+
+// x_out = x_in + dinv (b - A x_in)
+template <int LANES, class TV, class TB, class TO>
+__global__ void __launch_bounds__(256) k_jacobi(int n, const int* __restrict__ rp,
+                                                const int* __restrict__ col,
+                                                const TV* __restrict__ val,
+                                                const TV* __restrict__ dinv,
+                                                const TB* __restrict__ b,
+                                                const TV* __restrict__ xin, TO* __restrict__ xout) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / LANES, lane = t % LANES;
+  const bool valid = row < n;
+  TV ax = row_dot<LANES, TV, TV>(rp, col, val, xin, row, valid, lane);
+  if (valid && lane == 0) xout[row] = (TO)(xin[row] + dinv[row] * ((TV)b[row] - ax));
+}
+
+// x = dinv b (first sweep from a zero guess)
+template <class TV, class TB>
+__global__ void k_jacobi0(int n, const TV* __restrict__ dinv, const TB* __restrict__ b,
+                          TV* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = dinv[i] * (TV)b[i];
+}
+
+// r = b - A x
+template <int LANES, class TV, class TB>
+__global__ void __launch_bounds__(256) k_residual(int n, const int* __restrict__ rp,
+                                                  const int* __restrict__ col,
+                                                  const TV* __restrict__ val,
+                                                  const TB* __restrict__ b,
+                                                  const TV* __restrict__ x, TV* __restrict__ r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / LANES, lane = t % LANES;
+  const bool valid = row < n;
+  TV ax = row_dot<LANES, TV, TV>(rp, col, val, x, row, valid, lane);
+  if (valid && lane == 0) r[row] = (TV)b[row] - ax;
+}
+
+// y = A x (restriction with R)
+template <int LANES, class TV>
+__global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
+                                              const int* __restrict__ col,
+                                              const TV* __restrict__ val,
+                                              const TV* __restrict__ x, TV* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / LANES, lane = t % LANES;
+  const bool valid = row < n;
+  TV ax = row_dot<LANES, TV, TV>(rp, col, val, x, row, valid, lane);
+  if (valid && lane == 0) y[row] = ax;
+}
+
+// x += P e (prolongation)
+template <int LANES, class TV>
+__global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ rp,
+                                                 const int* __restrict__ col,
+                                                 const TV* __restrict__ val,
+                                                 const TV* __restrict__ e, TV* __restrict__ x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / LANES, lane = t % LANES;
+  const bool valid = row < n;
+  TV pe = row_dot<LANES, TV, TV>(rp, col, val, e, row, valid, lane);
+  if (valid && lane == 0) x[row] += pe;
+}
+
+// x = Ainv b on the coarsest level (dense FP64 inverse), one warp per row
+template <class TB, class TO>
+__global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __restrict__ b,
+                         TO* __restrict__ x) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += inv[(long long)row * n + j] * (double)b[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[row] = (TO)acc;
+}
+
+template <class TV, class TB, class TO>
+void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b, const TV* xin,
+            TO* xout, cudaStream_t s) {
+  const long long threads = (long long)A.n * lanes;
+  const int g = grid_for(threads);
+  switch (lanes) {
+#define TP_CASE(L)                                                                          \
+  case L:                                                                                   \
+    k_jacobi<L, TV, TB, TO><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, dinv, b, xin,   \
+                                                 xout);                                     \
+    break;
+    TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
+#undef TP_CASE
+  }
+  TP_LAUNCH_CHECK();
+}
+
+template <class TV, class TB>
+void residual(int lanes, const DevCSR& A, const TV* val, const TB* b, const TV* x, TV* r,
+              cudaStream_t s) {
+  const int g = grid_for((long long)A.n * lanes);
+  switch (lanes) {
+#define TP_CASE(L)                                                                      \
+  case L:                                                                               \
+    k_residual<L, TV, TB><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, b, x, r);     \
+    break;
+    TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
+#undef TP_CASE
+  }
+  TP_LAUNCH_CHECK();
+}
+
+template <class TV>
+void spmv(int lanes, const DevCSR& A, const TV* val, const TV* x, TV* y, cudaStream_t s) {
+  const int g = grid_for((long long)A.n * lanes);
+  switch (lanes) {
+#define TP_CASE(L)                                                              \
+  case L:                                                                       \
+    k_spmv<L, TV><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, x, y);        \
+    break;
+    TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
+#undef TP_CASE
+  }
+  TP_LAUNCH_CHECK();
+}
+
+template <class TV>
+void prolong(int lanes, const DevCSR& P, const TV* val, const TV* e, TV* x, cudaStream_t s) {
+  const int g = grid_for((long long)P.n * lanes);
+  switch (lanes) {
+#define TP_CASE(L)                                                              \
+  case L:                                                                       \
+    k_prolong<L, TV><<<g, kBlock, 0, s>>>(P.n, P.rowptr, P.col, val, e, x);     \
+    break;
+    TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
+#undef TP_CASE
+  }
+  TP_LAUNCH_CHECK();
+}
+
+template <class TB, class TO>
+void coarse(int n, const double* inv, const TB* b, TO* x, cudaStream_t s) {
+  k_coarse<TB, TO><<<grid_for((long long)n * 32), kBlock, 0, s>>>(n, inv, b, x);
+  TP_LAUNCH_CHECK();
+}
+
+template <class TV>
+struct Vals {
+  static const TV* A(const Level& l);
+  static const TV* P(const Level& l);
+  static const TV* R(const Level& l);
+  static const TV* dinv(const Level& l);
+};
+template <>
+struct Vals<double> {
+  static const double* A(const Level& l) { return l.A.val; }
+  static const double* P(const Level& l) { return l.P.val; }
+  static const double* R(const Level& l) { return l.R.val; }
+  static const double* dinv(const Level& l) { return l.dinv; }
+};
+template <>
+struct Vals<float> {
+  static const float* A(const Level& l) { return l.A.valf; }
+  static const float* P(const Level& l) { return l.P.valf; }
+  static const float* R(const Level& l) { return l.R.valf; }
+  static const float* dinv(const Level& l) { return l.dinvf; }
+};
+
+// One V-cycle on level l for right-hand side b (type TB). The result goes to
+// `final_out` (type TO) when non-null, else to one of the level's work
+// vectors, whose address is returned.
+template <class TV, class TB, class TO>
+TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, TO* final_out,
+              int nu_pre, int nu_post, cudaStream_t s) {
+  Level& v = L[l];
+  const int n = v.A.n;
+  TV* x = static_cast<TV*>(v.x);
+  TV* t = static_cast<TV*>(v.t);
+  if (l + 1 == L.size()) {
+    if (final_out) {
+      coarse<TB, TO>(n, cinv, b, final_out, s);
+      return nullptr;
+    }
+    coarse<TB, TV>(n, cinv, b, x, s);
+    return x;
+  }
+  const TV* A = Vals<TV>::A(v);
+  const TV* dinv = Vals<TV>::dinv(v);
+  // pre-smoothing from a zero guess
+  k_jacobi0<TV, TB><<<grid_for(n), kBlock, 0, s>>>(n, dinv, b, x);
+  TP_LAUNCH_CHECK();
+  TV* cur = x;
+  TV* oth = t;
+  for (int k = 1; k < nu_pre; ++k) {
+    jacobi<TV, TB, TV>(v.lanes_A, v.A, A, dinv, b, cur, oth, s);
+    std::swap(cur, oth);
+  }
+  // coarse-grid correction
+  TV* r = static_cast<TV*>(v.r);
+  residual<TV, TB>(v.lanes_A, v.A, A, b, cur, r, s);
+  Level& c = L[l + 1];
+  TV* bc = static_cast<TV*>(c.b);
+  spmv<TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
+  TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, s);
+  prolong<TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
+  // post-smoothing
+  for (int k = 1; k <= nu_post; ++k) {
+    if (k == nu_post && final_out) {
+      jacobi<TV, TB, TO>(v.lanes_A, v.A, A, dinv, b, cur, final_out, s);
+      return nullptr;
+    }
+    jacobi<TV, TB, TV>(v.lanes_A, v.A, A, dinv, b, cur, oth, s);
+    std::swap(cur, oth);
+  }
+  return cur;
+}
+
+}  // namespace
+
+void Hierarchy::vcycle(cudaStream_t s) {
+  if (opts.precision == 1) vcycle_fp32(s);
+  else vcycle_fp64(s);
+}
+
+void Hierarchy::vcycle_fp64(cudaStream_t s) {
+  run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s);
+}
+
+void Hierarchy::vcycle_fp32(cudaStream_t s) {
+  run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s);
+}
+
+}  // namespace tp
