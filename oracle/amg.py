@@ -369,18 +369,26 @@ def galerkin(A, P, R):
 
 # -------------------------------------------------------------------- setup
 def l1_diag(A):
-    """l1-Jacobi scaling d_i = a_ii + sum_{j != i} |a_ij|."""
+    """l1-Jacobi scaling d_i = sign(a_ii) (|a_ii| + sum_{j != i} |a_ij|).
+
+    Galerkin operators of the non-symmetric S~_T can carry a few negative
+    diagonals on coarse levels; taking the row's l1 norm with the sign of
+    its diagonal keeps every sweep a damped Jacobi step for that row (the
+    sign convention hypre uses for l1 norms)."""
     rp, c, v = A
     n = rp.size - 1
     d = np.zeros(n)
     for i in range(n):
-        s = 0.0
+        diag = 0.0
+        off = 0.0
         for e in range(rp[i], rp[i + 1]):
             if c[e] == i:
-                s += v[e]
+                diag = v[e]
             else:
-                s += abs(v[e])
-        d[i] = s
+                off += abs(v[e])
+        d[i] = diag + off if diag >= 0.0 else diag - off
+        if d[i] == 0.0:
+            raise RuntimeError(f"row {i} is empty")
     return d
 
 
