@@ -23,7 +23,11 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# the CPU-baseline / reference legs time the single-threaded oracle
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -45,6 +49,9 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--probe", type=int, default=0,
+                    help="kernel timed for the roofline: 0 finest A_pp sweep, "
+                         "1 finest S~ sweep, 2 block SpMV")
     a = ap.parse_args()
     a.config = int(a.config) if a.config.isdigit() else a.config
     return a
@@ -104,24 +111,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+PROBE_NAMES = {0: "k_jacobi (finest A_pp level, l1-Jacobi sweep)",
+               1: "k_jacobi (finest S~ level, l1-Jacobi sweep)",
+               2: "k_block_spmv (2x2 block-CSR SpMV, FP64)"}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the probed
+# kernel, keyed by (config, probe); None until a capture of the current kernel
+TRAFFIC = {}
+
+
 def cpu_baseline(seconds_target=20.0):
     """The oracle (as it stands) on a bounded sample of the same recipe."""
     from oracle import krylov as okry
-    import threading
     prob = make_problem(CPU_SAMPLE)
     N = prob["nx"] * prob["ny"] * prob["nz"]
     t0 = time.perf_counter()
     out = okry.solve(prob, rtol=1e-8)
     t = time.perf_counter() - t0
-    threads = 1
-    try:
-        threads = max(1, len(os.sched_getaffinity(0))) if os.environ.get("OMP_NUM_THREADS") is None else 1
-    except Exception:
-        pass
     return {"value": 2 * N / t, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
             "sample": f"one assemble+setup+solve of the 64x64x32 recipe at 32x32x16 "
                       f"({2 * N} unknowns, {out['iters']} FGMRES its, {t:.1f} s, single thread)",
-            "threads_visible": threads}
+            "host_cores": os.cpu_count()}
 
 
 def run_reference(args, rank, world):
@@ -177,6 +196,7 @@ def run_ours(args, rank, world, local):
     xp = torch.empty(N, dtype=torch.float64, device=dev)
     xT = torch.empty(N, dtype=torch.float64, device=dev)
     opts = thermo.default_opts(precision=args.precision)
+    s.probe_enable(args.probe)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
     def step():
@@ -196,6 +216,7 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
+    s.probe_read(reset=True)
     l0 = thermo.kernel_launches()
     t0 = time.perf_counter()
     infos = []
@@ -208,9 +229,20 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     launches = thermo.kernel_launches() - l0
+    pr = s.probe_read(reset=True)
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
+    peak, peak_kind = measured_peak()
+    achieved = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else None
+    roofline = {"bound": "hbm", "kernel": PROBE_NAMES[args.probe],
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "traffic": TRAFFIC.get((str(args.config), args.probe, args.precision)),
+                "launches_timed": pr["launches"],
+                "avg_launch_us": pr["ms"] * 1e3 / max(1, pr["launches"]),
+                "algorithmic_bytes_per_launch": pr["bytes"] / max(1, pr["launches"])}
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -265,6 +297,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"replicas{world}"},
         "e2e": e2e,
+        "roofline": roofline,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed": wall,

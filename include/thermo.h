@@ -155,6 +155,20 @@ int tp_solve(tp_ctx* ctx, const double* b_p, const double* b_T,
              double* x_p, double* x_T, double rtol, int maxit, int restart,
              tp_solve_info* info, int ptr_is_device);
 
+/* Timing probe for roofline measurements: CUDA events on the context stream
+ * around every launch of one kernel class during tp_solve, read back after
+ * the per-iteration host synchronisation FGMRES already performs.
+ * which = 0: finest-level l1-Jacobi sweeps of the A_pp hierarchy;
+ *         1: finest-level sweeps of the S~ hierarchy; 2: block SpMV;
+ *        -1: off. Enabling resets the totals and requires a new
+ * tp_build_preconditioner (the events are captured into the graph). */
+int tp_probe_enable(tp_ctx* ctx, int which);
+/* Totals since enabling (or the last reset): summed event time (ms), number
+ * of launches timed, and their summed algorithmic bytes (each matrix entry,
+ * index and vector element counted once). */
+int tp_probe_read(tp_ctx* ctx, double* total_ms, long long* launches,
+                  double* total_bytes, int reset);
+
 /* y = A x with the assembled Jacobian (Eq. AXR), no scaling. [N] each. */
 int tp_spmv(tp_ctx* ctx, const double* x_p, const double* x_T,
             double* y_p, double* y_T, int ptr_is_device);

@@ -25,6 +25,25 @@ struct AmgOpts {
   int max_pmis_rounds = 64;
 };
 
+// CUDA-event timing of one kernel class inside the timed region: events are
+// recorded around each launch (as external event nodes when captured into a
+// graph) and read back after the host syncs the solver already does.
+struct Probe {
+  static constexpr int kMaxPairs = 64;
+  cudaEvent_t ev[2 * kMaxPairs] = {};
+  double bytes[kMaxPairs] = {};
+  int npairs = 0;
+  bool created = false;
+  // accumulated over reads
+  double total_ms = 0.0, total_bytes = 0.0;
+  long long launches = 0;
+  void create();
+  void destroy();
+  void before(cudaStream_t s);
+  void after(cudaStream_t s, double algorithmic_bytes);
+  void read_and_accumulate();   // after a stream sync
+};
+
 struct Level {
   DevCSR A;
   int* dpos = nullptr;
@@ -59,6 +78,7 @@ class Hierarchy {
   double operator_complexity() const;
 
   AmgOpts opts;
+  Probe* probe = nullptr;  // times the finest-level smoothing sweeps when set
   std::vector<Level> L;
   int n0 = 0;
   double* in = nullptr;    // [n0] FP64 right-hand side

@@ -463,14 +463,20 @@ __global__ void k_spgemm_compact(int n, const int* __restrict__ off,
 }
 
 // ------------------------------------------------------------ smoother scaling
+// l1-Jacobi scaling d_i = sign(a_ii) (|a_ii| + sum_{j != i} |a_ij|): coarse
+// Galerkin operators of the advective S~_T can have a few negative diagonals
 __global__ void k_l1_dinv(int n, const int* __restrict__ rp, const int* __restrict__ col,
                           const double* __restrict__ val, double* __restrict__ dinv,
                           float* __restrict__ dinvf, int* __restrict__ err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) s += (col[e] == i) ? val[e] : fabs(val[e]);
-  if (!(s > 0.0)) {
+  double diag = 0.0, off = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    if (col[e] == i) diag = val[e];
+    else off += fabs(val[e]);
+  }
+  double s = diag >= 0.0 ? diag + off : diag - off;
+  if (s == 0.0 || !isfinite(s)) {
     atomicOr(err, 4);
     s = 1.0;
   }
@@ -785,7 +791,7 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
     v.lanes_P = v.P.nnz ? pick_lanes(v.P) : 1;
     v.lanes_R = v.R.nnz ? pick_lanes(v.R) : 1;
   }
-  if (read_int(err, s) & 4) fail(TP_SETUP_FAILED, "AMG: non-positive l1 row norm");
+  if (read_int(err, s) & 4) fail(TP_SETUP_FAILED, "AMG: empty or non-finite row");
   // coarsest level: explicit inverse by Gauss-Jordan with partial pivoting
   Level& cl = L.back();
   nc = cl.A.n;

@@ -105,6 +105,7 @@ void check_opts(const tp_precond_opts& o) {
 
 tp_ctx::~tp_ctx() {
   if (pc_graph) cudaGraphExecDestroy(pc_graph);
+  probe.destroy();
   hpp.reset();
   hS.reset();
   if (host_est) cudaFreeHost(host_est);
@@ -416,6 +417,8 @@ int tp_build_preconditioner(tp_ctx* c, const tp_precond_opts* opts) {
   tp::AmgOpts ao = amg_opts(o);
   c->hpp->setup(App, ao, s);
   c->hS->setup(S, ao, s);
+  c->hpp->probe = c->probe_which == 0 ? &c->probe : nullptr;
+  c->hS->probe = c->probe_which == 1 ? &c->probe : nullptr;
   if (o.use_graphs) {
     cudaGraph_t graph = nullptr;
     TP_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -476,6 +479,34 @@ int tp_solve(tp_ctx* c, const double* b_p, const double* b_T, double* x_p, doubl
   TP_CUDA_TRY(cudaStreamSynchronize(s));
   return st;
   TP_API_END
+}
+
+int tp_probe_enable(tp_ctx* c, int which) {
+  if (!c || which < -1 || which > 2) return TP_EINVAL;
+  TP_API_BEGIN
+  if (which >= 0) c->probe.create();
+  c->probe_which = which;
+  c->probe.npairs = 0;
+  c->probe.total_ms = 0.0;
+  c->probe.total_bytes = 0.0;
+  c->probe.launches = 0;
+  c->built = false;  // the preconditioner graph must be recaptured
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_probe_read(tp_ctx* c, double* total_ms, long long* launches, double* total_bytes,
+                  int reset) {
+  if (!c) return TP_EINVAL;
+  if (total_ms) *total_ms = c->probe.total_ms;
+  if (launches) *launches = c->probe.launches;
+  if (total_bytes) *total_bytes = c->probe.total_bytes;
+  if (reset) {
+    c->probe.total_ms = 0.0;
+    c->probe.total_bytes = 0.0;
+    c->probe.launches = 0;
+  }
+  return TP_OK;
 }
 
 int tp_spmv(tp_ctx* c, const double* x_p, const double* x_T, double* y_p, double* y_T,

@@ -357,6 +357,7 @@ void launch_block_spmv(int N, const int* rowptr, const int* col, const double* b
 }
 
 void precond_record(tp_ctx* c, cudaStream_t s) {
+  c->probe.npairs = 0;
   Hierarchy& hp = *c->hpp;
   Hierarchy& hs = *c->hS;
   const int N = c->N;
@@ -446,10 +447,17 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
         double* vj = c->Vb + (long long)j * n2;
         double* zj = c->Zb + (long long)j * n2;
         precond_apply(c, vj, vj + N, c->scales, s);
+        const bool probe_spmv = c->probe_which == 2;
+        if (probe_spmv) {
+          c->probe.npairs = 0;
+          c->probe.before(s);
+        }
         k_block_spmv<<<grid_for(N), kBlock, 0, s>>>(
             N, c->rowptr, c->col, reinterpret_cast<const double4_32a*>(c->bval), c->hpp->out,
             c->hS->out, zj, zj + N, c->w, c->w + N, c->scales);
         TP_LAUNCH_CHECK();
+        if (probe_spmv)
+          c->probe.after(s, 36.0 * c->nnzb + 4.0 * (N + 1) + 48.0 * N);
         // CGS2 against V_0..V_j
         double* h1 = c->h2;
         double* h2 = c->h2 + (restart + 2);
@@ -465,6 +473,7 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
         TP_LAUNCH_CHECK();
         TP_CUDA_TRY(cudaMemcpyAsync(hp_host, c->est, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         TP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (c->probe_which >= 0) c->probe.read_and_accumulate();
         const double est = hp_host[0], hnv = hp_host[1], den = hp_host[2];
         ++its;
         m = j + 1;

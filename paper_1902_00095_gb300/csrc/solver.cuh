@@ -45,6 +45,9 @@ struct tp_ctx {
   bool built = false;
   cudaGraphExec_t pc_graph = nullptr;
   long long pc_graph_kernels = 0;
+  // timing probe: -1 off, 0 finest A_pp sweeps, 1 finest S~ sweeps, 2 block SpMV
+  int probe_which = -1;
+  tp::Probe probe;
   // Krylov workspace
   tp::Pool kpool;
   int restart_alloc = 0;

@@ -200,9 +200,24 @@ struct Vals<float> {
 // One V-cycle on level l for right-hand side b (type TB). The result goes to
 // `final_out` (type TO) when non-null, else to one of the level's work
 // vectors, whose address is returned.
+// algorithmic bytes of one sweep x_out = x_in + dinv (b - A x_in)
+template <class TV, class TB, class TO>
+double sweep_bytes(const DevCSR& A) {
+  return (double)A.nnz * (sizeof(TV) + sizeof(int)) + 4.0 * (A.n + 1) +
+         (double)A.n * (2 * sizeof(TV) + sizeof(TB) + sizeof(TO));
+}
+
+template <class TV, class TB, class TO>
+void jacobi_probed(Probe* pr, int lanes, const DevCSR& A, const TV* val, const TV* dinv,
+                   const TB* b, const TV* xin, TO* xout, cudaStream_t s) {
+  if (pr) pr->before(s);
+  jacobi<TV, TB, TO>(lanes, A, val, dinv, b, xin, xout, s);
+  if (pr) pr->after(s, sweep_bytes<TV, TB, TO>(A));
+}
+
 template <class TV, class TB, class TO>
 TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, TO* final_out,
-              int nu_pre, int nu_post, cudaStream_t s) {
+              int nu_pre, int nu_post, cudaStream_t s, Probe* probe = nullptr) {
   Level& v = L[l];
   const int n = v.A.n;
   TV* x = static_cast<TV*>(v.x);
@@ -222,8 +237,9 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   TP_LAUNCH_CHECK();
   TV* cur = x;
   TV* oth = t;
+  Probe* pr = (l == 0) ? probe : nullptr;
   for (int k = 1; k < nu_pre; ++k) {
-    jacobi<TV, TB, TV>(v.lanes_A, v.A, A, dinv, b, cur, oth, s);
+    jacobi_probed<TV, TB, TV>(pr, v.lanes_A, v.A, A, dinv, b, cur, oth, s);
     std::swap(cur, oth);
   }
   // coarse-grid correction
@@ -237,10 +253,10 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   // post-smoothing
   for (int k = 1; k <= nu_post; ++k) {
     if (k == nu_post && final_out) {
-      jacobi<TV, TB, TO>(v.lanes_A, v.A, A, dinv, b, cur, final_out, s);
+      jacobi_probed<TV, TB, TO>(pr, v.lanes_A, v.A, A, dinv, b, cur, final_out, s);
       return nullptr;
     }
-    jacobi<TV, TB, TV>(v.lanes_A, v.A, A, dinv, b, cur, oth, s);
+    jacobi_probed<TV, TB, TV>(pr, v.lanes_A, v.A, A, dinv, b, cur, oth, s);
     std::swap(cur, oth);
   }
   return cur;
@@ -254,11 +270,50 @@ void Hierarchy::vcycle(cudaStream_t s) {
 }
 
 void Hierarchy::vcycle_fp64(cudaStream_t s) {
-  run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s);
+  run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s,
+                                    probe);
 }
 
 void Hierarchy::vcycle_fp32(cudaStream_t s) {
-  run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s);
+  run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s,
+                                   probe);
+}
+
+// ------------------------------------------------------------------ probe
+void Probe::create() {
+  if (created) return;
+  for (int k = 0; k < 2 * kMaxPairs; ++k) TP_CUDA_TRY(cudaEventCreate(&ev[k]));
+  created = true;
+}
+
+void Probe::destroy() {
+  if (!created) return;
+  for (int k = 0; k < 2 * kMaxPairs; ++k) cudaEventDestroy(ev[k]);
+  created = false;
+}
+
+void Probe::before(cudaStream_t s) {
+  if (npairs >= kMaxPairs) return;
+  if (g_capturing) TP_CUDA_TRY(cudaEventRecordWithFlags(ev[2 * npairs], s, cudaEventRecordExternal));
+  else TP_CUDA_TRY(cudaEventRecord(ev[2 * npairs], s));
+}
+
+void Probe::after(cudaStream_t s, double algorithmic_bytes) {
+  if (npairs >= kMaxPairs) return;
+  if (g_capturing) TP_CUDA_TRY(cudaEventRecordWithFlags(ev[2 * npairs + 1], s, cudaEventRecordExternal));
+  else TP_CUDA_TRY(cudaEventRecord(ev[2 * npairs + 1], s));
+  bytes[npairs] = algorithmic_bytes;
+  ++npairs;
+}
+
+void Probe::read_and_accumulate() {
+  for (int k = 0; k < npairs; ++k) {
+    float ms = 0.f;
+    TP_CUDA_TRY(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+    total_ms += ms;
+    total_bytes += bytes[k];
+    ++launches;
+  }
 }
 
 }  // namespace tp

@@ -71,6 +71,8 @@ SIGNATURES = {
     "tp_solve": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double, C.c_int, C.c_int,
                                                              C.POINTER(SolveInfo), C.c_int]),
     "tp_spmv": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
+    "tp_probe_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "tp_probe_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_longlong), _dp, C.c_int]),
     "tp_apply_preconditioner": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
     "tp_export_system": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp, _dp]),
     "tp_hierarchy_info": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, _ip, C.c_int]),
@@ -251,6 +253,18 @@ class Solver:
                                 int(restart), C.byref(info), d)
         _check(st, "tp_solve", warn_ok=True)
         return keep[2], keep[3], info.as_dict()
+
+    def probe_enable(self, which):
+        """Time every launch of one kernel class (0 finest A_pp sweeps,
+        1 finest S~ sweeps, 2 block SpMV, -1 off) during solves; call
+        before build()."""
+        _check(self._lib.tp_probe_enable(self._h, int(which)), "tp_probe_enable")
+
+    def probe_read(self, reset=False):
+        ms, n, by = C.c_double(), C.c_longlong(), C.c_double()
+        _check(self._lib.tp_probe_read(self._h, C.byref(ms), C.byref(n), C.byref(by), int(reset)),
+               "tp_probe_read")
+        return dict(ms=ms.value, launches=n.value, bytes=by.value)
 
     def spmv(self, x_p, x_T):
         y = (np.empty(self.N), np.empty(self.N)) if not _is_torch(x_p) else None

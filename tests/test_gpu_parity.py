@@ -248,8 +248,13 @@ def test_degenerate_single_cell_and_single_level():
     s.build()
     assert len(s.hierarchy_info(0)[0]) == 1
     xp, xT, info = s.solve(rtol=1e-10)
-    rp, rT = okry.direct_solution(osys, obp, obT)
-    assert np.allclose(xp, rp, rtol=1e-8) and np.allclose(xT, rT, rtol=1e-8)
+    assert info["status"] == 0 and info["iters"] <= 2
+    # the single-cell 2x2 system has condition number ~1e13 in SI units, so
+    # the check is against the oracle running the same method, and the
+    # residual of the oracle's own matrix
+    o = okry.solve(prob, rtol=1e-10)
+    assert np.allclose(xp, o["x"][:1], rtol=1e-12) and np.allclose(xT, o["x"][1:], rtol=1e-9)
+    assert _oracle_scaled_residual(osys, obp, obT, xp, xT) <= 1e-10
 
 
 def test_errors_are_status_codes_not_faults():
