@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--config", default="2")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", type=int, default=0,
@@ -203,7 +204,7 @@ def run_ours(args, rank, world, local):
         s.set_fields(*fields)
         s.assemble(*state, prob["dt"], R_m=Rm, R_e=Re)
         s.build(opts)
-        return s.solve(rtol=args.rtol, maxit=1000, out=(xp, xT))[2]
+        return s.solve(rtol=args.rtol, maxit=args.maxit, out=(xp, xT))[2]
 
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -263,7 +264,7 @@ def run_ours(args, rank, world, local):
             s.set_fields(*hf)
             s.assemble(*hs, prob["dt"])
             s.build(opts)
-            return s.solve(rtol=args.rtol, maxit=1000, out=hx)[2]
+            return s.solve(rtol=args.rtol, maxit=args.maxit, out=hx)[2]
 
         step_host()
         if world > 1:

@@ -87,12 +87,17 @@ typedef struct {
   int precision;    /* 0: FP64 hierarchy; 1: FP32 hierarchy values, smoothers */
                     /*    and V-cycles inside FP64 FGMRES (coarsest LU FP64)  */
   int interp;       /* 0: classical (Ruge-Stueben, modified); 1: extended+i   */
+                    /*    (default 1 for A_pp; S~ uses interp_S, default 0)  */
   int smoother;     /* 0: l1-Jacobi; 1: Chebyshev on D^-1 A                   */
   int nu_pre, nu_post, cheb_degree;
   double theta;     /* strength threshold                                     */
   int max_levels, coarse_size;
   unsigned long long seed;  /* PMIS tie-break seed                            */
   int use_graphs;   /* 1: replay each V-cycle / preconditioner as a CUDA graph */
+  /* overrides for the Schur hierarchy (-1 or 0: same as above) */
+  int interp_S;     /* -1 same, 0 classical (default), 1 extended+i           */
+  int max_levels_S; /* 0 same                                                 */
+  int nu_S;         /* 0 same; else nu_pre = nu_post = nu_S                   */
 } tp_precond_opts;
 
 typedef struct {
@@ -168,6 +173,32 @@ int tp_probe_enable(tp_ctx* ctx, int which);
  * index and vector element counted once). */
 int tp_probe_read(tp_ctx* ctx, double* total_ms, long long* launches,
                   double* total_bytes, int reset);
+
+/* Newton iteration of one backward-Euler step (Sec. 3 linearisation,
+ * Sec. 4 stopping rules): starting from x = (p_n, T_n), repeat assemble /
+ * precondition / FGMRES / x += dx until ||D G(x_k)|| <= tol_f ||D G(x_0)||
+ * (D the equation scaling of the first linearisation) or ||dx|| <= tol_dx
+ * ||x||, at most max_newton linear solves. reuse = 1 keeps the AMG structure
+ * of the first iteration and refreshes only the Galerkin values (and keeps
+ * the captured graph). Full Newton steps (no line search). The new state is
+ * written to p_out, T_out ([N] each). Returns TP_OK or TP_NOT_CONVERGED. */
+typedef struct {
+  int max_newton;
+  double tol_f, tol_dx;
+  double rtol;      /* FGMRES relative tolerance per linear solve */
+  int maxit, restart;
+  int reuse;
+} tp_newton_opts;
+
+typedef struct {
+  int newton_iters, linear_iters, status, last_linear_status;
+  double rel_f, rel_dx, t_ms;
+} tp_newton_info;
+
+int tp_newton_step(tp_ctx* ctx, const double* p_n, const double* T_n, double dt,
+                   double* p_out, double* T_out, const tp_precond_opts* popts,
+                   const tp_newton_opts* nopts, tp_newton_info* info,
+                   int ptr_is_device);
 
 /* y = A x with the assembled Jacobian (Eq. AXR), no scaling. [N] each. */
 int tp_spmv(tp_ctx* ctx, const double* x_p, const double* x_T,

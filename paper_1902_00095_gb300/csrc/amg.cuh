@@ -52,6 +52,7 @@ struct Level {
   signed char* cf = nullptr;
   int pmis_rounds = 0;
   DevCSR P, R;       // P: n x nc, R: nc x n
+  DevCSR AP;         // A P (kept for numeric-only refreshes)
   double* dinv = nullptr;   // smoother scaling (l1 or plain diagonal), FP64
   float* dinvf = nullptr;
   double cheb_lo = 0.0, cheb_hi = 0.0;
@@ -73,6 +74,12 @@ class Hierarchy {
   // Build from a CSR matrix whose arrays stay owned by the caller and must
   // outlive the hierarchy (level 0 borrows them).
   void setup(const DevCSR& A0, const AmgOpts& opts, cudaStream_t s);
+  // Numeric-only refresh after the level-0 values changed in place: keeps
+  // the C/F splits, P, R and every pattern; recomputes A P and R (A P) in the
+  // setup's canonical order, the smoother scaling, the FP32 copies and the
+  // coarsest inverse. Buffers keep their addresses (captured graphs stay
+  // valid).
+  void refresh(cudaStream_t s);
   // One V-cycle: out = V(in). in/out are the hierarchy's own FP64 buffers.
   void vcycle(cudaStream_t s);
   double operator_complexity() const;
@@ -86,8 +93,11 @@ class Hierarchy {
   double* coarse_inv = nullptr;   // [nc*nc] row-major inverse of the coarsest A
   int nc = 0;
   Pool pool;
+  double* coarse_dense = nullptr;   // [nc*nc] work for the inverse
+  int* err = nullptr;
 
  private:
+  void finish_levels(cudaStream_t s, bool allocate);
   void vcycle_fp64(cudaStream_t s);
   void vcycle_fp32(cudaStream_t s);
 };

@@ -449,6 +449,26 @@ __global__ void k_spgemm_rows(int n, const int* __restrict__ Arp, const int* __r
   cnt[i] = u;
 }
 
+// numeric-only C = A B on a known pattern (same canonical order)
+__global__ void k_spgemm_numeric(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
+                                 const double* __restrict__ Aval, const int* __restrict__ Brp,
+                                 const int* __restrict__ Bcol, const double* __restrict__ Bval,
+                                 const int* __restrict__ Crp, const int* __restrict__ Ccol,
+                                 double* __restrict__ Cval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c0 = Crp[i], c1 = Crp[i + 1];
+  for (int q = c0; q < c1; ++q) Cval[q] = 0.0;
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
+    const int k = Acol[e];
+    const double a = Aval[e];
+    for (int f = Brp[k]; f < Brp[k + 1]; ++f) {
+      const int q = find_in(Ccol, c0, c1, Bcol[f]);
+      Cval[q] = __dadd_rn(Cval[q], __dmul_rn(a, Bval[f]));
+    }
+  }
+}
+
 __global__ void k_spgemm_compact(int n, const int* __restrict__ off,
                                  const int* __restrict__ ccol, const double* __restrict__ cval,
                                  const int* __restrict__ Crp, int* __restrict__ Ccol,
@@ -664,7 +684,7 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
   L.clear();
   coarse_inv = nullptr;
   Pool scratch;
-  int* err = pool.alloc<int>(1);
+  err = pool.alloc<int>(1);
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   L.emplace_back();
   L[0].A = A0;
@@ -753,60 +773,94 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
     }
     cur.P = P;
     cur.R = transpose(P, pool, scratch, s);
-    DevCSR AP = spgemm(A, P, scratch, scratch, s);
-    DevCSR Ac = spgemm(cur.R, AP, pool, scratch, s);
+    cur.AP = spgemm(A, P, pool, scratch, s);
+    DevCSR Ac = spgemm(cur.R, cur.AP, pool, scratch, s);
     TP_CUDA_TRY(cudaStreamSynchronize(s));
     scratch.release();
     L.emplace_back();
     L.back().A = Ac;
   }
-  // smoother scaling, FP32 copies, work vectors
+  finish_levels(s, true);
+}
+
+// smoother scaling, FP32 copies, work vectors (allocate = first setup) and
+// the coarsest-level inverse
+void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
   const bool f32 = opts.precision == 1;
+  TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   for (size_t l = 0; l < L.size(); ++l) {
     Level& v = L[l];
     const int n = v.A.n;
-    v.dinv = pool.alloc<double>(n);
-    v.dinvf = f32 ? pool.alloc<float>(n) : nullptr;
+    if (allocate) {
+      v.dinv = pool.alloc<double>(n);
+      v.dinvf = f32 ? pool.alloc<float>(n) : nullptr;
+    }
     k_l1_dinv<<<grid_for(n), kBlock, 0, s>>>(n, v.A.rowptr, v.A.col, v.A.val, v.dinv, v.dinvf,
                                              err);
     TP_LAUNCH_CHECK();
     if (f32) {
-      v.A.valf = pool.alloc<float>(v.A.nnz);
+      if (allocate) v.A.valf = pool.alloc<float>(v.A.nnz);
       k_to_float<<<grid_for(v.A.nnz), kBlock, 0, s>>>(v.A.nnz, v.A.val, v.A.valf);
       TP_LAUNCH_CHECK();
       if (v.P.nnz) {
-        v.P.valf = pool.alloc<float>(v.P.nnz);
+        if (allocate) {
+          v.P.valf = pool.alloc<float>(v.P.nnz);
+          v.R.valf = pool.alloc<float>(v.R.nnz);
+        }
         k_to_float<<<grid_for(v.P.nnz), kBlock, 0, s>>>(v.P.nnz, v.P.val, v.P.valf);
-        v.R.valf = pool.alloc<float>(v.R.nnz);
         k_to_float<<<grid_for(v.R.nnz), kBlock, 0, s>>>(v.R.nnz, v.R.val, v.R.valf);
         TP_LAUNCH_CHECK();
       }
     }
-    const size_t es = f32 ? sizeof(float) : sizeof(double);
-    v.b = pool.alloc<char>(es * (n + 1));
-    v.x = pool.alloc<char>(es * (n + 1));
-    v.t = pool.alloc<char>(es * (n + 1));
-    v.r = pool.alloc<char>(es * (n + 1));
-    v.lanes_A = pick_lanes(v.A);
-    v.lanes_P = v.P.nnz ? pick_lanes(v.P) : 1;
-    v.lanes_R = v.R.nnz ? pick_lanes(v.R) : 1;
+    if (allocate) {
+      const size_t es = f32 ? sizeof(float) : sizeof(double);
+      v.b = pool.alloc<char>(es * (n + 1));
+      v.x = pool.alloc<char>(es * (n + 1));
+      v.t = pool.alloc<char>(es * (n + 1));
+      v.r = pool.alloc<char>(es * (n + 1));
+      v.lanes_A = pick_lanes(v.A);
+      v.lanes_P = v.P.nnz ? pick_lanes(v.P) : 1;
+      v.lanes_R = v.R.nnz ? pick_lanes(v.R) : 1;
+    }
   }
   if (read_int(err, s) & 4) fail(TP_SETUP_FAILED, "AMG: empty or non-finite row");
   // coarsest level: explicit inverse by Gauss-Jordan with partial pivoting
   Level& cl = L.back();
-  nc = cl.A.n;
-  if (nc > opts.max_coarse_dense) fail(TP_SETUP_FAILED, "AMG: coarsest level too large");
-  double* D = scratch.alloc<double>((size_t)nc * nc);
-  coarse_inv = pool.alloc<double>((size_t)nc * nc);
-  k_to_dense<<<grid_for(nc), kBlock, 0, s>>>(nc, cl.A.rowptr, cl.A.col, cl.A.val, D);
+  if (allocate) {
+    nc = cl.A.n;
+    if (nc > opts.max_coarse_dense) fail(TP_SETUP_FAILED, "AMG: coarsest level too large");
+    coarse_dense = pool.alloc<double>((size_t)nc * nc);
+    coarse_inv = pool.alloc<double>((size_t)nc * nc);
+  }
+  k_to_dense<<<grid_for(nc), kBlock, 0, s>>>(nc, cl.A.rowptr, cl.A.col, cl.A.val, coarse_dense);
   TP_LAUNCH_CHECK();
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  k_gauss_jordan<<<1, 1024, 0, s>>>(nc, D, coarse_inv, err);
+  k_gauss_jordan<<<1, 1024, 0, s>>>(nc, coarse_dense, coarse_inv, err);
   TP_LAUNCH_CHECK();
   if (read_int(err, s) != 0) fail(TP_SETUP_FAILED, "AMG: singular coarsest operator");
-  in = pool.alloc<double>(n0 + 1);
-  out = pool.alloc<double>(n0 + 1);
+  if (allocate) {
+    in = pool.alloc<double>(n0 + 1);
+    out = pool.alloc<double>(n0 + 1);
+  }
   TP_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+void Hierarchy::refresh(cudaStream_t s) {
+  if (L.empty()) fail(TP_ESTATE, "AMG: refresh before setup");
+  for (size_t l = 0; l + 1 < L.size(); ++l) {
+    Level& v = L[l];
+    const int n = v.A.n;
+    k_spgemm_numeric<<<grid_for(n, 128), 128, 0, s>>>(n, v.A.rowptr, v.A.col, v.A.val,
+                                                      v.P.rowptr, v.P.col, v.P.val, v.AP.rowptr,
+                                                      v.AP.col, v.AP.val);
+    TP_LAUNCH_CHECK();
+    Level& c = L[l + 1];
+    k_spgemm_numeric<<<grid_for(c.A.n, 128), 128, 0, s>>>(c.A.n, v.R.rowptr, v.R.col, v.R.val,
+                                                          v.AP.rowptr, v.AP.col, v.AP.val,
+                                                          c.A.rowptr, c.A.col, c.A.val);
+    TP_LAUNCH_CHECK();
+  }
+  finish_levels(s, false);
 }
 
 }  // namespace tp

@@ -99,6 +99,8 @@ void check_opts(const tp_precond_opts& o) {
     fail(TP_EINVAL, "nu_pre and nu_post must be in 1..8");
   if (!(o.theta > 0.0 && o.theta < 1.0)) fail(TP_EINVAL, "theta must be in (0, 1)");
   if (o.max_levels < 1 || o.coarse_size < 1) fail(TP_EINVAL, "max_levels, coarse_size >= 1");
+  if (o.interp_S < -1 || o.interp_S > 1 || o.max_levels_S < 0 || o.nu_S < 0 || o.nu_S > 8)
+    fail(TP_EINVAL, "bad Schur-hierarchy override");
 }
 
 }  // namespace
@@ -149,6 +151,9 @@ void tp_default_opts(tp_precond_opts* o) {
   o->coarse_size = 64;
   o->seed = 0;
   o->use_graphs = 1;
+  o->interp_S = 0;
+  o->max_levels_S = 0;
+  o->nu_S = 0;
 }
 
 const char* tp_status_string(int st) {
@@ -217,6 +222,7 @@ int tp_create(tp_ctx** out, const tp_grid* grid, const tp_fluid* fluid, void* cu
   c->ATT = P.alloc<double>(nnzb);
   c->scales = P.alloc<double>(2);
   c->ones = P.alloc<double>(2);
+  c->fscale = P.alloc<double>(2);
   const double one2[2] = {1.0, 1.0};
   TP_CUDA_TRY(cudaMemcpyAsync(c->ones, one2, sizeof(one2), cudaMemcpyHostToDevice, s));
   c->nparts = std::max(1, std::min(2 * c->num_sms, (n + 255) / 256));
@@ -366,26 +372,11 @@ int tp_assemble(tp_ctx* c, const double* p_k, const double* T_k, const double* p
   to_device(c->T, T_k, n, ptr_is_device, s);
   to_device(c->pn, p_n, n, ptr_is_device, s);
   to_device(c->Tn, T_n, n, ptr_is_device, s);
-  int* flags = reinterpret_cast<int*>(c->partials);
-  TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
-  for (const double* a : {c->p, c->T, c->pn, c->Tn}) {
-    k_check_finite<<<tp::grid_for(n), tp::kBlock, 0, s>>>(n, a, flags);
-    TP_LAUNCH_CHECK();
-  }
-  if (read_flags(flags, s)) return TP_ENONFINITE;
-  tp::launch_cell_props(c->N, c->p, c->T, c->fluid, c->rho, c->lam, c->lam_p, c->lam_T, s);
-  tp::launch_assemble(c->grid, c->fluid, c->rowptr, c->dpos, c->Kx, c->Ky, c->Kz, c->phi, c->kT,
-                      c->p, c->T, c->pn, c->Tn, c->rho, c->lam, c->lam_p, c->lam_T, dt, c->bval,
-                      c->Sval, c->Rm, c->Re, s);
-  tp::launch_wells(c->grid, c->fluid, c->wells, c->dpos, c->Kx, c->Ky, c->p, c->T, c->rho,
-                   c->lam, c->lam_p, c->lam_T, c->bval, c->Sval, c->Rm, c->Re, s);
-  TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
-  k_check_finite<<<tp::grid_for(4ll * c->nnzb), tp::kBlock, 0, s>>>(4ll * c->nnzb, c->bval, flags);
-  TP_LAUNCH_CHECK();
+  int st = tp::assemble_device(c, dt);
+  if (st != TP_OK) return st;
   if (R_m) from_device(R_m, c->Rm, n, ptr_is_device, s);
   if (R_e) from_device(R_e, c->Re, n, ptr_is_device, s);
-  if (read_flags(flags, s)) return TP_ENONFINITE;
-  c->assembled = true;
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
   c->built = false;
   return TP_OK;
   TP_API_END
@@ -399,53 +390,36 @@ int tp_build_preconditioner(tp_ctx* c, const tp_precond_opts* opts) {
   if (opts) o = *opts;
   else tp_default_opts(&o);
   check_opts(o);
-  cudaStream_t s = c->s;
-  if (c->pc_graph) {
-    cudaGraphExecDestroy(c->pc_graph);
-    c->pc_graph = nullptr;
-  }
-  c->built = false;
-  tp::launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
-  tp::launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
-                             c->scales, s);
-  c->S_active = (o.schur == 2) ? c->ATT : c->Sval;
-  tp::DevCSR App{c->N, c->N, c->nnzb, c->rowptr, c->col, c->App, nullptr};
-  tp::DevCSR S{c->N, c->N, c->nnzb, c->rowptr, c->col, c->S_active, nullptr};
-  c->opts = o;
-  c->hpp.reset(new tp::Hierarchy());
-  c->hS.reset(new tp::Hierarchy());
-  tp::AmgOpts ao = amg_opts(o);
-  c->hpp->setup(App, ao, s);
-  c->hS->setup(S, ao, s);
-  c->hpp->probe = c->probe_which == 0 ? &c->probe : nullptr;
-  c->hS->probe = c->probe_which == 1 ? &c->probe : nullptr;
-  if (o.use_graphs) {
-    cudaGraph_t graph = nullptr;
-    TP_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    tp::g_capturing = true;
-    try {
-      tp::precond_record(c, s);
-    } catch (...) {
-      tp::g_capturing = false;
-      cudaStreamEndCapture(s, &graph);
-      if (graph) cudaGraphDestroy(graph);
-      throw;
-    }
-    tp::g_capturing = false;
-    TP_CUDA_TRY(cudaStreamEndCapture(s, &graph));
-    size_t nodes = 0;
-    TP_CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nodes));
-    c->pc_graph_kernels = (long long)nodes;
-    cudaError_t e = cudaGraphInstantiate(&c->pc_graph, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      c->pc_graph = nullptr;
-      fail(TP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    }
-  }
-  TP_CUDA_TRY(cudaStreamSynchronize(s));
-  c->built = true;
+  tp::build_device(c, o);
   return TP_OK;
+  TP_API_END
+}
+
+int tp_newton_step(tp_ctx* c, const double* p_n, const double* T_n, double dt, double* p_out,
+                   double* T_out, const tp_precond_opts* popts, const tp_newton_opts* nopts,
+                   tp_newton_info* info, int ptr_is_device) {
+  if (!c || !p_n || !T_n || !p_out || !T_out || !nopts) return TP_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return TP_EINVAL;
+  if (nopts->max_newton < 1 || nopts->maxit < 1 || nopts->restart < 1 || nopts->restart > 200 ||
+      !(nopts->rtol > 0.0))
+    return TP_EINVAL;
+  if (!c->fields_set) return TP_ESTATE;
+  TP_API_BEGIN
+  tp_precond_opts o;
+  if (popts) o = *popts;
+  else tp_default_opts(&o);
+  check_opts(o);
+  cudaStream_t s = c->s;
+  const size_t n = c->N;
+  to_device(c->pn, p_n, n, ptr_is_device, s);
+  to_device(c->Tn, T_n, n, ptr_is_device, s);
+  TP_CUDA_TRY(cudaMemcpyAsync(c->p, c->pn, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(c->T, c->Tn, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int st = tp::newton_step(c, dt, o, *nopts, info);
+  from_device(p_out, c->p, n, ptr_is_device, s);
+  from_device(T_out, c->T, n, ptr_is_device, s);
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
   TP_API_END
 }
 
@@ -466,10 +440,7 @@ int tp_solve(tp_ctx* c, const double* b_p, const double* b_T, double* x_p, doubl
     to_device(c->io1, b_T, n, ptr_is_device, s);
   } else {
     // b = -R
-    TP_CUDA_TRY(cudaMemcpyAsync(c->io0, c->Rm, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    TP_CUDA_TRY(cudaMemcpyAsync(c->io1, c->Re, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    negate(c->io0, n, s);
-    negate(c->io1, n, s);
+    tp::negated_residual(c);
   }
   bp = c->io0;
   bT = c->io1;
@@ -720,3 +691,102 @@ int tp_amg_export_level(tp_amg* a, int level, int* rowptr, int* col, double* val
 
 }  // extern "C"
 
+
+// ------------------------------------------------------------ device steps
+namespace tp {
+
+int assemble_device(tp_ctx* c, double dt) {
+  cudaStream_t s = c->s;
+  const long long n = c->N;
+  int* flags = reinterpret_cast<int*>(c->partials);
+  TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  for (const double* a : {c->p, c->T, c->pn, c->Tn}) {
+    k_check_finite<<<grid_for(n), kBlock, 0, s>>>(n, a, flags);
+    TP_LAUNCH_CHECK();
+  }
+  if (read_flags(flags, s)) return TP_ENONFINITE;
+  launch_cell_props(c->N, c->p, c->T, c->fluid, c->rho, c->lam, c->lam_p, c->lam_T, s);
+  launch_assemble(c->grid, c->fluid, c->rowptr, c->dpos, c->Kx, c->Ky, c->Kz, c->phi, c->kT, c->p,
+                  c->T, c->pn, c->Tn, c->rho, c->lam, c->lam_p, c->lam_T, dt, c->bval, c->Sval,
+                  c->Rm, c->Re, s);
+  launch_wells(c->grid, c->fluid, c->wells, c->dpos, c->Kx, c->Ky, c->p, c->T, c->rho, c->lam,
+               c->lam_p, c->lam_T, c->bval, c->Sval, c->Rm, c->Re, s);
+  TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  k_check_finite<<<grid_for(4ll * c->nnzb), kBlock, 0, s>>>(4ll * c->nnzb, c->bval, flags);
+  TP_LAUNCH_CHECK();
+  if (read_flags(flags, s)) return TP_ENONFINITE;
+  c->assembled = true;
+  return TP_OK;
+}
+
+void build_device(tp_ctx* c, const tp_precond_opts& o) {
+  cudaStream_t s = c->s;
+  if (c->pc_graph) {
+    cudaGraphExecDestroy(c->pc_graph);
+    c->pc_graph = nullptr;
+  }
+  c->built = false;
+  launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+  launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
+                         c->scales, s);
+  c->S_active = (o.schur == 2) ? c->ATT : c->Sval;
+  DevCSR App{c->N, c->N, c->nnzb, c->rowptr, c->col, c->App, nullptr};
+  DevCSR S{c->N, c->N, c->nnzb, c->rowptr, c->col, c->S_active, nullptr};
+  c->opts = o;
+  c->hpp.reset(new Hierarchy());
+  c->hS.reset(new Hierarchy());
+  AmgOpts ao = amg_opts(o);
+  AmgOpts aS = ao;
+  if (o.interp_S >= 0) aS.interp = o.interp_S;
+  if (o.max_levels_S > 0) aS.max_levels = o.max_levels_S;
+  if (o.nu_S > 0) aS.nu_pre = aS.nu_post = o.nu_S;
+  c->hpp->setup(App, ao, s);
+  c->hS->setup(S, aS, s);
+  c->hpp->probe = c->probe_which == 0 ? &c->probe : nullptr;
+  c->hS->probe = c->probe_which == 1 ? &c->probe : nullptr;
+  if (o.use_graphs) {
+    cudaGraph_t graph = nullptr;
+    TP_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    try {
+      precond_record(c, s);
+    } catch (...) {
+      g_capturing = false;
+      cudaStreamEndCapture(s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    g_capturing = false;
+    TP_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+    size_t nodes = 0;
+    TP_CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nodes));
+    c->pc_graph_kernels = (long long)nodes;
+    cudaError_t e = cudaGraphInstantiate(&c->pc_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->pc_graph = nullptr;
+      fail(TP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+  }
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  c->built = true;
+}
+
+void refresh_device(tp_ctx* c) {
+  cudaStream_t s = c->s;
+  // A_pp and (for schur = 2) A_TT planes are the level-0 values in place
+  launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+  c->hpp->refresh(s);
+  c->hS->refresh(s);
+}
+
+void negated_residual(tp_ctx* c) {
+  cudaStream_t s = c->s;
+  const long long n = c->N;
+  TP_CUDA_TRY(cudaMemcpyAsync(c->io0, c->Rm, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(c->io1, c->Re, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  negate(c->io0, n, s);
+  negate(c->io1, n, s);
+}
+
+}  // namespace tp

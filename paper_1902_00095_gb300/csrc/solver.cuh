@@ -33,6 +33,7 @@ struct tp_ctx {
   double *App = nullptr, *ApT = nullptr, *ATp = nullptr, *ATT = nullptr;
   double* scales = nullptr;  // [2] equation scales s_m, s_e
   double* ones = nullptr;    // [2] = {1, 1}
+  double* fscale = nullptr;  // [2] scaling of the Newton function norm
   double* partials = nullptr;
   int nparts = 0;
   double* tmpN = nullptr;
@@ -70,4 +71,11 @@ void precond_apply(tp_ctx* c, const double* vp, const double* vT, const double* 
                    cudaStream_t s);
 int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, double* xT,
                  double rtol, int maxit, int restart, tp_solve_info* info);
+// device-resident steps shared by the C-ABI calls and the Newton driver
+int assemble_device(tp_ctx* c, double dt);              // at (c->p, c->T)
+void build_device(tp_ctx* c, const tp_precond_opts& o);  // full setup + graph
+void refresh_device(tp_ctx* c);                          // numeric-only
+void negated_residual(tp_ctx* c);                        // io0, io1 = -G
+int newton_step(tp_ctx* c, double dt, const tp_precond_opts& popts, const tp_newton_opts& no,
+                tp_newton_info* info);
 }  // namespace tp

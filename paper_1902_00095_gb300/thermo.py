@@ -41,7 +41,8 @@ class PrecondOpts(C.Structure):
                 ("interp", C.c_int), ("smoother", C.c_int), ("nu_pre", C.c_int),
                 ("nu_post", C.c_int), ("cheb_degree", C.c_int), ("theta", C.c_double),
                 ("max_levels", C.c_int), ("coarse_size", C.c_int), ("seed", C.c_ulonglong),
-                ("use_graphs", C.c_int)]
+                ("use_graphs", C.c_int), ("interp_S", C.c_int), ("max_levels_S", C.c_int),
+                ("nu_S", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -50,6 +51,20 @@ class SolveInfo(C.Structure):
                 ("rel_res_unscaled", C.c_double), ("rel_res_p", C.c_double),
                 ("rel_res_T", C.c_double), ("opc_pp", C.c_double), ("opc_S", C.c_double),
                 ("t_solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("max_newton", C.c_int), ("tol_f", C.c_double), ("tol_dx", C.c_double),
+                ("rtol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("reuse", C.c_int)]
+
+
+class NewtonInfo(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("linear_iters", C.c_int), ("status", C.c_int),
+                ("last_linear_status", C.c_int), ("rel_f", C.c_double), ("rel_dx", C.c_double),
+                ("t_ms", C.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -71,6 +86,9 @@ SIGNATURES = {
     "tp_solve": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double, C.c_int, C.c_int,
                                                              C.POINTER(SolveInfo), C.c_int]),
     "tp_spmv": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
+    "tp_newton_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                 C.c_void_p, C.POINTER(PrecondOpts), C.POINTER(NewtonOpts),
+                                 C.POINTER(NewtonInfo), C.c_int]),
     "tp_probe_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "tp_probe_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_longlong), _dp, C.c_int]),
     "tp_apply_preconditioner": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
@@ -252,6 +270,26 @@ class Solver:
         st = self._lib.tp_solve(self._h, p[0], p[1], p[2], p[3], float(rtol), int(maxit),
                                 int(restart), C.byref(info), d)
         _check(st, "tp_solve", warn_ok=True)
+        return keep[2], keep[3], info.as_dict()
+
+    def newton_step(self, p_n, T_n, dt, max_newton=3, tol_f=1e-8, tol_dx=1e-8, rtol=1e-8,
+                    maxit=500, restart=30, reuse=True, opts=None, out=None, **kw):
+        """One backward-Euler step by Newton's method from (p_n, T_n);
+        returns (p, T, info)."""
+        o = opts if opts is not None else default_opts(**kw)
+        no = NewtonOpts(int(max_newton), float(tol_f), float(tol_dx), float(rtol), int(maxit),
+                        int(restart), int(bool(reuse)))
+        if out is None:
+            if _is_torch(p_n):
+                import torch
+                out = (torch.empty_like(p_n), torch.empty_like(p_n))
+            else:
+                out = (np.empty(self.N), np.empty(self.N))
+        info = NewtonInfo()
+        p, d, keep = _args(p_n, T_n, out[0], out[1])
+        st = self._lib.tp_newton_step(self._h, p[0], p[1], float(dt), p[2], p[3], C.byref(o),
+                                      C.byref(no), C.byref(info), d)
+        _check(st, "tp_newton_step", warn_ok=True)
         return keep[2], keep[3], info.as_dict()
 
     def probe_enable(self, which):

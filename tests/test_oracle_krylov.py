@@ -117,3 +117,24 @@ def test_schur_approximation_beats_ATT_in_condition_number(variant):
     k_t = np.linalg.cond(np.linalg.solve(St, Sx))
     k_a = np.linalg.cond(np.linalg.solve(ATT, Sx))
     assert k_t < k_a
+
+
+def test_newton_converges_quadratically_to_a_root():
+    """Newton on the discrete residual with the analytic Jacobian (Sec. 3):
+    the scaled function norm falls quadratically and the final state is a
+    root of G to rounding."""
+    from oracle import newton
+    prob = make_problem("tiny", shape=(6, 5, 3), seed=5, dt_days=0.5)
+    prob["wells"][0]["value"] = 2e-4
+    prob["wells"][1]["value"] = 14.8e6
+    p, T, hist = newton.newton_step(prob, max_newton=8, tol_f=1e-13, tol_dx=0.0)
+    relf = [h[0] for h in hist]
+    assert relf[-1] < 1e-12
+    # e_{k+1} <= C e_k^2 over the last two steps (quadratic convergence)
+    for a, b in zip(relf[-3:-1], relf[-2:]):
+        assert b <= 1e3 * a * a, relf
+    sysb, bp, bT, _ = krylov.assemble(prob, p, T)
+    sys0, bp0, bT0, _ = krylov.assemble(prob)
+    g = np.hypot(np.linalg.norm(sys0.s_m * bp), np.linalg.norm(sys0.s_e * bT))
+    g0 = np.hypot(np.linalg.norm(sys0.s_m * bp0), np.linalg.norm(sys0.s_e * bT0))
+    assert g <= 1e-12 * g0
