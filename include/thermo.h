@@ -245,6 +245,28 @@ int  tp_export_level(tp_ctx* ctx, int which, int level, int* rowptr, int* col,
                      double* val, signed char* cf, signed char* strong,
                      int* P_nnz, int* P_rowptr, int* P_col, double* P_val);
 
+/* --- allocation-free equation scales -------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory (a frozen or defragmenting memory pool,
+ * allocator hooks, embedders with a fixed device budget). It computes the
+ * same equation scales as the solver, scales[0] = N / sum_i |A_pp,ii| and
+ * scales[1] = N / sum_i |A_TT,ii|, from a caller-owned block-CSR matrix in
+ * the layout tp_export_system returns (rowptr [N+1], col [nnzb], val
+ * [4*nnzb] row-major 2x2 blocks), all DEVICE pointers, writing scales [2]
+ * (device). It calls no cudaMalloc/cudaFree: its only scratch is a fixed
+ * 64 KiB __device__ array that every GPU loading this library keeps until
+ * exit. Limit: N <= 8,388,608 cells; larger N returns TP_EINVAL. The first
+ * call on each device looks up the array's device address (call it once
+ * before any stream capture). All calls share the array, so calls whose
+ * kernels overlap on the GPU (different streams, or concurrent host
+ * threads) race; serialise them. Work is enqueued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns without
+ * synchronising; the result is ready when the stream reaches that point.
+ * Returns TP_OK, TP_EINVAL or TP_ECUDA. */
+int tp_equation_scales_noalloc(int N, const int* rowptr, const int* col,
+                               const double* val, double* scales,
+                               void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

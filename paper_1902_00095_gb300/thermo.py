@@ -99,6 +99,8 @@ SIGNATURES = {
     "tp_amg_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.POINTER(PrecondOpts), C.c_void_p, C.c_int]),
     "tp_amg_destroy": (None, [C.c_void_p]),
+    "tp_equation_scales_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]),
     "tp_amg_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "tp_amg_info": (C.c_int, [C.c_void_p, _ip, _ip, _ip, C.c_int]),
     "tp_amg_export_level": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, _dp, _sp, _sp, _ip, _ip,
