@@ -112,8 +112,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-PROBE_NAMES = {0: "k_jacobi (finest A_pp level, l1-Jacobi sweep)",
-               1: "k_jacobi (finest S~ level, l1-Jacobi sweep)",
+PROBE_NAMES = {0: "k_jacobi_ell (finest A_pp level, l1-Jacobi sweep, ELL)",
+               1: "k_jacobi_ell (finest S~ level, l1-Jacobi sweep, ELL)",
                2: "k_block_spmv (2x2 block-CSR SpMV, FP64)"}
 
 

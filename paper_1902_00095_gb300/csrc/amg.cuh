@@ -62,7 +62,15 @@ struct Level {
   void* t = nullptr;
   void* r = nullptr;
   int lanes_A = 1, lanes_R = 1, lanes_P = 1;
+  // ELL copy of A (slot-major: entry k of row i at k * n + i, padded with
+  // column i and value 0) for levels whose rows have at most kEllMaxW entries
+  int ell_w = 0;
+  int* ell_col = nullptr;
+  double* ell_val = nullptr;
+  float* ell_valf = nullptr;
 };
+
+constexpr int kEllMaxW = 8;
 
 class Hierarchy {
  public:

@@ -289,15 +289,13 @@ __global__ void k_extpi_sets(int n, const int* __restrict__ rp, const int* __res
   cnt[i] = u;
 }
 
-__global__ void k_extpi_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
+__device__ void extpi_fill_row_serial(int i, const int* __restrict__ rp, const int* __restrict__ col,
                              const double* __restrict__ val, const int* __restrict__ dpos,
                              const unsigned char* __restrict__ strong,
                              const signed char* __restrict__ state, const int* __restrict__ cidx,
                              const int* __restrict__ off, const int* __restrict__ buf,
                              const int* __restrict__ Prp, int* __restrict__ Pcol,
                              double* __restrict__ Pval) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   const int p0 = Prp[i], p1 = Prp[i + 1];
   if (state[i] == kC) {
     Pcol[p0] = cidx[i];
@@ -352,6 +350,114 @@ __global__ void k_extpi_fill(int n, const int* __restrict__ rp, const int* __res
     }
   }
   for (int s = p0; s < p1; ++s) Pval[s] = __ddiv_rn(-Pval[s], denom);
+}
+
+
+// Warp-per-row extended+i fill with the arithmetic order of the serial form:
+// lanes evaluate the strong F neighbours' sums s_k (and t_k = a_ik / s_k)
+// independently, lane 0 accumulates the denominator over row i ascending,
+// and each lane owns interpolation slots, adding t_k * ahat_km over k
+// ascending. Rows longer than kFillMaxE use the serial form.
+constexpr int kFillMaxE = 256;
+constexpr int kFillWarps = 4;
+
+__global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
+    int n, const int* __restrict__ rp, const int* __restrict__ col,
+    const double* __restrict__ val, const int* __restrict__ dpos,
+    const unsigned char* __restrict__ strong, const signed char* __restrict__ state,
+    const int* __restrict__ cidx, const int* __restrict__ off, const int* __restrict__ buf,
+    const int* __restrict__ Prp, int* __restrict__ Pcol, double* __restrict__ Pval) {
+  __shared__ double s_t[kFillWarps][kFillMaxE];
+  __shared__ double s_akk[kFillWarps][kFillMaxE];
+  __shared__ double s_term[kFillWarps][kFillMaxE];
+  __shared__ unsigned char s_flag[kFillWarps][kFillMaxE];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kFillWarps + w;
+  if (i >= n) return;
+  const int p0 = Prp[i], p1 = Prp[i + 1];
+  if (state[i] == kC) {
+    if (lane == 0) {
+      Pcol[p0] = cidx[i];
+      Pval[p0] = 1.0;
+    }
+    return;
+  }
+  if (p0 == p1) return;
+  const int r0 = rp[i], r1 = rp[i + 1];
+  if (r1 - r0 > kFillMaxE) {
+    if (lane == 0)
+      extpi_fill_row_serial(i, rp, col, val, dpos, strong, state, cidx, off, buf, Prp, Pcol, Pval);
+    return;
+  }
+  const int* set = buf + off[i];
+  const int ns = p1 - p0;
+  double* t = s_t[w];
+  double* akk_e = s_akk[w];
+  double* term = s_term[w];
+  unsigned char* flag = s_flag[w];
+  // flags: 0 skip (diagonal or interpolated directly), 1 lump a_ie into the
+  // denominator, 3 strong F neighbour with t_k (term = t_k ahat_ki or 0)
+  for (int e = r0 + lane; e < r1; e += 32) {
+    const int q = e - r0;
+    const int k = col[e];
+    unsigned char fl = 0;
+    double tk = 0.0, tm = 0.0, ak = 0.0;
+    if (k == i) {
+      fl = 0;
+    } else if (strong[e] && state[k] != kC) {
+      ak = val[dpos[k]];
+      double sk = 0.0, aki = 0.0;
+      bool has_ki = false;
+      for (int f = rp[k]; f < rp[k + 1]; ++f) {
+        const int m = col[f];
+        if ((m == i || find_in(set, 0, ns, m) >= 0) && opposite(val[f], ak)) sk = __dadd_rn(sk, val[f]);
+        if (m == i) {
+          aki = val[f];
+          has_ki = true;
+        }
+      }
+      if (sk == 0.0) {
+        fl = 1;
+      } else {
+        fl = 3;
+        tk = __ddiv_rn(val[e], sk);
+        if (has_ki && opposite(aki, ak)) tm = __dmul_rn(tk, aki);
+      }
+    } else if (find_in(set, 0, ns, k) >= 0) {
+      fl = 0;
+    } else {
+      fl = 1;
+    }
+    flag[q] = fl;
+    t[q] = tk;
+    term[q] = tm;
+    akk_e[q] = ak;
+  }
+  __syncwarp();
+  double denom = 0.0;
+  if (lane == 0) {
+    denom = val[dpos[i]];
+    for (int e = r0; e < r1; ++e) {
+      const int q = e - r0;
+      if (flag[q] == 1) denom = __dadd_rn(denom, val[e]);
+      else if (flag[q] == 3 && term[q] != 0.0) denom = __dadd_rn(denom, term[q]);
+    }
+  }
+  denom = __shfl_sync(0xffffffffu, denom, 0);
+  for (int sl = lane; sl < ns; sl += 32) {
+    const int m = set[sl];
+    const int pe = find_in(col, r0, r1, m);
+    double num = pe >= 0 ? val[pe] : 0.0;
+    for (int e = r0; e < r1; ++e) {
+      const int q = e - r0;
+      if (flag[q] != 3) continue;
+      const int k = col[e];
+      const int f = find_in(col, rp[k], rp[k + 1], m);
+      if (f >= 0 && opposite(val[f], akk_e[q])) num = __dadd_rn(num, __dmul_rn(t[q], val[f]));
+    }
+    Pcol[p0 + sl] = cidx[m];
+    Pval[p0 + sl] = __ddiv_rn(-num, denom);
+  }
 }
 
 // ------------------------------------------------------------- transpose
@@ -449,6 +555,141 @@ __global__ void k_spgemm_rows(int n, const int* __restrict__ Arp, const int* __r
   cnt[i] = u;
 }
 
+// Warp-per-row variant of k_spgemm_rows with the same summation order.
+// The products of row i are staged in shared memory with key (column << 32 |
+// sequence number), sorted by a warp bitonic sort, and every column's run is
+// summed from 0.0 in sequence order by one lane. Rows with more than kSpCap
+// products fall back to the serial insertion of k_spgemm_rows (lane 0).
+constexpr int kSpCap = 1024;
+constexpr int kSpWarps = 2;  // 2 x 16 KiB static shared memory per block
+
+__device__ void spgemm_row_serial(int i, const int* __restrict__ Arp, const int* __restrict__ Acol,
+                                  const double* __restrict__ Aval, const int* __restrict__ Brp,
+                                  const int* __restrict__ Bcol, const double* __restrict__ Bval,
+                                  int* __restrict__ cc, double* __restrict__ cv, int* __restrict__ cnt) {
+  int u = 0;
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
+    const int k = Acol[e];
+    const double a = Aval[e];
+    for (int f = Brp[k]; f < Brp[k + 1]; ++f) {
+      const int j = Bcol[f];
+      const double prod = __dmul_rn(a, Bval[f]);
+      int lo = 0, hi = u;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cc[mid] < j) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < u && cc[lo] == j) {
+        cv[lo] = __dadd_rn(cv[lo], prod);
+      } else {
+        for (int q = u; q > lo; --q) {
+          cc[q] = cc[q - 1];
+          cv[q] = cv[q - 1];
+        }
+        cc[lo] = j;
+        cv[lo] = __dadd_rn(0.0, prod);
+        ++u;
+      }
+    }
+  }
+  cnt[i] = u;
+}
+
+__global__ void __launch_bounds__(32 * kSpWarps) k_spgemm_rows_warp(
+    int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
+    const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
+    const double* __restrict__ Bval, const int* __restrict__ off, const int* __restrict__ ub,
+    int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
+  __shared__ unsigned long long s_key[kSpWarps][kSpCap];
+  __shared__ double s_val[kSpWarps][kSpCap];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kSpWarps + w;
+  if (i >= n) return;
+  const int ex = ub[i];
+  int* cc = ccol + off[i];
+  double* cv = cval + off[i];
+  if (ex > kSpCap) {
+    if (lane == 0) spgemm_row_serial(i, Arp, Acol, Aval, Brp, Bcol, Bval, cc, cv, cnt);
+    return;
+  }
+  unsigned long long* key = s_key[w];
+  double* val = s_val[w];
+  // 1. products in canonical order (A row ascending, then B row ascending)
+  const int a0 = Arp[i], a1 = Arp[i + 1];
+  int base = 0;
+  for (int e0 = a0; e0 < a1; e0 += 32) {
+    const int e = e0 + lane;
+    int k = 0, len = 0;
+    if (e < a1) {
+      k = Acol[e];
+      len = Brp[k + 1] - Brp[k];
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (e < a1) {
+      const double a = Aval[e];
+      const int fb = Brp[k];
+      int pidx = base + incl - len;
+      for (int t = 0; t < len; ++t, ++pidx) {
+        key[pidx] = ((unsigned long long)(unsigned)Bcol[fb + t] << 32) | (unsigned)pidx;
+        val[pidx] = __dmul_rn(a, Bval[fb + t]);
+      }
+    }
+    base += total;
+  }
+  int P = 1;
+  while (P < ex) P <<= 1;
+  for (int q = ex + lane; q < P; q += 32) key[q] = ~0ull;
+  __syncwarp();
+  // 2. bitonic sort of the keys (ascending)
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = lane; t < (P >> 1); t += 32) {
+        const int lo = 2 * stride * (t / stride) + (t % stride);
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const unsigned long long x = key[lo], y = key[hi];
+        if ((x > y) == up) {
+          key[lo] = y;
+          key[hi] = x;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // 3. one lane per column run: sum from 0.0 in sequence order
+  int nrun = 0;
+  for (int q0 = 0; q0 < ex; q0 += 32) {
+    const int q = q0 + lane;
+    int start = 0;
+    if (q < ex) start = (q == 0) || ((key[q] >> 32) != (key[q - 1] >> 32));
+    int incl = start;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (start) {
+      const unsigned col = (unsigned)(key[q] >> 32);
+      double sum = 0.0;
+      for (int r = q; r < ex && (unsigned)(key[r] >> 32) == col; ++r)
+        sum = __dadd_rn(sum, val[(unsigned)(key[r] & 0xffffffffu)]);
+      const int rid = nrun + incl - 1;
+      cc[rid] = (int)col;
+      cv[rid] = sum;
+    }
+    nrun += total;
+  }
+  if (lane == 0) cnt[i] = nrun;
+}
+
 // numeric-only C = A B on a known pattern (same canonical order)
 __global__ void k_spgemm_numeric(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
                                  const double* __restrict__ Aval, const int* __restrict__ Brp,
@@ -507,6 +748,28 @@ __global__ void k_l1_dinv(int n, const int* __restrict__ rp, const int* __restri
 __global__ void k_to_float(long long n, const double* __restrict__ a, float* __restrict__ b) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
+}
+
+// --------------------------------------------------------------- ELL copy
+__global__ void k_max_row(int n, const int* __restrict__ rp, int* __restrict__ mx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(mx, rp[i + 1] - rp[i]);
+}
+
+__global__ void k_to_ell(int n, int w, const int* __restrict__ rp, const int* __restrict__ col,
+                         const double* __restrict__ val, int* __restrict__ ecol,
+                         double* __restrict__ eval, float* __restrict__ evalf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int r0 = rp[i], len = rp[i + 1] - r0;
+  for (int k = 0; k < w; ++k) {
+    const long long q = (long long)k * n + i;
+    const bool has = k < len;
+    if (ecol) ecol[q] = has ? col[r0 + k] : i;
+    const double v = has ? val[r0 + k] : 0.0;
+    eval[q] = v;
+    if (evalf) evalf[q] = (float)v;
+  }
 }
 
 // ------------------------------------------------------------ coarsest level
@@ -623,8 +886,8 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   int* ccol = scratch.alloc<int>(tot + 1);
   double* cval = scratch.alloc<double>(tot + 1);
   int* cnt = scratch.alloc<int>(n + 1);
-  k_spgemm_rows<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                                 B.val, off, ccol, cval, cnt);
+  k_spgemm_rows_warp<<<(n + kSpWarps - 1) / kSpWarps, 32 * kSpWarps, 0, s>>>(
+      n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
   DevCSR C;
   C.n = n;
@@ -684,7 +947,7 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
   L.clear();
   coarse_inv = nullptr;
   Pool scratch;
-  err = pool.alloc<int>(1);
+  err = pool.alloc<int>(2);
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   L.emplace_back();
   L[0].A = A0;
@@ -766,9 +1029,9 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
       P.nnz = (int)scan_exclusive(cnt, P.rowptr, n, scratch, s);
       P.col = pool.alloc<int>(P.nnz);
       P.val = pool.alloc<double>(P.nnz);
-      k_extpi_fill<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, cur.dpos,
-                                                    cur.strong, cur.cf, cidx, off, buf,
-                                                    P.rowptr, P.col, P.val);
+      k_extpi_fill_warp<<<(n + kFillWarps - 1) / kFillWarps, 32 * kFillWarps, 0, s>>>(
+          n, A.rowptr, A.col, A.val, cur.dpos, cur.strong, cur.cf, cidx, off, buf, P.rowptr,
+          P.col, P.val);
       TP_LAUNCH_CHECK();
     }
     cur.P = P;
@@ -811,6 +1074,25 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
         k_to_float<<<grid_for(v.R.nnz), kBlock, 0, s>>>(v.R.nnz, v.R.val, v.R.valf);
         TP_LAUNCH_CHECK();
       }
+    }
+    // ELL copy for short-row levels (the 7-point finest level)
+    if (allocate && n >= 4096) {
+      TP_CUDA_TRY(cudaMemsetAsync(err + 1, 0, sizeof(int), s));
+      k_max_row<<<grid_for(n), kBlock, 0, s>>>(n, v.A.rowptr, err + 1);
+      TP_LAUNCH_CHECK();
+      const int w = read_int(err + 1, s);
+      if (w <= kEllMaxW) {
+        v.ell_w = w;
+        v.ell_col = pool.alloc<int>((size_t)w * n);
+        v.ell_val = pool.alloc<double>((size_t)w * n);
+        v.ell_valf = f32 ? pool.alloc<float>((size_t)w * n) : nullptr;
+      }
+    }
+    if (v.ell_w > 0) {
+      k_to_ell<<<grid_for(n), kBlock, 0, s>>>(n, v.ell_w, v.A.rowptr, v.A.col, v.A.val,
+                                              allocate ? v.ell_col : nullptr, v.ell_val,
+                                              v.ell_valf);
+      TP_LAUNCH_CHECK();
     }
     if (allocate) {
       const size_t es = f32 ? sizeof(float) : sizeof(double);

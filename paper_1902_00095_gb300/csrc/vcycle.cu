@@ -55,6 +55,93 @@ __global__ void k_jacobi0(int n, const TV* __restrict__ dinv, const TB* __restri
   if (i < n) x[i] = dinv[i] * (TV)b[i];
 }
 
+// two sweeps from a zero guess in one pass:
+// x = d b + d (b - A d b)  (x1 = d b is recomputed for every neighbour)
+template <int LANES, class TV, class TB>
+__global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__ rp,
+                                                  const int* __restrict__ col,
+                                                  const TV* __restrict__ val,
+                                                  const TV* __restrict__ dinv,
+                                                  const TB* __restrict__ b, TV* __restrict__ x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / LANES, lane = t % LANES;
+  const bool valid = row < n;
+  TV acc = TV(0);
+  if (valid) {
+    const int e1 = rp[row + 1];
+    for (int e = rp[row] + lane; e < e1; e += LANES) {
+      const int j = col[e];
+      acc += val[e] * (dinv[j] * (TV)b[j]);
+    }
+  }
+  acc = group_sum<LANES>(acc);
+  if (valid && lane == 0) {
+    const TV d = dinv[row], bi = (TV)b[row];
+    x[row] = d * bi + d * (bi - acc);
+  }
+}
+
+// ELL forms (slot-major, one thread per row, coalesced over rows)
+template <class TV, class TX>
+__device__ __forceinline__ TV ell_dot(int n, int w, const int* __restrict__ ecol,
+                                      const TV* __restrict__ eval, const TX* __restrict__ x,
+                                      int row) {
+  TV acc = TV(0);
+#pragma unroll
+  for (int k = 0; k < kEllMaxW; ++k) {
+    if (k < w) {
+      const long long q = (long long)k * n + row;
+      acc += eval[q] * (TV)x[ecol[q]];
+    }
+  }
+  return acc;
+}
+
+template <class TV, class TB, class TO>
+__global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __restrict__ ecol,
+                                                    const TV* __restrict__ eval,
+                                                    const TV* __restrict__ dinv,
+                                                    const TB* __restrict__ b,
+                                                    const TV* __restrict__ xin,
+                                                    TO* __restrict__ xout) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const TV ax = ell_dot<TV, TV>(n, w, ecol, eval, xin, row);
+  xout[row] = (TO)(xin[row] + dinv[row] * ((TV)b[row] - ax));
+}
+
+template <class TV, class TB>
+__global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* __restrict__ ecol,
+                                                      const TV* __restrict__ eval,
+                                                      const TB* __restrict__ b,
+                                                      const TV* __restrict__ x,
+                                                      TV* __restrict__ r) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  r[row] = (TV)b[row] - ell_dot<TV, TV>(n, w, ecol, eval, x, row);
+}
+
+template <class TV, class TB>
+__global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* __restrict__ ecol,
+                                                      const TV* __restrict__ eval,
+                                                      const TV* __restrict__ dinv,
+                                                      const TB* __restrict__ b,
+                                                      TV* __restrict__ x) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  TV acc = TV(0);
+#pragma unroll
+  for (int k = 0; k < kEllMaxW; ++k) {
+    if (k < w) {
+      const long long q = (long long)k * n + row;
+      const int j = ecol[q];
+      acc += eval[q] * (dinv[j] * (TV)b[j]);
+    }
+  }
+  const TV d = dinv[row], bi = (TV)b[row];
+  x[row] = d * bi + d * (bi - acc);
+}
+
 // r = b - A x
 template <int LANES, class TV, class TB>
 __global__ void __launch_bounds__(256) k_residual(int n, const int* __restrict__ rp,
@@ -127,6 +214,21 @@ void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB*
 }
 
 template <class TV, class TB>
+void jacobi2z(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b, TV* x,
+              cudaStream_t s) {
+  const int g = grid_for((long long)A.n * lanes);
+  switch (lanes) {
+#define TP_CASE(L)                                                                       \
+  case L:                                                                                \
+    k_jacobi2z<L, TV, TB><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, dinv, b, x);   \
+    break;
+    TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
+#undef TP_CASE
+  }
+  TP_LAUNCH_CHECK();
+}
+
+template <class TV, class TB>
 void residual(int lanes, const DevCSR& A, const TV* val, const TB* b, const TV* x, TV* r,
               cudaStream_t s) {
   const int g = grid_for((long long)A.n * lanes);
@@ -184,6 +286,7 @@ struct Vals {
 };
 template <>
 struct Vals<double> {
+  static const double* E(const Level& l) { return l.ell_val; }
   static const double* A(const Level& l) { return l.A.val; }
   static const double* P(const Level& l) { return l.P.val; }
   static const double* R(const Level& l) { return l.R.val; }
@@ -191,6 +294,7 @@ struct Vals<double> {
 };
 template <>
 struct Vals<float> {
+  static const float* E(const Level& l) { return l.ell_valf; }
   static const float* A(const Level& l) { return l.A.valf; }
   static const float* P(const Level& l) { return l.P.valf; }
   static const float* R(const Level& l) { return l.R.valf; }
@@ -200,6 +304,42 @@ struct Vals<float> {
 // One V-cycle on level l for right-hand side b (type TB). The result goes to
 // `final_out` (type TO) when non-null, else to one of the level's work
 // vectors, whose address is returned.
+// level operations: ELL when the level has an ELL copy, CSR otherwise
+template <class TV, class TB, class TO>
+void level_sweep(const Level& v, const TV* dinv, const TB* b, const TV* xin, TO* xout,
+                 cudaStream_t s) {
+  if (v.ell_w > 0) {
+    k_jacobi_ell<TV, TB, TO><<<grid_for(v.A.n), kBlock, 0, s>>>(
+        v.A.n, v.ell_w, v.ell_col, Vals<TV>::E(v), dinv, b, xin, xout);
+    TP_LAUNCH_CHECK();
+  } else {
+    jacobi<TV, TB, TO>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, xin, xout, s);
+  }
+}
+
+template <class TV, class TB>
+void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_t s) {
+  if (v.ell_w > 0) {
+    k_residual_ell<TV, TB><<<grid_for(v.A.n), kBlock, 0, s>>>(v.A.n, v.ell_w, v.ell_col,
+                                                              Vals<TV>::E(v), b, x, r);
+    TP_LAUNCH_CHECK();
+  } else {
+    residual<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), b, x, r, s);
+  }
+}
+
+template <class TV, class TB>
+void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* x,
+                                cudaStream_t s) {
+  if (v.ell_w > 0) {
+    k_jacobi2z_ell<TV, TB><<<grid_for(v.A.n), kBlock, 0, s>>>(v.A.n, v.ell_w, v.ell_col,
+                                                              Vals<TV>::E(v), dinv, b, x);
+    TP_LAUNCH_CHECK();
+  } else {
+    jacobi2z<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, x, s);
+  }
+}
+
 // algorithmic bytes of one sweep x_out = x_in + dinv (b - A x_in)
 template <class TV, class TB, class TO>
 double sweep_bytes(const DevCSR& A) {
@@ -208,11 +348,11 @@ double sweep_bytes(const DevCSR& A) {
 }
 
 template <class TV, class TB, class TO>
-void jacobi_probed(Probe* pr, int lanes, const DevCSR& A, const TV* val, const TV* dinv,
-                   const TB* b, const TV* xin, TO* xout, cudaStream_t s) {
+void sweep_probed(Probe* pr, const Level& v, const TV* dinv, const TB* b, const TV* xin,
+                  TO* xout, cudaStream_t s) {
   if (pr) pr->before(s);
-  jacobi<TV, TB, TO>(lanes, A, val, dinv, b, xin, xout, s);
-  if (pr) pr->after(s, sweep_bytes<TV, TB, TO>(A));
+  level_sweep<TV, TB, TO>(v, dinv, b, xin, xout, s);
+  if (pr) pr->after(s, sweep_bytes<TV, TB, TO>(v.A));
 }
 
 template <class TV, class TB, class TO>
@@ -230,21 +370,26 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     coarse<TB, TV>(n, cinv, b, x, s);
     return x;
   }
-  const TV* A = Vals<TV>::A(v);
   const TV* dinv = Vals<TV>::dinv(v);
-  // pre-smoothing from a zero guess
-  k_jacobi0<TV, TB><<<grid_for(n), kBlock, 0, s>>>(n, dinv, b, x);
-  TP_LAUNCH_CHECK();
+  // pre-smoothing from a zero guess (the first two sweeps fused)
   TV* cur = x;
   TV* oth = t;
+  int done = 1;
+  if (nu_pre >= 2) {
+    level_two_sweeps_from_zero<TV, TB>(v, dinv, b, x, s);
+    done = 2;
+  } else {
+    k_jacobi0<TV, TB><<<grid_for(n), kBlock, 0, s>>>(n, dinv, b, x);
+    TP_LAUNCH_CHECK();
+  }
   Probe* pr = (l == 0) ? probe : nullptr;
-  for (int k = 1; k < nu_pre; ++k) {
-    jacobi_probed<TV, TB, TV>(pr, v.lanes_A, v.A, A, dinv, b, cur, oth, s);
+  for (int k = done; k < nu_pre; ++k) {
+    sweep_probed<TV, TB, TV>(pr, v, dinv, b, cur, oth, s);
     std::swap(cur, oth);
   }
   // coarse-grid correction
   TV* r = static_cast<TV*>(v.r);
-  residual<TV, TB>(v.lanes_A, v.A, A, b, cur, r, s);
+  level_residual<TV, TB>(v, b, cur, r, s);
   Level& c = L[l + 1];
   TV* bc = static_cast<TV*>(c.b);
   spmv<TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
@@ -253,10 +398,10 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   // post-smoothing
   for (int k = 1; k <= nu_post; ++k) {
     if (k == nu_post && final_out) {
-      jacobi_probed<TV, TB, TO>(pr, v.lanes_A, v.A, A, dinv, b, cur, final_out, s);
+      sweep_probed<TV, TB, TO>(pr, v, dinv, b, cur, final_out, s);
       return nullptr;
     }
-    jacobi_probed<TV, TB, TV>(pr, v.lanes_A, v.A, A, dinv, b, cur, oth, s);
+    sweep_probed<TV, TB, TV>(pr, v, dinv, b, cur, oth, s);
     std::swap(cur, oth);
   }
   return cur;

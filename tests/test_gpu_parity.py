@@ -40,6 +40,8 @@ PROBLEMS = {
     "cfg1": lambda: (make_problem(1), None),
     "ragged": lambda: (make_problem("tiny", shape=(13, 11, 7), seed=21), 7),
     "thin": lambda: (make_problem("tiny", shape=(37, 1, 3), seed=4), 8),
+    # more than 4096 cells: the finest level also gets the ELL copy
+    "mid": lambda: (make_problem("tiny", shape=(20, 16, 14), seed=6), 9),
 }
 
 
@@ -109,9 +111,9 @@ def _compare_hierarchies(gpu_amg, ohier, interp_name):
             assert np.array_equal(g["P"][2], P[2]), (l, interp_name)
 
 
-@pytest.mark.parametrize("interp", [1, 0])
-@pytest.mark.parametrize("which", ["App", "S"])
-@pytest.mark.parametrize("name", ["cfg1", "ragged"])
+@pytest.mark.parametrize("name,which,interp", [
+    (n, w, i) for n in ("cfg1", "ragged") for w in ("App", "S") for i in (1, 0)]
+    + [("mid", "App", 1), ("mid", "S", 0)])
 def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp):
     """Both sides set up AMG on the same FP64 matrix (assembled by the
     oracle): strength, PMIS split, interpolation and Galerkin operators of
