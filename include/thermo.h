@@ -245,6 +245,61 @@ int  tp_export_level(tp_ctx* ctx, int which, int level, int* rowptr, int* col,
                      double* val, signed char* cf, signed char* strong,
                      int* P_nnz, int* P_rowptr, int* P_col, double* P_val);
 
+/* --- learned correction of the Schur approximation -----------------------
+ * Not in the paper (a growth direction of this library): a per-cell MLP
+ * 24 -> 64 -> 64 -> 8 (GELU, tanh form) rescales row i of S~_T (Eq. Se):
+ *   S_ii <- S~_ii exp(o_0) + o_7 S~_ii,  S_ij <- S~_ij exp(o_d), d = 1..6 the
+ *   face direction of j (z-, y-, x-, x+, y+, z+).
+ * A row keeps plain S~_T when its corrected diagonal is not positive, an
+ * off-diagonal changes sign, or it loses the diagonal dominance the plain
+ * row had; if more than a quarter of the rows fall back, plain S~_T is used.
+ * Parameters: flat float64 [6280] in the order W1 [64][24], b1 [64],
+ * W2 [64][64], b2 [64], W3 [8][64], b3 [8] (row-major). The device keeps
+ * FP32 master weights and BF16 copies; inference and training run on BF16
+ * tensor cores with FP32 accumulation. */
+typedef struct tp_mlp tp_mlp;
+int  tp_mlp_create(tp_mlp** mlp, const double* params, void* cuda_stream);
+void tp_mlp_destroy(tp_mlp* mlp);
+int  tp_mlp_set_params(tp_mlp* mlp, const double* params);  /* resets Adam */
+int  tp_mlp_get_params(tp_mlp* mlp, double* params);
+/* O [n][8] = MLP(X [n][24]) (FP32). */
+int  tp_mlp_forward(tp_mlp* mlp, int n, const float* X, float* O, int ptr_is_device);
+/* Gradient (host [6280], may be NULL) and value of the loss
+ * mean_s ((S_learned,s - target_s) / Sd_s)^2 over B samples: features X
+ * [B][24], slot_s (0 diagonal, 1..6 face direction), S~ entry St_s, S~
+ * diagonal Sd_s, exact Schur entry target_s. */
+int  tp_mlp_gradient(tp_mlp* mlp, int B, const float* X, const int* slot,
+                     const double* St, const double* Sd, const double* target,
+                     double* grad, double* loss, int ptr_is_device);
+/* Same gradient, then one Adam step (Kingma and Ba 2015, beta 0.9/0.999,
+ * eps 1e-8, bias-corrected) with learning rate lr. */
+int  tp_mlp_train_step(tp_mlp* mlp, int B, const float* X, const int* slot,
+                       const double* St, const double* Sd, const double* target,
+                       double lr, double* loss, int ptr_is_device);
+/* Features of every cell at the last tp_assemble, X [N][24] FP32:
+ * 0-5 log10(T_f / 1e-12 m^3), 6-11 log10(Tc_f / (1 W/K)) per face direction
+ * (0 without a face), 12 log10(lambda / 1e6), 13-18 outward advective face
+ * coefficient c_v T_f lambda_up dPhi / S~_ii, 19 A_pT A_Tp / (A_pp A_TT) at
+ * the diagonal, 20 log10(A_pp,ii s_m), 21 log10(A_TT,ii s_e),
+ * 22 (A_TT,ii - S~_ii) / S~_ii, 23 accumulation / S~_ii. */
+int  tp_learned_features(tp_ctx* ctx, float* X, int ptr_is_device);
+/* Model used by tp_build_preconditioner when opts.schur == 1 (borrowed:
+ * must outlive its use). */
+int  tp_set_schur_model(tp_ctx* ctx, tp_mlp* model);
+/* Rows that fell back to plain S~ in the last learned build, and whether
+ * the whole matrix did. */
+int  tp_learned_status(tp_ctx* ctx, int* fallback_rows, int* global_fallback);
+/* Exact Schur complement columns restricted to the 7-point pattern
+ * (S = A_TT - A_Tp A_pp^{-1} A_pT, Eq. Afact): for each column j of cols,
+ * z = A_pp^{-1} A_pT e_j by FGMRES preconditioned with the A_pp V-cycle of
+ * the last build (relative tolerance rtol), then S_ij = (A_TT e_j -
+ * A_Tp z)_i for the rows i of column j. Host outputs entry [ncols][7]
+ * (pattern entry index of (i, j), -1 padding) and value [ncols][7];
+ * iters = total FGMRES iterations. TP_NOT_CONVERGED if a solve stopped
+ * above rtol. */
+int  tp_probe_schur_columns(tp_ctx* ctx, const int* cols, int ncols, double rtol,
+                            int* entry, double* value, int* iters);
+
 /* --- allocation-free equation scales -------------------------------------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory (a frozen or defragmenting memory pool,

@@ -17,6 +17,8 @@ import numpy as np
 import scipy.sparse
 import scipy.sparse.linalg
 
+from synthetic import mlp as _mlp_init
+
 from . import physics
 
 NF, NH, NO = 24, 64, 8
@@ -119,14 +121,10 @@ def gelu_grad(x):
 
 
 def init_params(seed):
-    """W1 [64, 24], b1 [64], W2 [64, 64], b2 [64], W3 [8, 64], b3 [8]; weights
-    uniform(-1, 1) / sqrt(fan_in) from PCG64(seed), W3 and biases zero (the
-    untrained network is the identity correction)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    W1 = rng.uniform(-1, 1, (NH, NF)) / np.sqrt(NF)
-    W2 = rng.uniform(-1, 1, (NH, NH)) / np.sqrt(NH)
-    return dict(W1=W1, b1=np.zeros(NH), W2=W2, b2=np.zeros(NH),
-                W3=np.zeros((NO, NH)), b3=np.zeros(NO))
+    """Seeded initial weights (synthetic.mlp: W1, W2 uniform / sqrt(fan_in),
+    W3 and biases zero, so the untrained network is the identity
+    correction)."""
+    return _mlp_init.initial_params(seed)
 
 
 def forward(params, X):

@@ -360,6 +360,19 @@ __device__ void extpi_fill_row_serial(int i, const int* __restrict__ rp, const i
 // ascending. Rows longer than kFillMaxE use the serial form.
 constexpr int kFillMaxE = 256;
 constexpr int kFillWarps = 4;
+constexpr int kFillShort = 16;  // rows up to this length: one thread per row
+
+__global__ void k_extpi_fill_short(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                   const double* __restrict__ val, const int* __restrict__ dpos,
+                                   const unsigned char* __restrict__ strong,
+                                   const signed char* __restrict__ state,
+                                   const int* __restrict__ cidx, const int* __restrict__ off,
+                                   const int* __restrict__ buf, const int* __restrict__ Prp,
+                                   int* __restrict__ Pcol, double* __restrict__ Pval) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || rp[i + 1] - rp[i] > kFillShort) return;
+  extpi_fill_row_serial(i, rp, col, val, dpos, strong, state, cidx, off, buf, Prp, Pcol, Pval);
+}
 
 __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
     int n, const int* __restrict__ rp, const int* __restrict__ col,
@@ -374,6 +387,7 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kFillWarps + w;
   if (i >= n) return;
+  if (rp[i + 1] - rp[i] <= kFillShort) return;  // done by k_extpi_fill_short
   const int p0 = Prp[i], p1 = Prp[i + 1];
   if (state[i] == kC) {
     if (lane == 0) {
@@ -516,14 +530,18 @@ __global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __res
 
 // Row i of C: products a_ik * b_kj in ascending k (row i of A) then ascending
 // j (row k of B); each column's sum starts at 0.0 and adds them in that
-// order. Columns kept sorted by insertion.
+// order. Columns kept sorted by insertion. This thread-per-row form takes
+// the rows with at most kSpShort products; k_spgemm_rows_warp the others.
+constexpr int kSpShort = 96;
+
 __global__ void k_spgemm_rows(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
                               const double* __restrict__ Aval, const int* __restrict__ Brp,
                               const int* __restrict__ Bcol, const double* __restrict__ Bval,
-                              const int* __restrict__ off, int* __restrict__ ccol,
-                              double* __restrict__ cval, int* __restrict__ cnt) {
+                              const int* __restrict__ off, const int* __restrict__ ub,
+                              int* __restrict__ ccol, double* __restrict__ cval,
+                              int* __restrict__ cnt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || ub[i] > kSpShort) return;
   int* cc = ccol + off[i];
   double* cv = cval + off[i];
   int u = 0;
@@ -607,6 +625,7 @@ __global__ void __launch_bounds__(32 * kSpWarps) k_spgemm_rows_warp(
   const int i = blockIdx.x * kSpWarps + w;
   if (i >= n) return;
   const int ex = ub[i];
+  if (ex <= kSpShort) return;  // done by the thread-per-row kernel
   int* cc = ccol + off[i];
   double* cv = cval + off[i];
   if (ex > kSpCap) {
@@ -886,6 +905,9 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   int* ccol = scratch.alloc<int>(tot + 1);
   double* cval = scratch.alloc<double>(tot + 1);
   int* cnt = scratch.alloc<int>(n + 1);
+  k_spgemm_rows<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                 B.val, off, ub, ccol, cval, cnt);
+  TP_LAUNCH_CHECK();
   k_spgemm_rows_warp<<<(n + kSpWarps - 1) / kSpWarps, 32 * kSpWarps, 0, s>>>(
       n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
@@ -1029,6 +1051,10 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
       P.nnz = (int)scan_exclusive(cnt, P.rowptr, n, scratch, s);
       P.col = pool.alloc<int>(P.nnz);
       P.val = pool.alloc<double>(P.nnz);
+      k_extpi_fill_short<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, cur.dpos,
+                                                         cur.strong, cur.cf, cidx, off, buf,
+                                                         P.rowptr, P.col, P.val);
+      TP_LAUNCH_CHECK();
       k_extpi_fill_warp<<<(n + kFillWarps - 1) / kFillWarps, 32 * kFillWarps, 0, s>>>(
           n, A.rowptr, A.col, A.val, cur.dpos, cur.strong, cur.cf, cidx, off, buf, P.rowptr,
           P.col, P.val);

@@ -90,7 +90,7 @@ tp::AmgOpts amg_opts(const tp_precond_opts& o) {
 }
 
 void check_opts(const tp_precond_opts& o) {
-  if (o.schur != 0 && o.schur != 2) fail(TP_EINVAL, "schur must be 0 (S~_T) or 2 (A_TT)");
+  if (o.schur < 0 || o.schur > 2) fail(TP_EINVAL, "schur must be 0 (S~_T), 1 (learned) or 2 (A_TT)");
   if (o.variant != 0 && o.variant != 1) fail(TP_EINVAL, "variant must be 0 or 1");
   if (o.precision != 0 && o.precision != 1) fail(TP_EINVAL, "precision must be 0 or 1");
   if (o.interp != 0 && o.interp != 1) fail(TP_EINVAL, "interp must be 0 or 1");
@@ -123,6 +123,39 @@ struct tp_amg {
     h.reset();
     pool.release();
     if (own_stream && s) cudaStreamDestroy(s);
+  }
+};
+
+struct tp_mlp {
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  tp::Pool pool;
+  tp::MlpDev m;
+  tp::Pool stage;  // device copies of host inputs
+  int cap = 0;
+  float* X = nullptr;
+  int* slot = nullptr;
+  double *St = nullptr, *Sd = nullptr, *tgt = nullptr;
+  float* O = nullptr;
+  float* partials = nullptr;
+  double* host = nullptr;  // pinned [kMlpPartial]
+  ~tp_mlp() {
+    stage.release();
+    pool.release();
+    if (host) cudaFreeHost(host);
+    if (own_stream && s) cudaStreamDestroy(s);
+  }
+  void ensure(int n) {
+    if (n <= cap) return;
+    stage.release();
+    cap = n;
+    X = stage.alloc<float>((size_t)n * tp::kMlpIn);
+    slot = stage.alloc<int>(n);
+    St = stage.alloc<double>(n);
+    Sd = stage.alloc<double>(n);
+    tgt = stage.alloc<double>(n);
+    O = stage.alloc<float>((size_t)n * tp::kMlpOut);
+    partials = stage.alloc<float>((size_t)((n + 15) / 16) * tp::kMlpPartial);
   }
 };
 
@@ -596,6 +629,204 @@ int tp_export_level(tp_ctx* c, int which, int level, int* rowptr, int* col, doub
                       strong, P_nnz, P_rowptr, P_col, P_val);
 }
 
+int tp_mlp_create(tp_mlp** out, const double* params, void* cuda_stream) {
+  if (!out || !params) return TP_EINVAL;
+  *out = nullptr;
+  tp_mlp* a = nullptr;
+  TP_API_BEGIN
+  a = new tp_mlp();
+  if (cuda_stream) {
+    a->s = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    TP_CUDA_TRY(cudaStreamCreate(&a->s));
+    a->own_stream = true;
+  }
+  tp::MlpDev& m = a->m;
+  m.params = a->pool.alloc<float>(tp::kMlpParams);
+  m.adam_m = a->pool.alloc<float>(tp::kMlpParams);
+  m.adam_v = a->pool.alloc<float>(tp::kMlpParams);
+  m.grad = a->pool.alloc<float>(tp::kMlpPartial);
+  m.W1 = a->pool.alloc<__nv_bfloat16>(tp::kMlpHidden * tp::kMlpInPad);
+  m.W2 = a->pool.alloc<__nv_bfloat16>(tp::kMlpHidden * tp::kMlpHidden);
+  m.W3 = a->pool.alloc<__nv_bfloat16>(tp::kMlpOut * tp::kMlpHidden);
+  m.W2T = a->pool.alloc<__nv_bfloat16>(tp::kMlpHidden * tp::kMlpHidden);
+  m.W3T = a->pool.alloc<__nv_bfloat16>(tp::kMlpHidden * 16);
+  TP_CUDA_TRY(cudaMallocHost(&a->host, sizeof(double) * tp::kMlpPartial));
+  *out = a;
+  int st = tp_mlp_set_params(a, params);
+  if (st != TP_OK) {
+    *out = nullptr;
+    delete a;
+  }
+  return st;
+  }
+  catch (const Error& e) {
+    g_last_error = e.what;
+    cudaGetLastError();
+    delete a;
+    return e.code;
+  }
+  catch (...) {
+    delete a;
+    return TP_ECUDA;
+  }
+}
+
+void tp_mlp_destroy(tp_mlp* a) {
+  if (!a) return;
+  cudaStreamSynchronize(a->s);
+  delete a;
+}
+
+int tp_mlp_set_params(tp_mlp* a, const double* params) {
+  if (!a || !params) return TP_EINVAL;
+  TP_API_BEGIN
+  std::vector<float> f(tp::kMlpParams);
+  for (int k = 0; k < tp::kMlpParams; ++k) {
+    if (!std::isfinite(params[k])) return TP_ENONFINITE;
+    f[k] = (float)params[k];
+  }
+  TP_CUDA_TRY(cudaMemcpyAsync(a->m.params, f.data(), sizeof(float) * tp::kMlpParams,
+                              cudaMemcpyHostToDevice, a->s));
+  TP_CUDA_TRY(cudaMemsetAsync(a->m.adam_m, 0, sizeof(float) * tp::kMlpParams, a->s));
+  TP_CUDA_TRY(cudaMemsetAsync(a->m.adam_v, 0, sizeof(float) * tp::kMlpParams, a->s));
+  a->m.step = 0;
+  tp::mlp_pack(a->m, a->s);
+  TP_CUDA_TRY(cudaStreamSynchronize(a->s));
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_mlp_get_params(tp_mlp* a, double* params) {
+  if (!a || !params) return TP_EINVAL;
+  TP_API_BEGIN
+  std::vector<float> f(tp::kMlpParams);
+  TP_CUDA_TRY(cudaMemcpyAsync(f.data(), a->m.params, sizeof(float) * tp::kMlpParams,
+                              cudaMemcpyDeviceToHost, a->s));
+  TP_CUDA_TRY(cudaStreamSynchronize(a->s));
+  for (int k = 0; k < tp::kMlpParams; ++k) params[k] = f[k];
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_mlp_forward(tp_mlp* a, int n, const float* X, float* O, int ptr_is_device) {
+  if (!a || n < 0 || (n > 0 && (!X || !O))) return TP_EINVAL;
+  TP_API_BEGIN
+  if (n == 0) return TP_OK;
+  const float* Xd = X;
+  float* Od = O;
+  if (!ptr_is_device) {
+    a->ensure(n);
+    TP_CUDA_TRY(cudaMemcpyAsync(a->X, X, sizeof(float) * n * tp::kMlpIn, cudaMemcpyHostToDevice, a->s));
+    Xd = a->X;
+    Od = a->O;
+  }
+  tp::mlp_forward(a->m, n, Xd, Od, a->s);
+  if (!ptr_is_device)
+    TP_CUDA_TRY(cudaMemcpyAsync(O, a->O, sizeof(float) * n * tp::kMlpOut, cudaMemcpyDeviceToHost, a->s));
+  TP_CUDA_TRY(cudaStreamSynchronize(a->s));
+  return TP_OK;
+  TP_API_END
+}
+
+static int mlp_grad_common(tp_mlp* a, int B, const float* X, const int* slot, const double* St,
+                           const double* Sd, const double* tgt, int ptr_is_device) {
+  a->ensure(B);
+  if (ptr_is_device) {
+    TP_CUDA_TRY(cudaMemcpyAsync(a->X, X, sizeof(float) * B * tp::kMlpIn, cudaMemcpyDeviceToDevice, a->s));
+  } else {
+    TP_CUDA_TRY(cudaMemcpyAsync(a->X, X, sizeof(float) * B * tp::kMlpIn, cudaMemcpyHostToDevice, a->s));
+  }
+  cudaMemcpyKind k = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  TP_CUDA_TRY(cudaMemcpyAsync(a->slot, slot, sizeof(int) * B, k, a->s));
+  TP_CUDA_TRY(cudaMemcpyAsync(a->St, St, sizeof(double) * B, k, a->s));
+  TP_CUDA_TRY(cudaMemcpyAsync(a->Sd, Sd, sizeof(double) * B, k, a->s));
+  TP_CUDA_TRY(cudaMemcpyAsync(a->tgt, tgt, sizeof(double) * B, k, a->s));
+  tp::mlp_gradient(a->m, B, a->X, a->slot, a->St, a->Sd, a->tgt, a->partials, a->m.grad, a->s);
+  return TP_OK;
+}
+
+int tp_mlp_gradient(tp_mlp* a, int B, const float* X, const int* slot, const double* St,
+                    const double* Sd, const double* target, double* grad, double* loss,
+                    int ptr_is_device) {
+  if (!a || B < 1 || !X || !slot || !St || !Sd || !target) return TP_EINVAL;
+  TP_API_BEGIN
+  mlp_grad_common(a, B, X, slot, St, Sd, target, ptr_is_device);
+  std::vector<float> f(tp::kMlpPartial);
+  TP_CUDA_TRY(cudaMemcpyAsync(f.data(), a->m.grad, sizeof(float) * tp::kMlpPartial,
+                              cudaMemcpyDeviceToHost, a->s));
+  TP_CUDA_TRY(cudaStreamSynchronize(a->s));
+  if (grad)
+    for (int k = 0; k < tp::kMlpParams; ++k) grad[k] = f[k];
+  if (loss) *loss = f[tp::kMlpParams];
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_mlp_train_step(tp_mlp* a, int B, const float* X, const int* slot, const double* St,
+                      const double* Sd, const double* target, double lr, double* loss,
+                      int ptr_is_device) {
+  if (!a || B < 1 || !X || !slot || !St || !Sd || !target || !(lr > 0.0)) return TP_EINVAL;
+  TP_API_BEGIN
+  mlp_grad_common(a, B, X, slot, St, Sd, target, ptr_is_device);
+  tp::mlp_adam(a->m, a->m.grad, (float)lr, a->s);
+  float l = 0.f;
+  TP_CUDA_TRY(cudaMemcpyAsync(&l, a->m.grad + tp::kMlpParams, sizeof(float), cudaMemcpyDeviceToHost, a->s));
+  TP_CUDA_TRY(cudaStreamSynchronize(a->s));
+  if (loss) *loss = l;
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_learned_features(tp_ctx* c, float* X, int ptr_is_device) {
+  if (!c || !X) return TP_EINVAL;
+  if (!c->assembled) return TP_ESTATE;
+  TP_API_BEGIN
+  tp::learned_features(c);
+  TP_CUDA_TRY(cudaMemcpyAsync(X, c->feat, sizeof(float) * (size_t)c->N * tp::kMlpIn,
+                              ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  TP_CUDA_TRY(cudaStreamSynchronize(c->s));
+  return TP_OK;
+  TP_API_END
+}
+
+int tp_set_schur_model(tp_ctx* c, tp_mlp* model) {
+  if (!c) return TP_EINVAL;
+  c->model = model;
+  c->built = false;
+  return TP_OK;
+}
+
+int tp_learned_status(tp_ctx* c, int* fallback_rows, int* global_fallback) {
+  if (!c) return TP_EINVAL;
+  if (fallback_rows) *fallback_rows = c->learned_fallback_rows;
+  if (global_fallback) *global_fallback = c->learned_global_fallback ? 1 : 0;
+  return TP_OK;
+}
+
+int tp_probe_schur_columns(tp_ctx* c, const int* cols, int ncols, double rtol, int* entry,
+                           double* value, int* iters) {
+  if (!c || !cols || ncols < 0 || !entry || !value || !(rtol > 0.0)) return TP_EINVAL;
+  if (!c->built) return TP_ESTATE;
+  TP_API_BEGIN
+  int* d_entry = reinterpret_cast<int*>(c->io2);
+  double* d_val = c->io3;
+  int total = 0, status = TP_OK;
+  for (int q = 0; q < ncols; ++q) {
+    const int j = cols[q];
+    if (j < 0 || j >= c->N) return TP_EINVAL;
+    const int its = tp::probe_schur_column(c, j, rtol, 500, d_entry, d_val);
+    if (its < 0) status = TP_NOT_CONVERGED;
+    total += its < 0 ? -its : its;
+    TP_CUDA_TRY(cudaMemcpyAsync(entry + 7 * q, d_entry, 7 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    TP_CUDA_TRY(cudaMemcpyAsync(value + 7 * q, d_val, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  }
+  TP_CUDA_TRY(cudaStreamSynchronize(c->s));
+  if (iters) *iters = total;
+  return status;
+  TP_API_END
+}
+
 int tp_amg_create(tp_amg** out, int n, int nnz, const int* rowptr, const int* col,
                   const double* val, const tp_precond_opts* opts, void* cuda_stream,
                   int ptr_is_device) {
@@ -695,6 +926,8 @@ int tp_amg_export_level(tp_amg* a, int level, int* rowptr, int* col, double* val
 // ------------------------------------------------------------ device steps
 namespace tp {
 
+void learned_schur_values(tp_ctx* c);
+
 int assemble_device(tp_ctx* c, double dt) {
   cudaStream_t s = c->s;
   const long long n = c->N;
@@ -716,7 +949,38 @@ int assemble_device(tp_ctx* c, double dt) {
   TP_LAUNCH_CHECK();
   if (read_flags(flags, s)) return TP_ENONFINITE;
   c->assembled = true;
+  c->dt_last = dt;
   return TP_OK;
+}
+
+// features -> MLP -> corrected S~ with the per-row guard; more than a quarter
+// of the rows falling back switches the whole matrix back to plain S~
+void learned_features(tp_ctx* c) {
+  cudaStream_t s = c->s;
+  if (!c->feat) {
+    c->feat = c->lpool.alloc<float>((size_t)c->N * kMlpIn);
+    c->mlp_out = c->lpool.alloc<float>((size_t)c->N * kMlpOut);
+    c->S_learned = c->lpool.alloc<double>(c->nnzb);
+    c->nbad = c->lpool.alloc<int>(1);
+  }
+  launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+  launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
+                         c->scales, s);
+  launch_features(c->grid, c->fluid, c->dpos, c->Kx, c->Ky, c->Kz, c->phi, c->kT, c->p, c->T,
+                  c->rho, c->lam, c->lam_p, c->lam_T, c->bval, c->Sval, c->scales, c->dt_last,
+                  c->feat, s);
+}
+
+void learned_schur_values(tp_ctx* c) {
+  if (!c->model) fail(TP_ESTATE, "schur = 1 needs a model (tp_set_schur_model)");
+  cudaStream_t s = c->s;
+  learned_features(c);
+  mlp_forward(c->model->m, c->N, c->feat, c->mlp_out, s);
+  TP_CUDA_TRY(cudaMemsetAsync(c->nbad, 0, sizeof(int), s));
+  learned_schur(c->N, c->grid.nx, c->grid.ny, c->rowptr, c->col, c->dpos, c->Sval, c->mlp_out,
+                c->S_learned, c->nbad, s);
+  c->learned_fallback_rows = read_flags(c->nbad, s);
+  c->learned_global_fallback = 4ll * c->learned_fallback_rows > c->N;
 }
 
 void build_device(tp_ctx* c, const tp_precond_opts& o) {
@@ -730,6 +994,10 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
   launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
                          c->scales, s);
   c->S_active = (o.schur == 2) ? c->ATT : c->Sval;
+  if (o.schur == 1) {
+    learned_schur_values(c);
+    c->S_active = c->learned_global_fallback ? c->Sval : c->S_learned;
+  }
   DevCSR App{c->N, c->N, c->nnzb, c->rowptr, c->col, c->App, nullptr};
   DevCSR S{c->N, c->N, c->nnzb, c->rowptr, c->col, c->S_active, nullptr};
   c->opts = o;
@@ -776,6 +1044,12 @@ void refresh_device(tp_ctx* c) {
   cudaStream_t s = c->s;
   // A_pp and (for schur = 2) A_TT planes are the level-0 values in place
   launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+  if (c->opts.schur == 1) {
+    learned_schur_values(c);
+    if (c->learned_global_fallback)
+      TP_CUDA_TRY(cudaMemcpyAsync(c->S_learned, c->Sval, sizeof(double) * c->nnzb,
+                                  cudaMemcpyDeviceToDevice, s));
+  }
   c->hpp->refresh(s);
   c->hS->refresh(s);
 }

@@ -302,7 +302,78 @@ __global__ void k_scales(int N, const double* __restrict__ sums, double* __restr
   }
 }
 
+// 24 learned-correction features per cell (FP32 [N][24]):
+// 0-5 log10(T_f/1e-12), 6-11 log10(Tc_f), 12 log10(lam/1e6), 13-18 outward
+// advective face coefficient / S~_ii, 19 A_pT A_Tp / (A_pp A_TT) at the
+// diagonal, 20 log10(A_pp,ii s_m), 21 log10(A_TT,ii s_e),
+// 22 (A_TT,ii - S~_ii) / S~_ii, 23 accumulation / S~_ii.
+__global__ void __launch_bounds__(128) k_features(
+    GridDev g, FluidDev f, const int* __restrict__ dpos, const double* __restrict__ Kx,
+    const double* __restrict__ Ky, const double* __restrict__ Kz, const double* __restrict__ phi,
+    const double* __restrict__ kT, const double* __restrict__ p, const double* __restrict__ T,
+    const double* __restrict__ rho, const double* __restrict__ lam,
+    const double* __restrict__ lam_p, const double* __restrict__ lam_T,
+    const double* __restrict__ bval, const double* __restrict__ Sval,
+    const double* __restrict__ scales, double dt, float* __restrict__ F) {
+  const int N = g.nx * g.ny * g.nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int nxy = g.nx * g.ny;
+  const int x = i % g.nx, y = (i / g.nx) % g.ny, z = i / nxy;
+  const int d = dpos[i];
+  const double Sd = Sval[d];
+  float* out = F + (size_t)i * 24;
+  const int nb[6] = {i - nxy, i - g.nx, i - 1, i + 1, i + g.nx, i + nxy};
+  const bool has[6] = {z > 0, y > 0, x > 0, x < g.nx - 1, y < g.ny - 1, z < g.nz - 1};
+  const int axis[6] = {2, 1, 0, 0, 1, 2};
+#pragma unroll 1
+  for (int q = 0; q < 6; ++q) {
+    if (!has[q]) {
+      out[q] = 0.f;
+      out[6 + q] = 0.f;
+      out[13 + q] = 0.f;
+      continue;
+    }
+    const int j = nb[q];
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    const int ax = axis[q];
+    const double area_over_d = ax == 0 ? (g.dy * g.dz) / g.dx
+                               : ax == 1 ? (g.dx * g.dz) / g.dy
+                                         : (g.dx * g.dy) / g.dz;
+    const double* K = ax == 0 ? Kx : ax == 1 ? Ky : Kz;
+    const double dzf = ax == 2 ? g.dz : 0.0;
+    Face o;
+    face_terms(lo, hi, area_over_d, K[lo], K[hi], kT[lo], kT[hi], dzf, p, T, rho, lam, lam_p,
+               lam_T, f, g.g, o);
+    const double Tf = area_over_d * (2.0 * K[lo] * K[hi] / (K[lo] + K[hi]));
+    out[q] = (float)log10(Tf / 1e-12);
+    out[6 + q] = (float)log10(o.Tcf);
+    out[13 + q] = (float)((i == lo ? o.adv : -o.adv) / Sd);
+  }
+  const double4_32a b = reinterpret_cast<const double4_32a*>(bval)[d];
+  out[12] = (float)log10(lam[i] / 1e6);
+  out[19] = (float)(b.y * b.z / (b.x * b.w));
+  out[20] = (float)log10(fabs(b.x) * scales[0]);
+  out[21] = (float)log10(fabs(b.w) * scales[1]);
+  out[22] = (float)((b.w - Sd) / Sd);
+  const double V = g.dx * g.dy * g.dz;
+  const double ph = phi[i];
+  out[23] = (float)(V * (ph * f.cv * rho[i] + (1.0 - ph) * f.rho_r * f.cr) / dt / Sd);
+}
+
 }  // namespace
+
+void launch_features(const GridDev& g, const FluidDev& f, const int* dpos, const double* Kx,
+                     const double* Ky, const double* Kz, const double* phi, const double* kT,
+                     const double* p, const double* T, const double* rho, const double* lam,
+                     const double* lam_p, const double* lam_T, const double* bval,
+                     const double* Sval, const double* scales, double dt, float* F,
+                     cudaStream_t s) {
+  int N = g.nx * g.ny * g.nz;
+  k_features<<<grid_for(N, 128), 128, 0, s>>>(g, f, dpos, Kx, Ky, Kz, phi, kT, p, T, rho, lam,
+                                              lam_p, lam_T, bval, Sval, scales, dt, F);
+  TP_LAUNCH_CHECK();
+}
 
 void launch_pattern(const GridDev& g, int* rowptr, int* col, int* dpos, cudaStream_t s) {
   int N = g.nx * g.ny * g.nz;

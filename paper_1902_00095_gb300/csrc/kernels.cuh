@@ -50,6 +50,14 @@ void launch_equation_scales(int N, const int* dpos, const double* App, const dou
                             double* tmp, double* partials, int nparts, double* scales,
                             cudaStream_t s);
 
+// learned-correction features (FP32 [N][24]) at the last assembly
+void launch_features(const GridDev& g, const FluidDev& f, const int* dpos, const double* Kx,
+                     const double* Ky, const double* Kz, const double* phi, const double* kT,
+                     const double* p, const double* T, const double* rho, const double* lam,
+                     const double* lam_p, const double* lam_T, const double* bval,
+                     const double* Sval, const double* scales, double dt, float* F,
+                     cudaStream_t s);
+
 // ------------------------------------------------------ sparse kernels
 // y = D A x for the block matrix; D = diag(scales[0], scales[1]) or identity
 // when scales == nullptr. Split vectors.

@@ -345,7 +345,182 @@ void ensure_workspace(tp_ctx* c, int restart) {
   c->restart_alloc = restart;
 }
 
+// y = A x (scalar CSR, one thread per row)
+__global__ void k_csr_spmv(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ x,
+                           double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) a += val[e] * x[col[e]];
+  y[i] = a;
+}
+
+// r = b - A x with partial ||r||^2 over a fixed block partition
+__global__ void __launch_bounds__(256) k_csr_residual(int n, const int* __restrict__ rp,
+                                                      const int* __restrict__ col,
+                                                      const double* __restrict__ val,
+                                                      const double* __restrict__ x,
+                                                      const double* __restrict__ b,
+                                                      double* __restrict__ r,
+                                                      double* __restrict__ partials) {
+  long long lo, hi;
+  chunk_of(n, lo, hi);
+  double s = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double a = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) a += val[e] * x[col[e]];
+    const double v = b[i] - a;
+    r[i] = v;
+    s += v * v;
+  }
+  block_sum_store(s, &partials[blockIdx.x]);
+}
+
+// column j of A_pT as a dense vector (rows of column j = rows of row j's
+// pattern, the pattern being symmetric)
+__global__ void k_column_rhs(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                             const double* __restrict__ ApT, int j, double* __restrict__ rhs) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) rhs[i] = 0.0;
+}
+
+__global__ void k_column_fill(const int* __restrict__ rp, const int* __restrict__ col,
+                              const double* __restrict__ ApT, int j, double* __restrict__ rhs) {
+  const int q = threadIdx.x;
+  const int e_j = rp[j] + q;
+  if (e_j >= rp[j + 1]) return;
+  const int i = col[e_j];
+  for (int e = rp[i]; e < rp[i + 1]; ++e)
+    if (col[e] == j) rhs[i] = ApT[e];
+}
+
+// S_ij = A_TT[i][j] - (A_Tp z)_i for the rows i of column j; writes the
+// pattern entry index of (i, j) and the value
+__global__ void k_column_schur(const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ ATp, const double* __restrict__ ATT,
+                               int j, const double* __restrict__ z, int* __restrict__ entry,
+                               double* __restrict__ value) {
+  const int q = threadIdx.x;
+  if (q >= 7) return;
+  const int e_j = rp[j] + q;
+  if (e_j >= rp[j + 1]) {
+    entry[q] = -1;
+    value[q] = 0.0;
+    return;
+  }
+  const int i = col[e_j];
+  double a = 0.0;
+  int eij = -1;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    a += ATp[e] * z[col[e]];
+    if (col[e] == j) eij = e;
+  }
+  entry[q] = eij;
+  value[q] = ATT[eij] - a;
+}
+
 }  // namespace
+
+// FGMRES(restart) on a scalar CSR system A x = b, right-preconditioned by
+// one V-cycle of h, x0 = 0, stop at ||b - A x|| <= rtol ||b||. Uses the
+// context's Krylov workspace. Returns the iteration count (negative when
+// rtol was not reached within maxit).
+int scalar_fgmres(tp_ctx* c, Hierarchy& h, const DevCSR& A, const double* b, double* x,
+                  double rtol, int maxit, int restart) {
+  cudaStream_t s = c->s;
+  ensure_workspace(c, restart);
+  const int n = A.n;
+  const int B = c->nparts;
+  const int ldh = restart + 1;
+  double* hp_host = c->host_est;
+  double* r = c->w;
+  TP_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  k_csr_residual<<<B, 256, 0, s>>>(n, A.rowptr, A.col, A.val, x, b, r, c->kparts);
+  TP_LAUNCH_CHECK();
+  k_sum_to<<<1, 256, 0, s>>>(c->kparts, B, c->hn + 2);
+  TP_LAUNCH_CHECK();
+  const double bnorm = std::sqrt(read_double(c->hn + 2, hp_host, s));
+  if (bnorm == 0.0) return 0;
+  int its = 0;
+  double beta = bnorm;
+  TP_CUDA_TRY(cudaMemcpyAsync(c->hn, c->hn + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  k_sqrt_inplace<<<1, 32, 0, s>>>(c->hn);
+  TP_LAUNCH_CHECK();
+  while (true) {
+    if (beta <= rtol * bnorm) return its;
+    if (its >= maxit) return -its;
+    k_start_cycle<<<grid_for(n), kBlock, 0, s>>>(n, r, c->hn, c->Vb, c->g, restart);
+    TP_LAUNCH_CHECK();
+    int m = 0;
+    for (int j = 0; j < restart; ++j) {
+      double* vj = c->Vb + (long long)j * n;
+      double* zj = c->Zb + (long long)j * n;
+      TP_CUDA_TRY(cudaMemcpyAsync(h.in, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      h.vcycle(s);
+      TP_CUDA_TRY(cudaMemcpyAsync(zj, h.out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      k_csr_spmv<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, A.val, zj, c->w);
+      TP_LAUNCH_CHECK();
+      double* h1 = c->h2;
+      double* h2 = c->h2 + (restart + 2);
+      mdot_all(n, c->Vb, n, j + 1, c->w, c->kparts, B, h1, s);
+      k_orth_update<<<B, 256, 0, s>>>(n, c->Vb, n, j + 1, h1, c->w, nullptr);
+      TP_LAUNCH_CHECK();
+      mdot_all(n, c->Vb, n, j + 1, c->w, c->kparts, B, h2, s);
+      double* npart = c->kparts + (long long)(restart + 2) * B;
+      k_orth_update<<<B, 256, 0, s>>>(n, c->Vb, n, j + 1, h2, c->w, npart);
+      TP_LAUNCH_CHECK();
+      k_arnoldi<<<1, 32, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, npart, B, c->hn,
+                                 c->est);
+      TP_LAUNCH_CHECK();
+      TP_CUDA_TRY(cudaMemcpyAsync(hp_host, c->est, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      TP_CUDA_TRY(cudaStreamSynchronize(s));
+      ++its;
+      m = j + 1;
+      if (!std::isfinite(hp_host[0]) || !(hp_host[2] > 0.0)) {
+        m = j;
+        break;
+      }
+      if (hp_host[0] <= rtol * bnorm || its >= maxit || hp_host[1] == 0.0) break;
+      k_normalize<<<grid_for(n), kBlock, 0, s>>>(n, c->w, c->hn, c->Vb + (long long)(j + 1) * n);
+      TP_LAUNCH_CHECK();
+    }
+    if (m > 0) {
+      k_hsolve<<<1, 32, 0, s>>>(m, ldh, c->H, c->g, c->yv);
+      TP_LAUNCH_CHECK();
+      k_update_x<<<grid_for(n), kBlock, 0, s>>>(n, c->Zb, n, m, c->yv, x);
+      TP_LAUNCH_CHECK();
+    } else {
+      return -its;
+    }
+    k_csr_residual<<<B, 256, 0, s>>>(n, A.rowptr, A.col, A.val, x, b, r, c->kparts);
+    TP_LAUNCH_CHECK();
+    k_sum_to<<<1, 256, 0, s>>>(c->kparts, B, c->hn);
+    TP_LAUNCH_CHECK();
+    k_sqrt_inplace<<<1, 32, 0, s>>>(c->hn);
+    TP_LAUNCH_CHECK();
+    beta = read_double(c->hn, hp_host, s);
+    if (!std::isfinite(beta)) return -its;
+  }
+}
+
+// Exact Schur complement column j restricted to the pattern (Eq. Afact):
+// z = A_pp^{-1} A_pT e_j by scalar FGMRES, then S_ij = A_TT e_j - A_Tp z.
+int probe_schur_column(tp_ctx* c, int j, double rtol, int maxit, int* entry, double* value) {
+  cudaStream_t s = c->s;
+  const int N = c->N;
+  double* rhs = c->io0;
+  double* z = c->io1;
+  k_column_rhs<<<grid_for(N), kBlock, 0, s>>>(N, c->rowptr, c->col, c->ApT, j, rhs);
+  TP_LAUNCH_CHECK();
+  k_column_fill<<<1, 32, 0, s>>>(c->rowptr, c->col, c->ApT, j, rhs);
+  TP_LAUNCH_CHECK();
+  DevCSR A{N, N, c->nnzb, c->rowptr, c->col, c->App, nullptr};
+  int its = scalar_fgmres(c, *c->hpp, A, rhs, z, rtol, maxit, 30);
+  k_column_schur<<<1, 32, 0, s>>>(c->rowptr, c->col, c->ATp, c->ATT, j, z, entry, value);
+  TP_LAUNCH_CHECK();
+  return its;
+}
 
 void launch_block_spmv(int N, const int* rowptr, const int* col, const double* bval,
                        const double* xp, const double* xT, double* yp, double* yT,

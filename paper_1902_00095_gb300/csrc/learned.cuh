@@ -1,0 +1,47 @@
+// Learned Schur correction: MLP parameters and launchers (internal header).
+#pragma once
+#include <cuda_bf16.h>
+#include "common.cuh"
+
+namespace tp {
+
+constexpr int kMlpIn = 24, kMlpInPad = 32, kMlpHidden = 64, kMlpOut = 8;
+// flat FP32 parameter layout: W1 [64][24], b1 [64], W2 [64][64], b2 [64],
+// W3 [8][64], b3 [8]
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpHidden * kMlpIn;
+constexpr int kOffW2 = kOffB1 + kMlpHidden;
+constexpr int kOffB2 = kOffW2 + kMlpHidden * kMlpHidden;
+constexpr int kOffW3 = kOffB2 + kMlpHidden;
+constexpr int kOffB3 = kOffW3 + kMlpOut * kMlpHidden;
+constexpr int kMlpParams = kOffB3 + kMlpOut;   // 6280
+constexpr int kMlpPartial = kMlpParams + 1;    // + loss
+
+struct MlpDev {
+  float* params = nullptr;  // FP32 master weights [kMlpParams]
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* grad = nullptr;    // [kMlpPartial]
+  __nv_bfloat16* W1 = nullptr;   // [64][32]
+  __nv_bfloat16* W2 = nullptr;   // [64][64]
+  __nv_bfloat16* W3 = nullptr;   // [8][64]
+  __nv_bfloat16* W2T = nullptr;  // [64][64]
+  __nv_bfloat16* W3T = nullptr;  // [64][16]
+  int step = 0;
+};
+
+void mlp_pack(const MlpDev& m, cudaStream_t s);
+void mlp_forward(const MlpDev& m, int n, const float* X, float* O, cudaStream_t s);
+// gradient of the mean squared relative error over B samples into grad
+// (loss in grad[kMlpParams]); partials holds ceil(B/16) * kMlpPartial floats
+void mlp_gradient(const MlpDev& m, int B, const float* X, const int* slot, const double* St,
+                  const double* Sd, const double* target, float* partials, float* grad,
+                  cudaStream_t s);
+void mlp_adam(MlpDev& m, const float* grad, float lr, cudaStream_t s);
+
+// learned S~ values on the 7-point pattern with the per-row guard; returns
+// (through *nbad, device int) the number of rows that fell back
+void learned_schur(int N, int nx, int ny, const int* rowptr, const int* col, const int* dpos,
+                   const double* S, const float* O, double* out, int* nbad, cudaStream_t s);
+
+}  // namespace tp

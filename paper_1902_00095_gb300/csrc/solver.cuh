@@ -3,6 +3,7 @@
 #include <memory>
 #include "amg.cuh"
 #include "kernels.cuh"
+#include "learned.cuh"
 
 struct tp_ctx {
   cudaStream_t s = nullptr;
@@ -56,6 +57,16 @@ struct tp_ctx {
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
          *hn = nullptr, *est = nullptr, *kparts = nullptr, *h2 = nullptr;
   double* host_est = nullptr;  // pinned
+  // learned Schur correction
+  struct tp_mlp* model = nullptr;
+  tp::Pool lpool;
+  float* feat = nullptr;      // [N][24]
+  float* mlp_out = nullptr;   // [N][8]
+  double* S_learned = nullptr;
+  int* nbad = nullptr;
+  int learned_fallback_rows = 0;
+  bool learned_global_fallback = false;
+  double dt_last = 0.0;
   // user-facing scratch for host pointer marshalling
   double *io0 = nullptr, *io1 = nullptr, *io2 = nullptr, *io3 = nullptr;
 
@@ -78,4 +89,8 @@ void refresh_device(tp_ctx* c);                          // numeric-only
 void negated_residual(tp_ctx* c);                        // io0, io1 = -G
 int newton_step(tp_ctx* c, double dt, const tp_precond_opts& popts, const tp_newton_opts& no,
                 tp_newton_info* info);
+int scalar_fgmres(tp_ctx* c, Hierarchy& h, const DevCSR& A, const double* b, double* x,
+                  double rtol, int maxit, int restart);
+int probe_schur_column(tp_ctx* c, int j, double rtol, int maxit, int* entry, double* value);
+void learned_features(tp_ctx* c);  // features of the last assembly into c->feat
 }  // namespace tp

@@ -99,6 +99,19 @@ SIGNATURES = {
     "tp_amg_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.POINTER(PrecondOpts), C.c_void_p, C.c_int]),
     "tp_amg_destroy": (None, [C.c_void_p]),
+    "tp_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p]),
+    "tp_mlp_destroy": (None, [C.c_void_p]),
+    "tp_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tp_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tp_mlp_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "tp_mlp_gradient": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 7 + [C.c_int]),
+    "tp_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 5 +
+                          [C.c_double, C.c_void_p, C.c_int]),
+    "tp_learned_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "tp_set_schur_model": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tp_learned_status": (C.c_int, [C.c_void_p, _ip, _ip]),
+    "tp_probe_schur_columns": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                         C.c_void_p, C.c_void_p, _ip]),
     "tp_equation_scales_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]),
     "tp_amg_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -294,6 +307,38 @@ class Solver:
         _check(st, "tp_newton_step", warn_ok=True)
         return keep[2], keep[3], info.as_dict()
 
+    def learned_features(self):
+        """Features of every cell at the last assemble, float32 [N, 24]."""
+        X = np.empty((self.N, 24), np.float32)
+        _check(self._lib.tp_learned_features(self._h, C.c_void_p(X.ctypes.data), 0),
+               "tp_learned_features")
+        return X
+
+    def set_schur_model(self, mlp):
+        """Model used by build(schur=1); None detaches."""
+        self._model = mlp
+        _check(self._lib.tp_set_schur_model(self._h, mlp._h if mlp is not None else None),
+               "tp_set_schur_model")
+
+    def learned_status(self):
+        rows, glob = C.c_int(), C.c_int()
+        _check(self._lib.tp_learned_status(self._h, C.byref(rows), C.byref(glob)),
+               "tp_learned_status")
+        return rows.value, bool(glob.value)
+
+    def probe_schur_columns(self, cols, rtol=1e-12):
+        """Exact Schur columns on the pattern: (entry [n, 7], value [n, 7],
+        total FGMRES iterations, status)."""
+        cols = np.ascontiguousarray(cols, np.int32)
+        entry = np.empty((cols.size, 7), np.int32)
+        value = np.empty((cols.size, 7))
+        its = C.c_int()
+        st = self._lib.tp_probe_schur_columns(self._h, C.c_void_p(cols.ctypes.data), int(cols.size),
+                                              float(rtol), C.c_void_p(entry.ctypes.data),
+                                              C.c_void_p(value.ctypes.data), C.byref(its))
+        _check(st, "tp_probe_schur_columns", warn_ok=True)
+        return entry, value, its.value, st
+
     def probe_enable(self, which):
         """Time every launch of one kernel class (0 finest A_pp sweeps,
         1 finest S~ sweeps, 2 block SpMV, -1 off) during solves; call
@@ -366,6 +411,73 @@ def _export_level(fn, n, nnz):
                   pc.ctypes.data_as(_ip), pv.ctypes.data_as(_dp)), "export_level")
         P = (prp, pc, pv)
     return dict(A=(rp, col, val), cf=cf, strong=strong.astype(bool), P=P)
+
+
+NPARAM = 6280
+
+
+class MLP:
+    """The per-cell Schur-correction network on the GPU (BF16 tensor cores,
+    FP32 master weights, Adam)."""
+
+    def __init__(self, params):
+        lib = load()
+        self._lib = lib
+        self._h = C.c_void_p()
+        p = np.ascontiguousarray(params, np.float64)
+        if p.size != NPARAM:
+            raise ValueError(f"expected {NPARAM} parameters")
+        _check(lib.tp_mlp_create(C.byref(self._h), C.c_void_p(p.ctypes.data), None),
+               "tp_mlp_create")
+
+    def close(self):
+        if self._h:
+            self._lib.tp_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(NPARAM)
+        _check(self._lib.tp_mlp_get_params(self._h, C.c_void_p(out.ctypes.data)), "tp_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float64)
+        _check(self._lib.tp_mlp_set_params(self._h, C.c_void_p(p.ctypes.data)), "tp_mlp_set_params")
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, np.float32)
+        O = np.empty((X.shape[0], 8), np.float32)
+        _check(self._lib.tp_mlp_forward(self._h, X.shape[0], C.c_void_p(X.ctypes.data),
+                                        C.c_void_p(O.ctypes.data), 0), "tp_mlp_forward")
+        return O
+
+    @staticmethod
+    def _batch(X, slot, St, Sd, target):
+        return (np.ascontiguousarray(X, np.float32), np.ascontiguousarray(slot, np.int32),
+                np.ascontiguousarray(St, np.float64), np.ascontiguousarray(Sd, np.float64),
+                np.ascontiguousarray(target, np.float64))
+
+    def gradient(self, X, slot, St, Sd, target):
+        b = self._batch(X, slot, St, Sd, target)
+        g = np.empty(NPARAM)
+        loss = C.c_double()
+        _check(self._lib.tp_mlp_gradient(self._h, b[0].shape[0], *[C.c_void_p(a.ctypes.data) for a in b],
+                                         C.c_void_p(g.ctypes.data), C.byref(loss), 0),
+               "tp_mlp_gradient")
+        return loss.value, g
+
+    def train_step(self, X, slot, St, Sd, target, lr=1e-3):
+        b = self._batch(X, slot, St, Sd, target)
+        loss = C.c_double()
+        _check(self._lib.tp_mlp_train_step(self._h, b[0].shape[0], *[C.c_void_p(a.ctypes.data) for a in b],
+                                           float(lr), C.byref(loss), 0), "tp_mlp_train_step")
+        return loss.value
 
 
 class AMG:

@@ -1,0 +1,163 @@
+"""Parity of the GPU learned Schur correction with the FP64 oracle.
+
+Tolerances: features are computed in FP64 and stored as FP32 (1e-5
+relative); the MLP runs on BF16 tensor cores with FP32 accumulation, so its
+outputs and gradients are compared at 2e-2 of their scale; exact Schur
+columns come from FGMRES solves at rtol 1e-12 (1e-7 relative)."""
+import numpy as np
+import pytest
+
+from oracle import krylov as okry
+from oracle import learned as olearn
+from oracle import physics as ophys
+from synthetic import make_problem
+from synthetic.configs import perturbed_state
+from synthetic.mlp import flatten, initial_params, unflatten
+
+pytestmark = pytest.mark.gpu
+
+thermo = pytest.importorskip("paper_1902_00095_gb300.thermo")
+
+
+def problem(shape=(12, 10, 6), seed=4):
+    prob = make_problem("tiny", shape=shape, seed=seed)
+    p, T = perturbed_state(prob, seed=seed)
+    prob["p_n"] = prob["p_n"] + 3e4
+    return prob, p, T
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    P = initial_params(seed)
+    P["W3"] = rng.normal(0, 0.2, P["W3"].shape)
+    P["b1"] = rng.normal(0, 0.1, P["b1"].shape)
+    P["b2"] = rng.normal(0, 0.1, P["b2"].shape)
+    P["b3"] = rng.normal(0, 0.05, P["b3"].shape)
+    return P
+
+
+def test_features_match_oracle():
+    prob, p, T = problem()
+    s = thermo.Solver.from_problem(prob)
+    s.assemble(p, T, prob["p_n"], prob["T_n"], prob["dt"])
+    X = s.learned_features().astype(np.float64)
+    rowptr, col, val = ophys.jacobian(prob, p, T)
+    _, _, S = ophys.schur_approx(prob, p, T)
+    Xo = olearn.features(prob, p, T, val, S)
+    scale = np.maximum(np.abs(Xo).max(axis=0), 1e-30)
+    assert np.all(np.abs(X - Xo) <= 1e-5 * scale + 1e-6 * np.abs(Xo))
+
+
+def test_mlp_forward_matches_oracle():
+    P = random_params(3)
+    mlp = thermo.MLP(flatten(P))
+    X = np.random.default_rng(1).normal(0, 1, (1000, 24))
+    O = mlp.forward(X).astype(np.float64)
+    Oo, _ = olearn.forward(P, X)
+    assert np.max(np.abs(O - Oo)) <= 2e-2 * np.max(np.abs(Oo))
+    # the parameters round-trip through FP32
+    assert np.allclose(mlp.params(), flatten(P), rtol=1e-6, atol=1e-7)
+
+
+def _batch(seed, B=777):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, (B, 24))
+    slot = rng.integers(0, 7, B)
+    Sd = rng.uniform(1, 2, B)
+    St = np.where(slot == 0, Sd, -rng.uniform(0.05, 0.3, B))
+    target = St * rng.uniform(0.7, 1.3, B)
+    return X, slot, St, Sd, target
+
+
+def test_mlp_gradients_match_oracle():
+    P = random_params(5)
+    mlp = thermo.MLP(flatten(P))
+    X, slot, St, Sd, target = _batch(2)
+    loss, g = mlp.gradient(X, slot, St, Sd, target)
+    lo, go = olearn.loss_and_grads(P, X, slot, St, Sd, target)
+    assert abs(loss - lo) <= 2e-2 * lo
+    G = unflatten(g)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        ref = go[k]
+        assert np.linalg.norm(G[k] - ref) <= 2e-2 * np.linalg.norm(ref), k
+
+
+def test_adam_step_matches_oracle_on_the_gpu_gradient():
+    P = random_params(6)
+    mlp = thermo.MLP(flatten(P))
+    X, slot, St, Sd, target = _batch(3)
+    _, g = mlp.gradient(X, slot, St, Sd, target)
+    mlp.train_step(X, slot, St, Sd, target, lr=1e-3)
+    new = mlp.params()
+    ref = flatten(olearn.adam_step(dict(P), unflatten(g), {}, lr=1e-3))
+    assert np.max(np.abs(new - ref)) <= 2e-6
+
+
+def test_probed_schur_columns_are_exact():
+    prob, p, T = problem((10, 9, 5), seed=7)
+    s = thermo.Solver.from_problem(prob)
+    s.assemble(p, T, prob["p_n"], prob["T_n"], prob["dt"])
+    s.build()
+    cols = np.array([0, 17, 123, s.N - 1])
+    entry, value, its, st = s.probe_schur_columns(cols, rtol=1e-12)
+    assert st == 0 and its > 0
+    rowptr, col, val = ophys.jacobian(prob, p, T)
+    ex = olearn.exact_schur_columns(rowptr, col, val, cols)
+    for q, j in enumerate(cols):
+        ref = dict(ex[int(j)])
+        got = {int(e): v for e, v in zip(entry[q], value[q]) if e >= 0}
+        assert set(got) == set(ref)
+        scale = max(abs(v) for v in ref.values())
+        for e in ref:
+            assert abs(got[e] - ref[e]) <= 1e-7 * scale
+
+
+def test_identity_network_reproduces_the_plain_solve():
+    """W3 = 0, b3 = 0: every output is 0, the corrected S~ equals S~ and the
+    solve is the plain one."""
+    prob, p, T = problem()
+    s = thermo.Solver.from_problem(prob)
+    s.assemble(p, T, prob["p_n"], prob["T_n"], prob["dt"])
+    s.build(schur=0)
+    _, _, plain = s.solve(rtol=1e-8)
+    mlp = thermo.MLP(flatten(initial_params(0)))
+    s.set_schur_model(mlp)
+    s.build(schur=1)
+    _, _, learned = s.solve(rtol=1e-8)
+    assert s.learned_status() == (0, False)
+    assert learned["iters"] == plain["iters"]
+    assert abs(learned["rel_res"] - plain["rel_res"]) <= 1e-12
+
+
+def test_guard_rejects_a_destructive_network():
+    """A network whose o_7 = -3 makes every corrected diagonal negative: all
+    rows fall back, the whole matrix reverts to plain S~ and the solve still
+    converges."""
+    prob, p, T = problem()
+    P = initial_params(0)
+    P["b3"][7] = -3.0
+    s = thermo.Solver.from_problem(prob)
+    s.assemble(p, T, prob["p_n"], prob["T_n"], prob["dt"])
+    mlp = thermo.MLP(flatten(P))
+    s.set_schur_model(mlp)
+    s.build(schur=1)
+    rows, glob = s.learned_status()
+    assert rows == s.N and glob
+    _, _, info = s.solve(rtol=1e-8)
+    assert info["status"] == 0
+
+
+def test_training_on_probed_columns_reduces_the_loss_and_solves():
+    from paper_1902_00095_gb300 import learned as L
+    rng = np.random.Generator(np.random.PCG64(0))
+    parts = []
+    for q in range(3):
+        prob = make_problem("tiny", shape=(16, 16, 8), seed=100 + q)
+        s = thermo.Solver.from_problem(prob)
+        parts.append(L.collect_samples(s, prob, 96, rng))
+        s.close()
+    data = L.concat(parts)
+    mlp, hist = L.train(data, flatten(initial_params(0)), epochs=30, batch=512, lr=3e-3)
+    assert hist[-1] < 0.7 * hist[0]
+    ev = L.evaluate(mlp, make_problem("tiny", shape=(16, 16, 8), seed=777))
+    assert ev["learned_rel_res"] <= 1e-8
