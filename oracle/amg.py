@@ -324,6 +324,41 @@ def interpolation_extpi(A, S, cf):
     return (P_rp, P_c, P_v), nc
 
 
+def truncate(P, pmax):
+    """Interpolation truncation: an F row with more than pmax entries keeps
+    the pmax largest |w| (ties to the lower column), each kept weight scaled
+    by (sum of all weights) / (sum of kept weights) so the row sum, and with
+    it the interpolation of constants, is unchanged. Sums run over the row in
+    ascending column order from 0.0; a zero kept sum leaves the kept weights
+    unscaled. pmax <= 0 disables truncation."""
+    if pmax <= 0:
+        return P
+    rp, c, v = P
+    n = rp.size - 1
+    rows = []
+    for i in range(n):
+        cols = c[rp[i]:rp[i + 1]]
+        w = v[rp[i]:rp[i + 1]]
+        if cols.size <= pmax:
+            rows.append((list(cols), list(w)))
+            continue
+        order = sorted(range(cols.size), key=lambda q: (-abs(w[q]), cols[q]))
+        keep = sorted(order[:pmax])
+        s_all = 0.0
+        for q in range(cols.size):
+            s_all = s_all + w[q]
+        s_keep = 0.0
+        for q in keep:
+            s_keep = s_keep + w[q]
+        f = s_all / s_keep if s_keep != 0.0 else 1.0
+        rows.append(([cols[q] for q in keep], [w[q] * f for q in keep]))
+    P_rp = np.zeros(n + 1, np.int64)
+    P_rp[1:] = np.cumsum([len(r[0]) for r in rows])
+    P_c = np.array([j for r in rows for j in r[0]], dtype=np.int64)
+    P_v = np.array([x for r in rows for x in r[1]], dtype=np.float64)
+    return P_rp, P_c, P_v
+
+
 def transpose(P, ncols):
     """R = P^T with ascending columns per row."""
     rp, c, v = P
@@ -394,7 +429,7 @@ def l1_diag(A):
 
 def setup(A, theta=0.25, seed=0, coarse_size=64, max_levels=25,
           max_coarse_dense=4096, smoother="l1jacobi", cheb_degree=2,
-          interp="ext+i"):
+          interp="ext+i", pmax=4):
     """Build the hierarchy. Coarsening stops when the level has at most
     coarse_size rows, when max_levels is reached, or when a split keeps
     more than 90% of the points (or none); the coarsest matrix is factored
@@ -416,6 +451,7 @@ def setup(A, theta=0.25, seed=0, coarse_size=64, max_levels=25,
             P, nc = interpolation(cur, S, cf)
         else:
             P, nc = interpolation_extpi(cur, S, cf)
+        P = truncate(P, pmax)
         R = transpose(P, nc)
         lev.update(S=S, cf=cf, rounds=rounds, P=P, R=R)
         cur = galerkin(cur, P, R)

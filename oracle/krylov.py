@@ -164,7 +164,7 @@ def assemble(prob, p=None, T=None):
 def solve(prob, rtol=1e-8, maxit=300, restart=30, theta=0.25, seed=0,
           variant="full", smoother="l1jacobi", nu_pre=2, nu_post=2,
           coarse_size=64, p=None, T=None, schur="plain", interp="ext+i",
-          interp_S="classical", cheb_degree=2):
+          interp_S="classical", cheb_degree=2, pmax=4):
     """Assemble, build the block preconditioner with one V-cycle per
     approximate inverse, and solve with FGMRES(restart) in the scaled
     system. A_pp's hierarchy uses `interp` (extended+i by default: the
@@ -176,9 +176,9 @@ def solve(prob, rtol=1e-8, maxit=300, restart=30, theta=0.25, seed=0,
     if schur == "att":
         S = sys.ATT
     h_pp = amg.setup(sys.App, theta, seed, coarse_size, smoother=smoother,
-                     interp=interp, cheb_degree=cheb_degree)
+                     interp=interp, cheb_degree=cheb_degree, pmax=pmax)
     h_S = amg.setup(S, theta, seed, coarse_size, smoother=smoother,
-                    interp=interp_S, cheb_degree=cheb_degree)
+                    interp=interp_S, cheb_degree=cheb_degree, pmax=pmax)
     sm, se = sys.s_m, sys.s_e
     V_pp = lambda r: amg.vcycle(h_pp, r, 0, nu_pre, nu_post)
     V_S = lambda r: amg.vcycle(h_S, r, 0, nu_pre, nu_post)

@@ -237,3 +237,30 @@ def test_structurally_unsymmetric_pattern_is_rejected():
     S = amg.strength(A, 0.25)
     with pytest.raises(ValueError):
         amg.pmis(A, S, 0)
+
+
+def test_truncation_keeps_the_largest_weights_and_row_sums():
+    P = (np.array([0, 1, 6]), np.array([0, 0, 1, 2, 3, 4]),
+         np.array([1.0, 0.1, -0.4, 0.3, 0.05, 0.4]))
+    T = amg.truncate(P, 3)
+    rp, c, v = T
+    assert list(rp) == [0, 1, 4]
+    assert list(c[1:]) == [1, 2, 4]   # |w| 0.4, 0.3, 0.4 kept; ties to the lower column
+    s_all = 0.1 - 0.4 + 0.3 + 0.05 + 0.4
+    s_keep = -0.4 + 0.3 + 0.4
+    assert np.allclose(v[1:], np.array([-0.4, 0.3, 0.4]) * (s_all / s_keep), rtol=0, atol=1e-15)
+    assert abs(v[1:].sum() - s_all) < 1e-15
+    assert amg.truncate(P, 0) is P
+
+
+def test_truncated_hierarchy_still_contracts():
+    A = lap2d(16, neumann=False, ay=0.3)
+    h = amg.setup(A, coarse_size=20, pmax=2)
+    for lev in h["levels"][:-1]:
+        assert np.max(np.diff(lev["P"][0])) <= 2
+    n = A[0].size - 1
+    b = np.random.default_rng(0).standard_normal(n)
+    x = np.zeros(n)
+    for _ in range(20):
+        x = x + amg.vcycle(h, b - amg.spmv(A, x))
+    assert np.linalg.norm(b - amg.spmv(A, x)) < 1e-3 * np.linalg.norm(b)
