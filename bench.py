@@ -127,7 +127,8 @@ def measured_peak():
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the probed
 # kernel, keyed by (config, probe); None until a capture of the current kernel
-TRAFFIC = {}
+TRAFFIC = {("2", 0, 0): 14.16e6,   # profiles/k_jacobi_ell_config2_64x64x32_fp64.md
+           ("3", 0, 0): 118.3e6}  # profiles/k_jacobi_ell_config3_128x128x64_fp64.md
 
 
 def cpu_baseline(seconds_target=20.0):
@@ -305,6 +306,7 @@ def run_ours(args, rank, world, local):
         "solver": {k: infos[-1][k] for k in ("iters", "restarts", "rel_res", "rel_res_unscaled",
                                               "levels_pp", "levels_S", "opc_pp", "opc_S",
                                               "t_solve_ms")},
+        "setup_ms": {"A_pp": s.setup_timings(0), "S": s.setup_timings(1)},
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

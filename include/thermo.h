@@ -98,6 +98,8 @@ typedef struct {
   int interp_S;     /* -1 same, 0 classical (default), 1 extended+i           */
   int max_levels_S; /* 0 same                                                 */
   int nu_S;         /* 0 same; else nu_pre = nu_post = nu_S                   */
+  int pmax;         /* interpolation truncation: at most pmax weights per row  */
+                    /* (largest |w|, row sums kept); default 4, 0 = off, <=16 */
 } tp_precond_opts;
 
 typedef struct {
@@ -215,6 +217,12 @@ int tp_apply_preconditioner(tp_ctx* ctx, const double* v_p, const double* v_T,
  * NULL. Also the equation scales (s_m, s_e) used by tp_solve. */
 int tp_export_system(tp_ctx* ctx, int* rowptr, int* col, double* val,
                      double* schur_val, double* scales);
+
+/* Host wall time (ms) of the last AMG setup of hierarchy which (0 A_pp,
+ * 1 Schur) by phase: ms[0] strength + PMIS, ms[1] interpolation,
+ * ms[2] transpose, ms[3] Galerkin products, ms[4] smoother scaling, ELL copy
+ * and coarsest inverse. */
+int tp_setup_timings(tp_ctx* ctx, int which, double* ms);
 
 /* Hierarchy introspection: which = 0 (A_pp) or 1 (Schur). n/nnz receive
  * up to max_levels entries. */

@@ -23,6 +23,7 @@ struct AmgOpts {
   unsigned long long seed = 0;
   int precision = 0;     // 0 FP64, 1 FP32 hierarchy
   int max_pmis_rounds = 64;
+  int pmax = 0;          // interpolation truncation (0 = off)
 };
 
 // CUDA-event timing of one kernel class inside the timed region: events are
@@ -102,6 +103,9 @@ class Hierarchy {
   int nc = 0;
   Pool pool;
   double* coarse_dense = nullptr;   // [nc*nc] work for the inverse
+  // host wall time of the setup phases (ms): strength + PMIS, interpolation,
+  // transpose, Galerkin products, smoother scaling + coarse inverse
+  double phase_ms[5] = {0, 0, 0, 0, 0};
   int* err = nullptr;
 
  private:

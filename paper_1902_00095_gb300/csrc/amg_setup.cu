@@ -8,6 +8,7 @@
 // its distance-two extended+i form; all structure-deciding arithmetic uses
 // __dmul_rn / __dadd_rn / __ddiv_rn in a fixed ascending-column order.
 #include "amg.cuh"
+#include <chrono>
 #include <cmath>
 #include <algorithm>
 
@@ -474,6 +475,67 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
   }
 }
 
+// --------------------------------------------------- interpolation truncation
+constexpr int kPmaxLimit = 16;
+
+__global__ void k_trunc_count(int n, const int* __restrict__ Prp, int pmax, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int len = Prp[i + 1] - Prp[i];
+  cnt[i] = len < pmax ? len : pmax;
+}
+
+// keep the pmax largest |w| (ties to the lower column) and scale them by
+// (sum of all) / (sum of kept), sums over the row ascending from 0.0
+__global__ void k_trunc_fill(int n, const int* __restrict__ Prp, const int* __restrict__ Pcol,
+                             const double* __restrict__ Pval, int pmax,
+                             const int* __restrict__ Trp, int* __restrict__ Tcol,
+                             double* __restrict__ Tval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p0 = Prp[i], p1 = Prp[i + 1], len = p1 - p0, t0 = Trp[i];
+  if (len <= pmax) {
+    for (int q = 0; q < len; ++q) {
+      Tcol[t0 + q] = Pcol[p0 + q];
+      Tval[t0 + q] = Pval[p0 + q];
+    }
+    return;
+  }
+  int keep[kPmaxLimit];
+  int nk = 0;
+  for (int r = 0; r < pmax; ++r) {
+    int best = -1;
+    double bw = -1.0;
+    for (int q = 0; q < len; ++q) {
+      bool taken = false;
+      for (int u = 0; u < nk; ++u) taken |= keep[u] == q;
+      if (taken) continue;
+      const double a = fabs(Pval[p0 + q]);
+      if (a > bw) {  // first maximum in column order wins ties
+        bw = a;
+        best = q;
+      }
+    }
+    keep[nk++] = best;
+  }
+  for (int a = 1; a < nk; ++a) {  // ascending position = ascending column
+    int v = keep[a], b = a - 1;
+    while (b >= 0 && keep[b] > v) {
+      keep[b + 1] = keep[b];
+      --b;
+    }
+    keep[b + 1] = v;
+  }
+  double s_all = 0.0, s_keep = 0.0;
+  for (int q = 0; q < len; ++q) s_all = __dadd_rn(s_all, Pval[p0 + q]);
+  for (int u = 0; u < nk; ++u) s_keep = __dadd_rn(s_keep, Pval[p0 + keep[u]]);
+  const double f = s_keep != 0.0 ? __ddiv_rn(s_all, s_keep) : 1.0;
+  for (int u = 0; u < nk; ++u) {
+    Tcol[t0 + u] = Pcol[p0 + keep[u]];
+    Tval[t0 + u] = s_keep != 0.0 ? __dmul_rn(Pval[p0 + keep[u]], f) : Pval[p0 + keep[u]];
+  }
+}
+
 // ------------------------------------------------------------- transpose
 __global__ void k_count_cols(int n, const int* __restrict__ rp, const int* __restrict__ col,
                              int* __restrict__ cnt) {
@@ -614,26 +676,14 @@ __device__ void spgemm_row_serial(int i, const int* __restrict__ Arp, const int*
   cnt[i] = u;
 }
 
-__global__ void __launch_bounds__(32 * kSpWarps) k_spgemm_rows_warp(
-    int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
-    const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
-    const double* __restrict__ Bval, const int* __restrict__ off, const int* __restrict__ ub,
-    int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
-  __shared__ unsigned long long s_key[kSpWarps][kSpCap];
-  __shared__ double s_val[kSpWarps][kSpCap];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kSpWarps + w;
-  if (i >= n) return;
-  const int ex = ub[i];
-  if (ex <= kSpShort) return;  // done by the thread-per-row kernel
-  int* cc = ccol + off[i];
-  double* cv = cval + off[i];
-  if (ex > kSpCap) {
-    if (lane == 0) spgemm_row_serial(i, Arp, Acol, Aval, Brp, Bcol, Bval, cc, cv, cnt);
-    return;
-  }
-  unsigned long long* key = s_key[w];
-  double* val = s_val[w];
+// one warp: products of row i staged in key/val (capacity >= ex), sorted,
+// runs summed in sequence order
+__device__ void spgemm_row_warp(int i, int ex, int lane, const int* __restrict__ Arp,
+                                const int* __restrict__ Acol, const double* __restrict__ Aval,
+                                const int* __restrict__ Brp, const int* __restrict__ Bcol,
+                                const double* __restrict__ Bval, unsigned long long* key,
+                                double* val, int* __restrict__ cc, double* __restrict__ cv,
+                                int* __restrict__ cnt) {
   // 1. products in canonical order (A row ascending, then B row ascending)
   const int a0 = Arp[i], a1 = Arp[i + 1];
   int base = 0;
@@ -707,6 +757,132 @@ __global__ void __launch_bounds__(32 * kSpWarps) k_spgemm_rows_warp(
     nrun += total;
   }
   if (lane == 0) cnt[i] = nrun;
+}
+
+// rows with kSpShort < ex <= kSpCap: two warps per block, static shared memory
+__global__ void __launch_bounds__(32 * kSpWarps) k_spgemm_rows_warp(
+    int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
+    const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
+    const double* __restrict__ Bval, const int* __restrict__ off, const int* __restrict__ ub,
+    int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
+  __shared__ unsigned long long s_key[kSpWarps][kSpCap];
+  __shared__ double s_val[kSpWarps][kSpCap];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = blockIdx.x * kSpWarps + w; i < n; i += gridDim.x * kSpWarps) {
+    const int ex = ub[i];
+    if (ex <= kSpShort || ex > kSpCap) continue;
+    spgemm_row_warp(i, ex, lane, Arp, Acol, Aval, Brp, Bcol, Bval, s_key[w], s_val[w],
+                    ccol + off[i], cval + off[i], cnt);
+    __syncwarp();
+  }
+}
+
+// rows with ex > kSpCap: one 256-thread block per row with kSpBig entries of
+// dynamic shared memory (products staged by warp 0, the bitonic sort shared
+// by all threads); rows beyond that are summed serially
+constexpr int kSpBig = 8192;
+constexpr int kSpBigThreads = 256;
+constexpr size_t kSpBigSmem = (size_t)kSpBig * (sizeof(unsigned long long) + sizeof(double));
+
+__global__ void __launch_bounds__(kSpBigThreads) k_spgemm_rows_big(
+    int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
+    const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
+    const double* __restrict__ Bval, const int* __restrict__ off, const int* __restrict__ ub,
+    int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
+  extern __shared__ unsigned long long s_big[];
+  unsigned long long* key = s_big;
+  double* val = reinterpret_cast<double*>(s_big + kSpBig);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int ex = ub[i];  // uniform over the block
+    if (ex <= kSpCap) continue;
+    int* cc = ccol + off[i];
+    double* cv = cval + off[i];
+    if (ex > kSpBig) {
+      if (tid == 0) spgemm_row_serial(i, Arp, Acol, Aval, Brp, Bcol, Bval, cc, cv, cnt);
+      __syncthreads();
+      continue;
+    }
+    // 1. products in canonical order (warp 0)
+    if (warp == 0) {
+      const int a0 = Arp[i], a1 = Arp[i + 1];
+      int base = 0;
+      for (int e0 = a0; e0 < a1; e0 += 32) {
+        const int e = e0 + lane;
+        int k = 0, len = 0;
+        if (e < a1) {
+          k = Acol[e];
+          len = Brp[k + 1] - Brp[k];
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (e < a1) {
+          const double a = Aval[e];
+          const int fb = Brp[k];
+          int pidx = base + incl - len;
+          for (int t = 0; t < len; ++t, ++pidx) {
+            key[pidx] = ((unsigned long long)(unsigned)Bcol[fb + t] << 32) | (unsigned)pidx;
+            val[pidx] = __dmul_rn(a, Bval[fb + t]);
+          }
+        }
+        base += total;
+      }
+    }
+    int P = 1;
+    while (P < ex) P <<= 1;
+    __syncthreads();
+    for (int q = ex + tid; q < P; q += kSpBigThreads) key[q] = ~0ull;
+    __syncthreads();
+    // 2. block bitonic sort
+    for (int size = 2; size <= P; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = tid; t < (P >> 1); t += kSpBigThreads) {
+          const int lo = 2 * stride * (t / stride) + (t % stride);
+          const int hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const unsigned long long x = key[lo], y = key[hi];
+          if ((x > y) == up) {
+            key[lo] = y;
+            key[hi] = x;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // 3. runs summed in sequence order (warp 0)
+    if (warp == 0) {
+      int nrun = 0;
+      for (int q0 = 0; q0 < ex; q0 += 32) {
+        const int q = q0 + lane;
+        int start = 0;
+        if (q < ex) start = (q == 0) || ((key[q] >> 32) != (key[q - 1] >> 32));
+        int incl = start;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (start) {
+          const unsigned col = (unsigned)(key[q] >> 32);
+          double sum = 0.0;
+          for (int r = q; r < ex && (unsigned)(key[r] >> 32) == col; ++r)
+            sum = __dadd_rn(sum, val[(unsigned)(key[r] & 0xffffffffu)]);
+          const int rid = nrun + incl - 1;
+          cc[rid] = (int)col;
+          cv[rid] = sum;
+        }
+        nrun += total;
+      }
+      if (lane == 0) cnt[i] = nrun;
+    }
+    __syncthreads();
+  }
 }
 
 // numeric-only C = A B on a known pattern (same canonical order)
@@ -908,7 +1084,26 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   k_spgemm_rows<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col,
                                                  B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
-  k_spgemm_rows_warp<<<(n + kSpWarps - 1) / kSpWarps, 32 * kSpWarps, 0, s>>>(
+  static int num_sms = 0;
+  if (!num_sms) {
+    int dev = 0;
+    TP_CUDA_TRY(cudaGetDevice(&dev));
+    TP_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  {
+    long long blocks = (n + kSpWarps - 1) / kSpWarps;
+    if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
+    k_spgemm_rows_warp<<<(int)blocks, 32 * kSpWarps, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr,
+                                                             B.col, B.val, off, ub, ccol, cval, cnt);
+  }
+  TP_LAUNCH_CHECK();
+  static bool big_attr = false;
+  if (!big_attr) {
+    TP_CUDA_TRY(cudaFuncSetAttribute(k_spgemm_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSpBigSmem));
+    big_attr = true;
+  }
+  k_spgemm_rows_big<<<n < num_sms ? n : num_sms, kSpBigThreads, kSpBigSmem, s>>>(
       n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
   DevCSR C;
@@ -963,8 +1158,23 @@ double Hierarchy::operator_complexity() const {
   return s / L[0].A.nnz;
 }
 
+namespace {
+struct PhaseClock {
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  double lap(cudaStream_t s) {
+    TP_CUDA_TRY(cudaStreamSynchronize(s));
+    auto n = std::chrono::steady_clock::now();
+    double ms = std::chrono::duration<double, std::milli>(n - t).count();
+    t = n;
+    return ms;
+  }
+};
+}  // namespace
+
 void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
   opts = o;
+  for (double& x : phase_ms) x = 0.0;
+  PhaseClock clk;
   pool.release();
   L.clear();
   coarse_inv = nullptr;
@@ -1012,6 +1222,7 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
       if (read_int(undecided, s) == 0) break;
     }
     cur.pmis_rounds = rounds;
+    phase_ms[0] += clk.lap(s);
     int* flag = scratch.alloc<int>(n + 1);
     int* cidx = scratch.alloc<int>(n + 1);
     k_cflag<<<grid_for(n), kBlock, 0, s>>>(n, cur.cf, flag);
@@ -1060,16 +1271,36 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
           P.col, P.val);
       TP_LAUNCH_CHECK();
     }
+    if (opts.pmax > 0) {
+      DevCSR T;
+      T.n = n;
+      T.m = nc;
+      T.rowptr = pool.alloc<int>(n + 1);
+      k_trunc_count<<<grid_for(n), kBlock, 0, s>>>(n, P.rowptr, opts.pmax, cnt);
+      TP_LAUNCH_CHECK();
+      T.nnz = (int)scan_exclusive(cnt, T.rowptr, n, scratch, s);
+      T.col = pool.alloc<int>(T.nnz + 1);
+      T.val = pool.alloc<double>(T.nnz + 1);
+      k_trunc_fill<<<grid_for(n), kBlock, 0, s>>>(n, P.rowptr, P.col, P.val, opts.pmax, T.rowptr,
+                                                  T.col, T.val);
+      TP_LAUNCH_CHECK();
+      P = T;
+    }
     cur.P = P;
+    phase_ms[1] += clk.lap(s);
     cur.R = transpose(P, pool, scratch, s);
+    phase_ms[2] += clk.lap(s);
     cur.AP = spgemm(A, P, pool, scratch, s);
     DevCSR Ac = spgemm(cur.R, cur.AP, pool, scratch, s);
     TP_CUDA_TRY(cudaStreamSynchronize(s));
+    phase_ms[3] += clk.lap(s);
     scratch.release();
     L.emplace_back();
     L.back().A = Ac;
   }
+  clk.lap(s);
   finish_levels(s, true);
+  phase_ms[4] += clk.lap(s);
 }
 
 // smoother scaling, FP32 copies, work vectors (allocate = first setup) and

@@ -86,6 +86,7 @@ tp::AmgOpts amg_opts(const tp_precond_opts& o) {
   a.coarse_size = o.coarse_size;
   a.seed = o.seed;
   a.precision = o.precision;
+  a.pmax = o.pmax;
   return a;
 }
 
@@ -101,6 +102,7 @@ void check_opts(const tp_precond_opts& o) {
   if (o.max_levels < 1 || o.coarse_size < 1) fail(TP_EINVAL, "max_levels, coarse_size >= 1");
   if (o.interp_S < -1 || o.interp_S > 1 || o.max_levels_S < 0 || o.nu_S < 0 || o.nu_S > 8)
     fail(TP_EINVAL, "bad Schur-hierarchy override");
+  if (o.pmax < 0 || o.pmax > 16) fail(TP_EINVAL, "pmax must be in 0..16");
 }
 
 }  // namespace
@@ -187,6 +189,7 @@ void tp_default_opts(tp_precond_opts* o) {
   o->interp_S = 0;
   o->max_levels_S = 0;
   o->nu_S = 0;
+  o->pmax = 4;
 }
 
 const char* tp_status_string(int st) {
@@ -612,6 +615,14 @@ static int export_level(tp::Hierarchy* h, cudaStream_t s, int level, int* rowptr
   TP_CUDA_TRY(cudaStreamSynchronize(s));
   return TP_OK;
   TP_API_END
+}
+
+int tp_setup_timings(tp_ctx* c, int which, double* ms) {
+  if (!c || !ms || (which != 0 && which != 1)) return TP_EINVAL;
+  if (!c->built) return TP_ESTATE;
+  tp::Hierarchy* h = which == 0 ? c->hpp.get() : c->hS.get();
+  for (int k = 0; k < 5; ++k) ms[k] = h->phase_ms[k];
+  return TP_OK;
 }
 
 int tp_hierarchy_info(tp_ctx* c, int which, int* nlevels, int* n, int* nnz, int max_levels) {

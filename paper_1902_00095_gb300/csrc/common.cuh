@@ -84,6 +84,35 @@ inline int grid_for(long long n, int block = kBlock) {
   return (int)g;
 }
 
+// ----------------------------------------------------- dependent launch
+// Programmatic dependent launch: a kernel started with launch_pdl may begin
+// while the previous kernel on the stream finishes; it must call pdl_wait()
+// before reading anything that kernel wrote, and calls pdl_trigger() once
+// its own inputs are consumed so the next kernel can start launching.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+  count_launch();
+}
+
 // exclusive scan of n ints: out[0] = 0, out[i] = sum in[0..i-1]; out has
 // n + 1 entries and out[n] is the total. `in` and `out` may alias only if
 // equal. Returns the total (synchronises the stream).

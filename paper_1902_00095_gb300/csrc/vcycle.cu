@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, const int* __restrict__ r
                                                 const TV* __restrict__ dinv,
                                                 const TB* __restrict__ b,
                                                 const TV* __restrict__ xin, TO* __restrict__ xout) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
@@ -51,6 +53,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, const int* __restrict__ r
 template <class TV, class TB>
 __global__ void k_jacobi0(int n, const TV* __restrict__ dinv, const TB* __restrict__ b,
                           TV* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = dinv[i] * (TV)b[i];
 }
@@ -63,6 +67,8 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
                                                   const TV* __restrict__ val,
                                                   const TV* __restrict__ dinv,
                                                   const TB* __restrict__ b, TV* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
@@ -104,6 +110,8 @@ __global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __r
                                                     const TB* __restrict__ b,
                                                     const TV* __restrict__ xin,
                                                     TO* __restrict__ xout) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   const TV ax = ell_dot<TV, TV>(n, w, ecol, eval, xin, row);
@@ -116,6 +124,8 @@ __global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* _
                                                       const TB* __restrict__ b,
                                                       const TV* __restrict__ x,
                                                       TV* __restrict__ r) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   r[row] = (TV)b[row] - ell_dot<TV, TV>(n, w, ecol, eval, x, row);
@@ -127,6 +137,8 @@ __global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* _
                                                       const TV* __restrict__ dinv,
                                                       const TB* __restrict__ b,
                                                       TV* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   TV acc = TV(0);
@@ -149,6 +161,8 @@ __global__ void __launch_bounds__(256) k_residual(int n, const int* __restrict__
                                                   const TV* __restrict__ val,
                                                   const TB* __restrict__ b,
                                                   const TV* __restrict__ x, TV* __restrict__ r) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
@@ -162,6 +176,8 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
                                               const int* __restrict__ col,
                                               const TV* __restrict__ val,
                                               const TV* __restrict__ x, TV* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
@@ -175,6 +191,8 @@ __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ 
                                                  const int* __restrict__ col,
                                                  const TV* __restrict__ val,
                                                  const TV* __restrict__ e, TV* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
@@ -186,6 +204,8 @@ __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ 
 template <class TB, class TO>
 __global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __restrict__ b,
                          TO* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -204,8 +224,8 @@ void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB*
   switch (lanes) {
 #define TP_CASE(L)                                                                          \
   case L:                                                                                   \
-    k_jacobi<L, TV, TB, TO><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, dinv, b, xin,   \
-                                                 xout);                                     \
+    launch_pdl(k_jacobi<L, TV, TB, TO>, g, kBlock, s, A.n, A.rowptr, A.col, val, dinv, b,  \
+               xin, xout);                                                                  \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -220,7 +240,7 @@ void jacobi2z(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const T
   switch (lanes) {
 #define TP_CASE(L)                                                                       \
   case L:                                                                                \
-    k_jacobi2z<L, TV, TB><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, dinv, b, x);   \
+    launch_pdl(k_jacobi2z<L, TV, TB>, g, kBlock, s, A.n, A.rowptr, A.col, val, dinv, b, x); \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -235,7 +255,7 @@ void residual(int lanes, const DevCSR& A, const TV* val, const TB* b, const TV* 
   switch (lanes) {
 #define TP_CASE(L)                                                                      \
   case L:                                                                               \
-    k_residual<L, TV, TB><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, b, x, r);     \
+    launch_pdl(k_residual<L, TV, TB>, g, kBlock, s, A.n, A.rowptr, A.col, val, b, x, r);  \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -249,7 +269,7 @@ void spmv(int lanes, const DevCSR& A, const TV* val, const TV* x, TV* y, cudaStr
   switch (lanes) {
 #define TP_CASE(L)                                                              \
   case L:                                                                       \
-    k_spmv<L, TV><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, val, x, y);        \
+    launch_pdl(k_spmv<L, TV>, g, kBlock, s, A.n, A.rowptr, A.col, val, x, y);   \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -263,7 +283,7 @@ void prolong(int lanes, const DevCSR& P, const TV* val, const TV* e, TV* x, cuda
   switch (lanes) {
 #define TP_CASE(L)                                                              \
   case L:                                                                       \
-    k_prolong<L, TV><<<g, kBlock, 0, s>>>(P.n, P.rowptr, P.col, val, e, x);     \
+    launch_pdl(k_prolong<L, TV>, g, kBlock, s, P.n, P.rowptr, P.col, val, e, x);  \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -273,8 +293,7 @@ void prolong(int lanes, const DevCSR& P, const TV* val, const TV* e, TV* x, cuda
 
 template <class TB, class TO>
 void coarse(int n, const double* inv, const TB* b, TO* x, cudaStream_t s) {
-  k_coarse<TB, TO><<<grid_for((long long)n * 32), kBlock, 0, s>>>(n, inv, b, x);
-  TP_LAUNCH_CHECK();
+  launch_pdl(k_coarse<TB, TO>, grid_for((long long)n * 32), kBlock, s, n, inv, b, x);
 }
 
 template <class TV>
@@ -309,9 +328,8 @@ template <class TV, class TB, class TO>
 void level_sweep(const Level& v, const TV* dinv, const TB* b, const TV* xin, TO* xout,
                  cudaStream_t s) {
   if (v.ell_w > 0) {
-    k_jacobi_ell<TV, TB, TO><<<grid_for(v.A.n), kBlock, 0, s>>>(
-        v.A.n, v.ell_w, v.ell_col, Vals<TV>::E(v), dinv, b, xin, xout);
-    TP_LAUNCH_CHECK();
+    launch_pdl(k_jacobi_ell<TV, TB, TO>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
+               Vals<TV>::E(v), dinv, b, xin, xout);
   } else {
     jacobi<TV, TB, TO>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, xin, xout, s);
   }
@@ -320,9 +338,8 @@ void level_sweep(const Level& v, const TV* dinv, const TB* b, const TV* xin, TO*
 template <class TV, class TB>
 void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_t s) {
   if (v.ell_w > 0) {
-    k_residual_ell<TV, TB><<<grid_for(v.A.n), kBlock, 0, s>>>(v.A.n, v.ell_w, v.ell_col,
-                                                              Vals<TV>::E(v), b, x, r);
-    TP_LAUNCH_CHECK();
+    launch_pdl(k_residual_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
+               Vals<TV>::E(v), b, x, r);
   } else {
     residual<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), b, x, r, s);
   }
@@ -332,9 +349,8 @@ template <class TV, class TB>
 void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* x,
                                 cudaStream_t s) {
   if (v.ell_w > 0) {
-    k_jacobi2z_ell<TV, TB><<<grid_for(v.A.n), kBlock, 0, s>>>(v.A.n, v.ell_w, v.ell_col,
-                                                              Vals<TV>::E(v), dinv, b, x);
-    TP_LAUNCH_CHECK();
+    launch_pdl(k_jacobi2z_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
+               Vals<TV>::E(v), dinv, b, x);
   } else {
     jacobi2z<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, x, s);
   }
@@ -379,8 +395,7 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     level_two_sweeps_from_zero<TV, TB>(v, dinv, b, x, s);
     done = 2;
   } else {
-    k_jacobi0<TV, TB><<<grid_for(n), kBlock, 0, s>>>(n, dinv, b, x);
-    TP_LAUNCH_CHECK();
+    launch_pdl(k_jacobi0<TV, TB>, grid_for(n), kBlock, s, n, dinv, b, x);
   }
   Probe* pr = (l == 0) ? probe : nullptr;
   for (int k = done; k < nu_pre; ++k) {

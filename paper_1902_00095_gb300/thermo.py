@@ -42,7 +42,7 @@ class PrecondOpts(C.Structure):
                 ("nu_post", C.c_int), ("cheb_degree", C.c_int), ("theta", C.c_double),
                 ("max_levels", C.c_int), ("coarse_size", C.c_int), ("seed", C.c_ulonglong),
                 ("use_graphs", C.c_int), ("interp_S", C.c_int), ("max_levels_S", C.c_int),
-                ("nu_S", C.c_int)]
+                ("nu_S", C.c_int), ("pmax", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -94,6 +94,7 @@ SIGNATURES = {
     "tp_apply_preconditioner": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
     "tp_export_system": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp, _dp]),
     "tp_hierarchy_info": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, _ip, C.c_int]),
+    "tp_setup_timings": (C.c_int, [C.c_void_p, C.c_int, _dp]),
     "tp_export_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip, _ip, _dp, _sp, _sp, _ip,
                                   _ip, _ip, _dp]),
     "tp_amg_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -377,6 +378,11 @@ class Solver:
                                           val.ctypes.data_as(_dp), sv.ctypes.data_as(_dp),
                                           sc.ctypes.data_as(_dp)), "tp_export_system")
         return rp, col, val, sv, sc
+
+    def setup_timings(self, which):
+        ms = np.empty(5)
+        _check(self._lib.tp_setup_timings(self._h, which, ms.ctypes.data_as(_dp)), "tp_setup_timings")
+        return dict(zip(("pmis", "interp", "transpose", "galerkin", "finish"), ms.tolist()))
 
     def hierarchy_info(self, which):
         nl = C.c_int()

@@ -111,10 +111,11 @@ def _compare_hierarchies(gpu_amg, ohier, interp_name):
             assert np.array_equal(g["P"][2], P[2]), (l, interp_name)
 
 
-@pytest.mark.parametrize("name,which,interp", [
-    (n, w, i) for n in ("cfg1", "ragged") for w in ("App", "S") for i in (1, 0)]
-    + [("mid", "App", 1), ("mid", "S", 0)])
-def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp):
+@pytest.mark.parametrize("name,which,interp,pmax", [
+    (n, w, i, 0) for n in ("cfg1", "ragged") for w in ("App", "S") for i in (1, 0)]
+    + [("mid", "App", 1, 4), ("mid", "S", 0, 4), ("cfg1", "App", 1, 4), ("ragged", "S", 1, 3),
+       ("cfg1", "S", 0, 4)])
+def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax):
     """Both sides set up AMG on the same FP64 matrix (assembled by the
     oracle): strength, PMIS split, interpolation and Galerkin operators of
     every level agree bit for bit."""
@@ -123,8 +124,8 @@ def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp):
     A = osys.App if which == "App" else oS
     seed = 12345
     iname = "ext+i" if interp == 1 else "classical"
-    oh = oamg.setup(A, theta=0.25, seed=seed, coarse_size=64, interp=iname)
-    g = thermo.AMG(A[0], A[1], A[2], interp=interp, seed=seed)
+    oh = oamg.setup(A, theta=0.25, seed=seed, coarse_size=64, interp=iname, pmax=pmax)
+    g = thermo.AMG(A[0], A[1], A[2], interp=interp, seed=seed, pmax=pmax)
     _compare_hierarchies(g, oh, iname)
     # one V-cycle from zero: same linear operator up to rounding
     rng = np.random.default_rng(3)
