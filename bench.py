@@ -32,10 +32,10 @@ import numpy as np  # noqa: E402
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synthetic import make_problem  # noqa: E402
+from synthetic import RECIPE_SHAPES, make_problem  # noqa: E402
 
 METRIC = "unknowns/s (assemble + preconditioner setup + FGMRES to rel-res 1e-8)"
-CPU_SAMPLE = "4train"  # the 64x64x32 recipe at 32x32x16 (1/8 of the cells)
+CPU_SAMPLE = "grf32"  # the 64x64x32 recipe at 32x32x16 (1/8 of the cells)
 
 
 def parse():
@@ -44,18 +44,32 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="2")
+    ap.add_argument("--config", default="grf64", choices=sorted(RECIPE_SHAPES),
+                    help="workload recipe (default: the 64x64x32 five-spot)")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-sample", default=CPU_SAMPLE,
+                    help="recipe the reference arm times per step (default: the 64x64x32 "
+                         "recipe at 32x32x16)")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="skip the FP32-hierarchy + learned-Schur variant")
+    ap.add_argument("--train-problems", type=int, default=16)
+    ap.add_argument("--nu", type=int, default=2, help="l1-Jacobi sweeps before and after")
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--sequence", type=int, default=0,
+                    help="run this many backward-Euler steps with Newton (e.g. on "
+                         "layered256) instead of the single-system benchmark")
+    ap.add_argument("--max-newton", type=int, default=4,
+                    help="Newton iterations per time step in --sequence mode")
+    ap.add_argument("--sequence-variant", action="store_true",
+                    help="--sequence with FP32 hierarchies + learned S~ (trained untimed)")
     ap.add_argument("--probe", type=int, default=0,
                     help="kernel timed for the roofline: 0 finest A_pp sweep, "
                          "1 finest S~ sweep, 2 block SpMV")
-    a = ap.parse_args()
-    a.config = int(a.config) if a.config.isdigit() else a.config
-    return a
+    return ap.parse_args()
 
 
 def dist_env():
@@ -126,9 +140,10 @@ def measured_peak():
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the probed
-# kernel, keyed by (config, probe); None until a capture of the current kernel
-TRAFFIC = {("2", 0, 0): 14.16e6,   # profiles/k_jacobi_ell_config2_64x64x32_fp64.md
-           ("3", 0, 0): 118.3e6}  # profiles/k_jacobi_ell_config3_128x128x64_fp64.md
+# kernel, keyed by (recipe, probe, precision); None until a capture of the
+# current kernel
+TRAFFIC = {("grf64", 0, 0): 14.16e6,  # profiles/k_jacobi_ell_grf64_64x64x32_fp64.md
+           ("channel128", 0, 0): 118.3e6}  # profiles/k_jacobi_ell_channel128_128x128x64_fp64.md
 
 
 def cpu_baseline(seconds_target=20.0):
@@ -150,7 +165,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from oracle import krylov as okry
-    prob = make_problem(CPU_SAMPLE)
+    prob = make_problem(args.ref_sample)
     N = prob["nx"] * prob["ny"] * prob["nz"]
     for _ in range(args.warmup):
         okry.solve(prob, rtol=args.rtol)
@@ -166,15 +181,52 @@ def run_reference(args, rank, world):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "64x64x32 five-spot recipe, bounded sample 32x32x16",
-                   "grid": [32, 32, 16], "unknowns": 2 * N, "rtol": args.rtol},
+        "config": {"workload": f"64x64x32 five-spot recipe, bounded sample "
+                               f"{prob['nx']}x{prob['ny']}x{prob['nz']}",
+                   "grid": [prob["nx"], prob["ny"], prob["nz"]], "unknowns": 2 * N,
+                   "rtol": args.rtol},
         "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                         "sample": "32x32x16 grid of the 64x64x32 recipe per step, single thread"},
+                         "sample": f"{prob['nx']}x{prob['ny']}x{prob['nz']} grid per step, "
+                                   f"single thread"},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "fgmres_iters": int(np.median(its)),
     }
     print(json.dumps(line), flush=True)
+
+
+def train_schur_model(args):
+    """Train the learned Schur correction on the GPU (untimed): exact Schur
+    columns probed on --train-problems seeded 32x32x16 problems of the
+    64x64x32 recipe, 128 columns each, 40 epochs of Adam."""
+    from paper_1902_00095_gb300 import learned as L
+    from paper_1902_00095_gb300 import thermo
+    from synthetic.mlp import flatten, initial_params
+    t0 = time.perf_counter()
+    rng = np.random.Generator(np.random.PCG64(12345))
+    parts = []
+    ts = None
+    for q in range(args.train_problems):
+        tp = make_problem("grf32", seed=1000 + q)
+        if ts is None:
+            ts = thermo.Solver.from_problem(tp)
+        else:
+            ts.set_fields(tp["Kx"], tp["Ky"], tp["Kz"], tp["phi"], tp["kTr"])
+            ts.set_wells(tp["wells"])
+        parts.append(L.collect_samples(ts, tp, 128, rng))
+    ts.close()
+    mlp, hist = L.train(L.concat(parts), flatten(initial_params(0)), epochs=40)
+    return mlp, hist, time.perf_counter() - t0
+
+
+WORKLOAD = {
+    "iid16": "16x16x8 i.i.d. log-normal permeability, two wells, 1-day step",
+    "grf64": "64x64x32 Gaussian-random-field permeability, five-spot, 10-day step",
+    "grf32": "32x32x16 Gaussian-random-field permeability, five-spot, 10-day step",
+    "grf96": "96x96x48 Gaussian-random-field permeability, five-spot, 10-day step",
+    "channel128": "128x128x64 channelised permeability, five-spot, 10-day step",
+    "layered256": "256x256x64 layered permeability, five-spot, 30-day steps",
+}
 
 
 def run_ours(args, rank, world, local):
@@ -197,7 +249,7 @@ def run_ours(args, rank, world, local):
     Re = torch.empty(N, dtype=torch.float64, device=dev)
     xp = torch.empty(N, dtype=torch.float64, device=dev)
     xT = torch.empty(N, dtype=torch.float64, device=dev)
-    opts = thermo.default_opts(precision=args.precision)
+    opts = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
     s.probe_enable(args.probe)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
@@ -205,7 +257,7 @@ def run_ours(args, rank, world, local):
         s.set_fields(*fields)
         s.assemble(*state, prob["dt"], R_m=Rm, R_e=Re)
         s.build(opts)
-        return s.solve(rtol=args.rtol, maxit=args.maxit, out=(xp, xT))[2]
+        return s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart, out=(xp, xT))[2]
 
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -241,7 +293,7 @@ def run_ours(args, rank, world, local):
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "traffic": TRAFFIC.get((str(args.config), args.probe, args.precision)),
+                "traffic": TRAFFIC.get((args.config, args.probe, args.precision)),
                 "launches_timed": pr["launches"],
                 "avg_launch_us": pr["ms"] * 1e3 / max(1, pr["launches"]),
                 "algorithmic_bytes_per_launch": pr["bytes"] / max(1, pr["launches"])}
@@ -284,6 +336,49 @@ def run_ours(args, rank, world, local):
                "h2d_bytes_per_step": 9 * N * 8, "d2h_bytes_per_step": 2 * N * 8 + 2 * N * 8,
                "ms_per_step": te * 1e3}
 
+    # variant: FP32 hierarchy + learned Schur correction (network trained on
+    # probed exact Schur columns of the 32x32x16 recipe before timing)
+    variant = None
+    if not args.no_variant:
+        mlp, hist, t_train = train_schur_model(args)
+        s.set_schur_model(mlp)
+        vopts = thermo.default_opts(precision=1, schur=1)
+        s.probe_enable(args.probe)
+
+        def step_variant():
+            s.set_fields(*fields)
+            s.assemble(*state, prob["dt"], R_m=Rm, R_e=Re)
+            s.build(vopts)
+            return s.solve(rtol=args.rtol, maxit=args.maxit, out=(xp, xT))[2]
+
+        for _ in range(args.warmup):
+            step_variant()
+        torch.cuda.synchronize()
+        s.probe_read(reset=True)
+        vev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        vinfo = None
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            vev[k][0].record(stream)
+            vinfo = step_variant()
+            vev[k][1].record(stream)
+        torch.cuda.synchronize()
+        vms = sum(a.elapsed_time(b) for a, b in vev) / args.steps
+        vpr = s.probe_read(reset=True)
+        fb_rows, fb_all = s.learned_status()
+        variant = {"name": "fp32 hierarchy + learned S~ (FP64 FGMRES)", "ms_per_step": vms,
+                   "value": world * 2 * N / (vms * 1e-3), "unit": "unknowns/s",
+                   "speedup_vs_fp64_plain": ms / vms, "iters": vinfo["iters"],
+                   "rel_res": vinfo["rel_res"], "rel_res_unscaled": vinfo["rel_res_unscaled"],
+                   "t_solve_ms": vinfo["t_solve_ms"],
+                   "finest_sweep_gbs": (vpr["bytes"] / (vpr["ms"] * 1e-3) / 1e9) if vpr["ms"] > 0 else None,
+                   "learned_fallback_rows": fb_rows, "learned_global_fallback": fb_all,
+                   "training": {"problems": args.train_problems, "columns_per_problem": 128,
+                                "loss_first": hist[0], "loss_last": hist[-1],
+                                "seconds_untimed": t_train}}
+
     if rank != 0:
         return
     line = {
@@ -292,13 +387,14 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == 0 else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": f"config {args.config}: {prob['nx']}x{prob['ny']}x{prob['nz']} five-spot, "
-                               f"{2 * N} unknowns, one Newton system",
+        "config": {"workload": f"{args.config}: {WORKLOAD[args.config]}, {2 * N} unknowns, "
+                               f"one Newton system",
                    "grid": [prob["nx"], prob["ny"], prob["nz"]], "unknowns": 2 * N,
                    "rtol": args.rtol, "precision": "fp64" if args.precision == 0 else "fp32 hierarchy",
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"replicas{world}"},
         "e2e": e2e,
+        "variant": variant,
         "roofline": roofline,
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -313,6 +409,60 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_sequence(args, rank, world, local):
+    """Backward-Euler time steps, each solved by Newton with line search (at
+    most --max-newton linear solves, AMG structure reused between Newton
+    iterations) on one GPU; with --sequence-variant the hierarchies run in
+    FP32 with the learned Schur correction."""
+    import torch
+    from paper_1902_00095_gb300 import thermo
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = make_problem(args.config)
+    N = prob["nx"] * prob["ny"] * prob["nz"]
+    s = thermo.Solver.from_problem(prob)
+    train = None
+    if args.sequence_variant:
+        mlp, hist, t_train = train_schur_model(args)
+        s.set_schur_model(mlp)
+        opts = thermo.default_opts(precision=1, schur=1, nu_pre=args.nu, nu_post=args.nu)
+        train = {"problems": args.train_problems, "loss_first": hist[0], "loss_last": hist[-1],
+                 "seconds_untimed": t_train}
+    else:
+        opts = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
+    d = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
+    p, T = d(prob["p_n"]), d(prob["T_n"])
+    steps = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.sequence):
+        p, T, info = s.newton_step(p, T, prob["dt"], max_newton=args.max_newton, tol_f=1e-8,
+                                   tol_dx=1e-8, rtol=args.rtol, maxit=args.maxit,
+                                   restart=args.restart, reuse=True, opts=opts)
+        steps.append(info)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": "backward-Euler steps (Newton + block-preconditioned FGMRES) per second",
+        "value": args.sequence / wall, "unit": "steps/s", "n_gpus": world, "steps": args.sequence,
+        "ms_per_step": wall * 1e3 / args.sequence, "higher_is_better": True,
+        "dtype": "f64+f32" if (args.sequence_variant or args.precision) else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.config}: {WORKLOAD[args.config]}, {args.sequence} steps",
+                   "unknowns": 2 * N, "nu": args.nu, "restart": args.restart,
+                   "max_newton": args.max_newton,
+                   "solver": "fp32 hierarchy + learned S~" if args.sequence_variant else
+                             ("fp32 hierarchy" if args.precision else "fp64 plain")},
+        "newton": [{k: st[k] for k in ("newton_iters", "linear_iters", "status", "rel_f", "rel_dx",
+                                       "line_search_halvings", "t_ms")} for st in steps],
+        "learned": (dict(train, fallback=s.learned_status()) if train else None),
+        "final_T_range": [float(T.min()), float(T.max())],
+        "final_p_range": [float(p.min()), float(p.max())],
+    }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -325,6 +475,8 @@ def main():
         dist.init_process_group(backend=backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.sequence > 0:
+        run_sequence(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -176,25 +176,31 @@ int tp_probe_enable(tp_ctx* ctx, int which);
 int tp_probe_read(tp_ctx* ctx, double* total_ms, long long* launches,
                   double* total_bytes, int reset);
 
-/* Newton iteration of one backward-Euler step (Sec. 3 linearisation,
- * Sec. 4 stopping rules): starting from x = (p_n, T_n), repeat assemble /
- * precondition / FGMRES / x += dx until ||D G(x_k)|| <= tol_f ||D G(x_0)||
- * (D the equation scaling of the first linearisation) or ||dx|| <= tol_dx
- * ||x||, at most max_newton linear solves. reuse = 1 keeps the AMG structure
- * of the first iteration and refreshes only the Galerkin values (and keeps
- * the captured graph). Full Newton steps (no line search). The new state is
- * written to p_out, T_out ([N] each). Returns TP_OK or TP_NOT_CONVERGED. */
+/* Newton iteration with line search of one backward-Euler step (Sec. 3
+ * linearisation; Sec. 4: Newton with line search, relative function-norm and
+ * step tolerances): starting from x = (p_n, T_n), repeat assemble /
+ * precondition / FGMRES / line search until ||D G(x_k)|| <= tol_f
+ * ||D G(x_0)|| (D the equation scaling of the first linearisation) or
+ * alpha ||dx|| <= tol_dx ||x||, at most max_newton linear solves. The line
+ * search backtracks x_k + alpha dx (alpha = 1, 1/2, ..., at most 6 halvings)
+ * until ||D G|| <= (1 - 1e-4 alpha) ||D G(x_k)||; line_search = 0 takes full
+ * steps. reuse = 1 keeps the AMG structure of the first iteration and
+ * refreshes only the Galerkin values (and keeps the captured graph). The new
+ * state is written to p_out, T_out ([N] each). Returns TP_OK or
+ * TP_NOT_CONVERGED. */
 typedef struct {
   int max_newton;
   double tol_f, tol_dx;
   double rtol;      /* FGMRES relative tolerance per linear solve */
   int maxit, restart;
   int reuse;
+  int line_search;
 } tp_newton_opts;
 
 typedef struct {
   int newton_iters, linear_iters, status, last_linear_status;
   double rel_f, rel_dx, t_ms;
+  int line_search_halvings;
 } tp_newton_info;
 
 int tp_newton_step(tp_ctx* ctx, const double* p_n, const double* T_n, double dt,

@@ -1,6 +1,6 @@
-// Newton iteration of one backward-Euler step (Sec. 3: linearise G(x) = 0 at
-// x_k and solve Eq. AXR for the increment; Sec. 4: relative function-norm and
-// relative step tolerances). The first iteration builds the preconditioner;
+// Newton iteration with line search of one backward-Euler step (Sec. 3:
+// linearise G(x) = 0 at x_k and solve Eq. AXR for the increment; Sec. 4:
+// line search, relative function-norm and relative step tolerances). The first iteration builds the preconditioner;
 // later ones optionally keep the AMG structure (C/F splits, P, R, patterns)
 // and refresh only the Galerkin values, so the captured graph is reused.
 #include <chrono>
@@ -51,12 +51,15 @@ __global__ void k_finish_sum(const double* __restrict__ partials, int B, double*
   }
 }
 
-__global__ void k_axpy2(int N, double* __restrict__ p, double* __restrict__ T,
-                        const double* __restrict__ dp, const double* __restrict__ dT) {
+// (p, T) = (p0, T0) + alpha (dp, dT)
+__global__ void k_axpby2(int N, const double* __restrict__ p0, const double* __restrict__ T0,
+                         double alpha, const double* __restrict__ dp,
+                         const double* __restrict__ dT, double* __restrict__ p,
+                         double* __restrict__ T) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
-    p[i] += dp[i];
-    T[i] += dT[i];
+    p[i] = p0[i] + alpha * dp[i];
+    T[i] = T0[i] + alpha * dT[i];
   }
 }
 
@@ -80,25 +83,28 @@ int newton_step(tp_ctx* c, double dt, const tp_precond_opts& popts, const tp_new
   const int N = c->N;
   auto t0 = std::chrono::steady_clock::now();
   double G0 = -1.0, relf = 1.0, reldx = 1.0;
-  int k = 0, lin_its = 0, lin_status = TP_OK, status = TP_NOT_CONVERGED;
+  int k = 0, lin_its = 0, lin_status = TP_OK, status = TP_NOT_CONVERGED, ls_total = 0;
   double* dp = c->io2;
   double* dT = c->io3;
+  if (!c->xsave_p) {
+    c->xsave_p = c->pool.alloc<double>(N);
+    c->xsave_T = c->pool.alloc<double>(N);
+  }
+  // linearise at x_0
+  int st = assemble_device(c, dt);
+  if (st != TP_OK) return st;
+  launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+  launch_equation_scales(N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
+                         c->scales, s);
+  // the first linearisation fixes the scaling of the function norm
+  TP_CUDA_TRY(cudaMemcpyAsync(c->fscale, c->scales, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double G = std::sqrt(sumsq2(c, c->Rm, c->Re, c->fscale));
+  G0 = G;
   for (k = 0;; ++k) {
-    int st = assemble_device(c, dt);
-    if (st != TP_OK) return st;
-    // equation scales of this linearisation (also used by the solve)
-    launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
-    launch_equation_scales(N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
-                           c->scales, s);
-    // the first linearisation fixes the scaling of the function norm
-    if (k == 0) TP_CUDA_TRY(cudaMemcpyAsync(c->fscale, c->scales, 2 * sizeof(double),
-                                            cudaMemcpyDeviceToDevice, s));
-    const double G = std::sqrt(sumsq2(c, c->Rm, c->Re, c->fscale));
     if (!std::isfinite(G)) {
       status = TP_ENONFINITE;
       break;
     }
-    if (k == 0) G0 = G;
     relf = G0 > 0.0 ? G / G0 : 0.0;
     if (G == 0.0 || (k > 0 && relf <= no.tol_f)) {
       status = TP_OK;
@@ -115,14 +121,41 @@ int newton_step(tp_ctx* c, double dt, const tp_precond_opts& popts, const tp_new
     lin_status = fgmres_solve(c, c->io0, c->io1, dp, dT, no.rtol, no.maxit, no.restart, &si);
     lin_its += si.iters;
     if (lin_status < 0) return lin_status;
-    k_axpy2<<<grid_for(N), kBlock, 0, s>>>(N, c->p, c->T, dp, dT);
-    TP_LAUNCH_CHECK();
-    const double dx = std::sqrt(sumsq2(c, dp, dT, nullptr));
+    // line search (Sec. 4 names Newton with line search without its form;
+    // taken as backtracking on the scaled function norm): x_k + alpha dx,
+    // alpha = 1, 1/2, ... until ||G|| <= (1 - 1e-4 alpha) ||G(x_k)||, at most
+    // max_ls halvings; a non-finite trial state counts as a rejected step
+    TP_CUDA_TRY(cudaMemcpyAsync(c->xsave_p, c->p, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    TP_CUDA_TRY(cudaMemcpyAsync(c->xsave_T, c->T, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    double alpha = 1.0, Gt = G;
+    const int max_ls = no.line_search ? 6 : 0;
+    for (int ls = 0;; ++ls) {
+      k_axpby2<<<grid_for(N), kBlock, 0, s>>>(N, c->xsave_p, c->xsave_T, alpha, dp, dT, c->p, c->T);
+      TP_LAUNCH_CHECK();
+      st = assemble_device(c, dt);
+      if (st != TP_OK && st != TP_ENONFINITE) return st;
+      const bool finite = st == TP_OK;
+      if (finite) {
+        launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
+        launch_equation_scales(N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
+                               c->scales, s);
+        Gt = std::sqrt(sumsq2(c, c->Rm, c->Re, c->fscale));
+      }
+      if ((finite && std::isfinite(Gt) && Gt <= (1.0 - 1e-4 * alpha) * G) || ls >= max_ls) {
+        if (!finite) return st;
+        break;
+      }
+      alpha *= 0.5;
+      ++ls_total;
+    }
+    G = Gt;
+    const double dx = alpha * std::sqrt(sumsq2(c, dp, dT, nullptr));
     const double xn = std::sqrt(sumsq2(c, c->p, c->T, nullptr));
     reldx = xn > 0.0 ? dx / xn : 0.0;
     if (reldx <= no.tol_dx) {
       status = TP_OK;
       ++k;
+      relf = G0 > 0.0 ? G / G0 : 0.0;
       break;
     }
   }
@@ -136,6 +169,7 @@ int newton_step(tp_ctx* c, double dt, const tp_precond_opts& popts, const tp_new
     info->rel_f = relf;
     info->rel_dx = reldx;
     info->t_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->line_search_halvings = ls_total;
   }
   return status;
 }

@@ -67,6 +67,7 @@ struct tp_ctx {
   int learned_fallback_rows = 0;
   bool learned_global_fallback = false;
   double dt_last = 0.0;
+  double *xsave_p = nullptr, *xsave_T = nullptr;  // Newton line-search base point
   // user-facing scratch for host pointer marshalling
   double *io0 = nullptr, *io1 = nullptr, *io2 = nullptr, *io3 = nullptr;
 

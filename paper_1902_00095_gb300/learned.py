@@ -108,7 +108,7 @@ def main():
     parts = []
     s = None
     for q in range(a.problems):
-        prob = make_problem("4train", seed=1000 + q)
+        prob = make_problem("grf32", seed=1000 + q)
         if s is None:
             s = thermo.Solver.from_problem(prob)
         else:
@@ -120,7 +120,7 @@ def main():
     mlp, hist = train(data, flatten(initial_params(0)), epochs=a.epochs)
     t2 = time.time()
     shape = tuple(int(v) for v in a.eval_shape.split(","))
-    evals = [evaluate(mlp, make_problem("4eval", seed=5000 + q, shape=shape)) for q in range(a.eval)]
+    evals = [evaluate(mlp, make_problem("grf96", seed=5000 + q, shape=shape)) for q in range(a.eval)]
     if a.out:
         np.save(a.out, mlp.params())
     print(json.dumps(dict(samples=int(data["target"].size), probe_s=t1 - t0, train_s=t2 - t1,

@@ -58,13 +58,14 @@ class SolveInfo(C.Structure):
 
 class NewtonOpts(C.Structure):
     _fields_ = [("max_newton", C.c_int), ("tol_f", C.c_double), ("tol_dx", C.c_double),
-                ("rtol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("reuse", C.c_int)]
+                ("rtol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("reuse", C.c_int),
+                ("line_search", C.c_int)]
 
 
 class NewtonInfo(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("linear_iters", C.c_int), ("status", C.c_int),
                 ("last_linear_status", C.c_int), ("rel_f", C.c_double), ("rel_dx", C.c_double),
-                ("t_ms", C.c_double)]
+                ("t_ms", C.c_double), ("line_search_halvings", C.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -289,12 +290,13 @@ class Solver:
         return keep[2], keep[3], info.as_dict()
 
     def newton_step(self, p_n, T_n, dt, max_newton=3, tol_f=1e-8, tol_dx=1e-8, rtol=1e-8,
-                    maxit=500, restart=30, reuse=True, opts=None, out=None, **kw):
+                    maxit=500, restart=30, reuse=True, line_search=True, opts=None, out=None,
+                    **kw):
         """One backward-Euler step by Newton's method from (p_n, T_n);
         returns (p, T, info)."""
         o = opts if opts is not None else default_opts(**kw)
         no = NewtonOpts(int(max_newton), float(tol_f), float(tol_dx), float(rtol), int(maxit),
-                        int(restart), int(bool(reuse)))
+                        int(restart), int(bool(reuse)), int(bool(line_search)))
         if out is None:
             if _is_torch(p_n):
                 import torch

@@ -1,4 +1,19 @@
-"""The five workload recipes as plain data (fields, wells, constants).
+"""The workload recipes as plain data (fields, wells, constants).
+
+Recipes (name: grid, permeability, wells, time step):
+  "iid16"      16x16x8, i.i.d. log-normal (mean -13, std 0.5), injector at
+               (0,0) and BHP producer at the far corner, 1 day
+  "grf64"      64x64x32, Gaussian random field (mean -13, std 1, correlation
+               8x8x2 cells, kv/kh 0.1), five-spot, 10 days
+  "grf32"      the grf64 recipe at 32x32x16 (learned-part training, seeds
+               1000..)
+  "grf96"      the grf64 recipe at 96x96x48 (learned-part evaluation, seeds
+               5000..)
+  "channel128" 128x128x64, binary channelised (30% sand 1e-12, shale 1e-15,
+               conductivity 3.0 / 1.5 by facies), five-spot, 10 days
+  "layered256" 256x256x64, 8 layers (means -12..-14, std 0.8), five-spot,
+               30 days
+  "tiny"       the iid16 recipe at a given shape
 
 A problem is a dict with:
   grid  : nx, ny, nz, dx, dy, dz, g           (10 m cubes, gravity 9.81, z up,
@@ -19,13 +34,13 @@ from .fields import gaussian_random_field, iid_log_normal, channelised, layered
 
 DAY = 86400.0
 
-CONFIG_SHAPES = {
-    1: (16, 16, 8),
-    2: (64, 64, 32),
-    3: (128, 128, 64),
-    "4train": (32, 32, 16),
-    "4eval": (96, 96, 48),
-    5: (256, 256, 64),
+RECIPE_SHAPES = {
+    "iid16": (16, 16, 8),
+    "grf64": (64, 64, 32),
+    "channel128": (128, 128, 64),
+    "grf32": (32, 32, 16),
+    "grf96": (96, 96, 48),
+    "layered256": (256, 256, 64),
 }
 
 
@@ -58,20 +73,19 @@ def _five_spot(nx, ny, nz, rate=1.0e-3, T_inj=450.0, p_bh=10.0e6):
     return wells
 
 
-def make_problem(config, seed=None, shape=None, dt_days=None, fluid=None):
-    """Build one problem of the given workload recipe.
-
-    config: 1, 2, 3, "4train", "4eval", 5, or "tiny" (a small config-1 style
-    case whose shape must be given).
-    """
+def make_problem(recipe, seed=None, shape=None, dt_days=None, fluid=None):
+    """Build one problem of the given workload recipe (a name of
+    RECIPE_SHAPES, or "tiny", whose shape must be given)."""
+    if recipe not in RECIPE_SHAPES and recipe != "tiny":
+        raise ValueError(f"unknown recipe {recipe!r}")
     if shape is None:
-        shape = CONFIG_SHAPES[config]
+        shape = RECIPE_SHAPES[recipe]
     nx, ny, nz = shape
     N = nx * ny * nz
     sh = (nz, ny, nx)
     fl = default_fluid() if fluid is None else dict(fluid)
     phi = np.full(N, 0.2)
-    if config in (1, "tiny"):
+    if recipe in ("iid16", "tiny"):
         rng = np.random.Generator(np.random.PCG64(1 if seed is None else seed))
         K = iid_log_normal(rng, sh, -13.0, 0.5).ravel()
         Kx, Ky, Kz = K.copy(), K.copy(), K.copy()
@@ -81,8 +95,8 @@ def make_problem(config, seed=None, shape=None, dt_days=None, fluid=None):
                  dict(i=nx - 1, j=ny - 1, k0=0, k1=nz - 1, kind=1,
                       value=10.0e6, T_inj=0.0, U=0.0)]
         dt = 1.0 * DAY
-    elif config in (2, "4train", "4eval"):
-        default_seed = {2: 2, "4train": 1000, "4eval": 5000}[config]
+    elif recipe in ("grf64", "grf32", "grf96"):
+        default_seed = {"grf64": 2, "grf32": 1000, "grf96": 5000}[recipe]
         rng = np.random.Generator(np.random.PCG64(default_seed if seed is None else seed))
         f = gaussian_random_field(rng, sh, (8.0, 8.0, 2.0))
         K = (10.0 ** (-13.0 + 1.0 * f)).ravel()
@@ -90,7 +104,7 @@ def make_problem(config, seed=None, shape=None, dt_days=None, fluid=None):
         kTr = np.full(N, 2.0)
         wells = _five_spot(nx, ny, nz)
         dt = 10.0 * DAY
-    elif config == 3:
+    elif recipe == "channel128":
         rng = np.random.Generator(np.random.PCG64(3 if seed is None else seed))
         K, sand = channelised(rng, sh, (16.0, 4.0, 2.0), 0.30, 1.0e-12, 1.0e-15)
         K = K.ravel()
@@ -98,21 +112,19 @@ def make_problem(config, seed=None, shape=None, dt_days=None, fluid=None):
         kTr = np.where(sand.ravel(), 3.0, 1.5)
         wells = _five_spot(nx, ny, nz)
         dt = 10.0 * DAY
-    elif config == 5:
+    else:  # layered256
         rng = np.random.Generator(np.random.PCG64(7 if seed is None else seed))
         K = layered(rng, sh, 8, -12.0, -14.0, 0.8).ravel()
         Kx, Ky, Kz = K.copy(), K.copy(), K.copy()
         kTr = np.full(N, 2.0)
         wells = _five_spot(nx, ny, nz)
         dt = 30.0 * DAY
-    else:
-        raise ValueError(f"unknown config {config!r}")
     if dt_days is not None:
         dt = dt_days * DAY
     p_n = np.full(N, 15.0e6)
     T_n = np.full(N, 320.0)
     return dict(
-        config=config, nx=nx, ny=ny, nz=nz, dx=10.0, dy=10.0, dz=10.0, g=9.81,
+        recipe=recipe, nx=nx, ny=ny, nz=nz, dx=10.0, dy=10.0, dz=10.0, g=9.81,
         fluid=fl, Kx=Kx, Ky=Ky, Kz=Kz, phi=phi, kTr=kTr, wells=wells,
         p_n=p_n, T_n=T_n, p_k=p_n.copy(), T_k=T_n.copy(), dt=dt,
     )

@@ -11,7 +11,7 @@ from oracle import krylov as okry
 from oracle import learned as olearn
 from oracle import physics as ophys
 from synthetic import make_problem
-from synthetic.configs import perturbed_state
+from synthetic.recipes import perturbed_state
 from synthetic.mlp import flatten, initial_params, unflatten
 
 pytestmark = pytest.mark.gpu

@@ -16,7 +16,7 @@ from oracle import amg as oamg
 from oracle import krylov as okry
 from oracle import physics as ophys
 from synthetic import make_problem
-from synthetic.configs import perturbed_state
+from synthetic.recipes import perturbed_state
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,7 @@ def assemble_both(prob, p=None, T=None):
 
 
 PROBLEMS = {
-    "cfg1": lambda: (make_problem(1), None),
+    "iid16": lambda: (make_problem("iid16"), None),
     "ragged": lambda: (make_problem("tiny", shape=(13, 11, 7), seed=21), 7),
     "thin": lambda: (make_problem("tiny", shape=(37, 1, 3), seed=4), 8),
     # more than 4096 cells: the finest level also gets the ELL copy
@@ -112,9 +112,9 @@ def _compare_hierarchies(gpu_amg, ohier, interp_name):
 
 
 @pytest.mark.parametrize("name,which,interp,pmax", [
-    (n, w, i, 0) for n in ("cfg1", "ragged") for w in ("App", "S") for i in (1, 0)]
-    + [("mid", "App", 1, 4), ("mid", "S", 0, 4), ("cfg1", "App", 1, 4), ("ragged", "S", 1, 3),
-       ("cfg1", "S", 0, 4)])
+    (n, w, i, 0) for n in ("iid16", "ragged") for w in ("App", "S") for i in (1, 0)]
+    + [("mid", "App", 1, 4), ("mid", "S", 0, 4), ("iid16", "App", 1, 4), ("ragged", "S", 1, 3),
+       ("iid16", "S", 0, 4)])
 def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax):
     """Both sides set up AMG on the same FP64 matrix (assembled by the
     oracle): strength, PMIS split, interpolation and Galerkin operators of
@@ -137,7 +137,7 @@ def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax
 
 
 def test_amg_setup_is_deterministic():
-    prob, p, T = problem("cfg1")
+    prob, p, T = problem("iid16")
     osys, *_ = okry.assemble(prob, p, T)
     A = osys.App
     a1 = thermo.AMG(*A)
@@ -193,7 +193,7 @@ def _oracle_scaled_residual(osys, obp, obT, xp, xT):
     return np.linalg.norm(r) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged", "thin"])
+@pytest.mark.parametrize("name", ["iid16", "ragged", "thin"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_solve_matches_direct_solution(name, precision):
     prob, p, T = problem(name)
@@ -211,7 +211,7 @@ def test_solve_matches_direct_solution(name, precision):
 
 
 def test_tight_solve_resolves_both_blocks():
-    prob, p, T = problem("cfg1")
+    prob, p, T = problem("iid16")
     s, _, (osys, obp, obT, oS) = assemble_both(prob, p, T)
     s.build()
     xp, xT, info = s.solve(rtol=1e-11, maxit=600)
@@ -221,10 +221,10 @@ def test_tight_solve_resolves_both_blocks():
     assert ep <= 1e-6 and eT <= 1e-6, (ep, eT)
 
 
-def test_solve_iterations_match_oracle_on_config1():
+def test_solve_iterations_match_oracle_on_iid16():
     """Same method on both sides: FGMRES iteration counts agree within a
     couple of iterations (rounding differs, the preconditioner does not)."""
-    prob = make_problem(1)
+    prob = make_problem("iid16")
     s = gpu_solver(prob)
     s.assemble(prob["p_k"], prob["T_k"], prob["p_n"], prob["T_n"], prob["dt"])
     s.build()
@@ -261,7 +261,7 @@ def test_degenerate_single_cell_and_single_level():
 
 
 def test_errors_are_status_codes_not_faults():
-    prob = make_problem(1)
+    prob = make_problem("iid16")
     s = gpu_solver(prob)
     with pytest.raises(thermo.ThermoError) as e:
         s.solve()
@@ -286,8 +286,8 @@ def test_errors_are_status_codes_not_faults():
     assert info["status"] == thermo.TP_NOT_CONVERGED and info["iters"] == 1
 
 
-@pytest.mark.parametrize("cfg", [2, 3])
-def test_full_size_configs_reach_the_tolerance(cfg):
+@pytest.mark.parametrize("cfg", ["grf64", "channel128"])
+def test_full_size_recipes_reach_the_tolerance(cfg):
     """At the full sizes the oracle's own assembly (vectorised, seconds) is
     the checker: the GPU solution must give relative residual <= 1e-8 on
     the oracle's matrix, and sampled rows of the GPU matrix must match the
@@ -295,13 +295,13 @@ def test_full_size_configs_reach_the_tolerance(cfg):
     prob = make_problem(cfg)
     s = gpu_solver(prob)
     s.assemble(prob["p_k"], prob["T_k"], prob["p_n"], prob["T_n"], prob["dt"])
-    s.build(precision=1 if cfg == 3 else 0)
+    s.build(precision=1 if cfg == "channel128" else 0)
     xp, xT, info = s.solve(rtol=1e-8, maxit=600)
     assert info["status"] == 0, info
     osys, obp, obT, oS = okry.assemble(prob)
     assert _oracle_scaled_residual(osys, obp, obT, xp, xT) <= 1.5e-8
     rp, col, val, sv, scales = s.export_system()
-    rng = np.random.default_rng(cfg)
+    rng = np.random.default_rng(len(cfg))
     rows = rng.choice(s.N, 2000, replace=False)
     for i in rows:
         a, b = rp[i], rp[i + 1]
@@ -331,3 +331,25 @@ def test_newton_step_matches_oracle_newton(reuse):
     assert np.linalg.norm(dpg - dpo) <= 1e-6 * np.linalg.norm(dpo)
     assert np.linalg.norm(dTg - dTo) <= 1e-6 * np.linalg.norm(dTo)
     assert abs(info["rel_f"] - hist[-1][0]) <= 1e-3 * hist[-1][0] + 1e-12
+    assert info["line_search_halvings"] == 0
+
+
+def test_newton_line_search_matches_oracle():
+    """A 30-day step at 10x the injection rate, where full Newton steps
+    leave the physical range: the GPU line search takes the same step
+    lengths as the oracle's and both converge to the same root."""
+    from oracle import newton as onewton
+    prob = make_problem("tiny", shape=(12, 10, 6), seed=5, dt_days=30)
+    prob["wells"][0]["value"] = 2e-3
+    prob["wells"][1]["value"] = 14.8e6
+    po, To, hist = onewton.newton_step(prob, max_newton=12, tol_f=1e-11, tol_dx=0.0)
+    halvings = sum(int(round(-np.log2(h[2]))) for h in hist[:-1])
+    assert halvings > 0
+    s = gpu_solver(prob)
+    p, T, info = s.newton_step(prob["p_n"], prob["T_n"], prob["dt"], max_newton=12,
+                               tol_f=1e-11, tol_dx=0.0, rtol=1e-11, maxit=1000)
+    assert info["status"] == 0, info
+    assert info["newton_iters"] == len(hist) - 1
+    assert info["line_search_halvings"] == halvings
+    assert np.linalg.norm(p - po) <= 1e-6 * np.linalg.norm(po - prob["p_n"])
+    assert np.linalg.norm(T - To) <= 1e-6 * np.linalg.norm(To - prob["T_n"])

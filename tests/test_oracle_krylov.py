@@ -11,7 +11,7 @@ import pytest
 
 from oracle import amg, krylov, physics
 from synthetic import make_problem
-from synthetic.configs import perturbed_state
+from synthetic.recipes import perturbed_state
 
 
 def small_system(shape=(5, 4, 3), seed=1):
@@ -91,7 +91,7 @@ def test_fgmres_residuals_are_krylov_least_squares_minima():
 
 
 def test_amg_preconditioned_solve_matches_direct_solve():
-    prob = make_problem(1)
+    prob = make_problem("iid16")
     out = krylov.solve(prob, rtol=1e-10)
     assert out["status"] == "converged"
     xp, xT = krylov.direct_solution(out["sys"], out["bp"], out["bT"])
@@ -138,3 +138,46 @@ def test_newton_converges_quadratically_to_a_root():
     g = np.hypot(np.linalg.norm(sys0.s_m * bp), np.linalg.norm(sys0.s_e * bT))
     g0 = np.hypot(np.linalg.norm(sys0.s_m * bp0), np.linalg.norm(sys0.s_e * bT0))
     assert g <= 1e-12 * g0
+
+
+def test_line_search_keeps_full_steps_on_a_mild_step():
+    """Where full Newton steps already decrease the function norm enough,
+    the line search (Sec. 4) accepts alpha = 1 every time and the iterates
+    are those of plain Newton."""
+    from oracle import newton
+    prob = make_problem("tiny", shape=(6, 5, 3), seed=5, dt_days=0.5)
+    prob["wells"][0]["value"] = 2e-4
+    prob["wells"][1]["value"] = 14.8e6
+    p, T, hist = newton.newton_step(prob, max_newton=8, tol_f=1e-13, tol_dx=0.0)
+    pf, Tf, histf = newton.newton_step(prob, max_newton=8, tol_f=1e-13, tol_dx=0.0,
+                                       line_search=False)
+    assert all(h[2] == 1.0 for h in hist[:-1])
+    assert np.array_equal(p, pf) and np.array_equal(T, Tf)
+
+
+def test_line_search_rescues_a_step_where_full_newton_diverges():
+    """30-day step with a 10x injection rate: full Newton steps leave the
+    physical range (non-finite or growing function norm) while the
+    backtracking line search converges quadratically to a root; every
+    accepted step meets the sufficient-decrease test with alpha a power of
+    1/2 no smaller than 2^-6."""
+    from oracle import newton
+    prob = make_problem("tiny", shape=(6, 5, 3), seed=5, dt_days=30)
+    prob["wells"][0]["value"] = 2e-3
+    prob["wells"][1]["value"] = 14.8e6
+    try:
+        _, _, hf = newton.newton_step(prob, max_newton=12, tol_f=1e-12, tol_dx=0.0,
+                                      line_search=False)
+        assert not hf[-1][0] <= 1e-12
+    except FloatingPointError:
+        pass
+    p, T, hist = newton.newton_step(prob, max_newton=12, tol_f=1e-12, tol_dx=0.0)
+    relf = [h[0] for h in hist]
+    alphas = [h[2] for h in hist[:-1]]
+    assert relf[-1] <= 1e-12
+    assert min(alphas) < 1.0
+    for a in alphas:
+        assert a >= 2.0 ** -6 and np.log2(a) == np.round(np.log2(a))
+    for k, a in enumerate(alphas):
+        assert relf[k + 1] <= (1.0 - 1e-4 * a) * relf[k]
+    assert relf[-1] <= 1e3 * relf[-2] ** 2

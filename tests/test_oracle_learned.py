@@ -6,7 +6,7 @@ import pytest
 
 from oracle import krylov, learned, physics
 from synthetic import make_problem, default_fluid
-from synthetic.configs import perturbed_state
+from synthetic.recipes import perturbed_state
 
 
 def small(shape=(5, 4, 3), seed=3, fluid=None):

@@ -11,7 +11,7 @@ import pytest
 
 from oracle import physics
 from synthetic import make_problem, default_fluid
-from synthetic.configs import perturbed_state
+from synthetic.recipes import perturbed_state
 
 
 def tiny(shape=(4, 3, 3), seed=11, fluid=None, wells=True):

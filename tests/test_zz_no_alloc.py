@@ -13,7 +13,7 @@ def test_noalloc_scales_match_solver_scales_twice():
     torch = pytest.importorskip("torch")
     from paper_1902_00095_gb300 import thermo
     from synthetic import make_problem
-    from synthetic.configs import perturbed_state
+    from synthetic.recipes import perturbed_state
     import ctypes as C
 
     lib = thermo.load()
