@@ -88,8 +88,10 @@ typedef struct {
                     /*    and V-cycles inside FP64 FGMRES (coarsest LU FP64)  */
   int interp;       /* 0: classical (Ruge-Stueben, modified); 1: extended+i   */
                     /*    (default 1 for A_pp; S~ uses interp_S, default 0)  */
-  int smoother;     /* 0: l1-Jacobi; 1: Chebyshev on D^-1 A                   */
-  int nu_pre, nu_post, cheb_degree;
+  int smoother;     /* 0: l1-Jacobi; 1: Chebyshev on D^-1 A, D = diag(A),     */
+                    /*    over [lambda/30, 1.1 lambda], lambda from 10 power  */
+                    /*    iterations (A_pp; S~ uses smoother_S)               */
+  int nu_pre, nu_post, cheb_degree;  /* cheb_degree in 1..4                   */
   double theta;     /* strength threshold                                     */
   int max_levels, coarse_size;
   unsigned long long seed;  /* PMIS tie-break seed                            */
@@ -100,6 +102,7 @@ typedef struct {
   int nu_S;         /* 0 same; else nu_pre = nu_post = nu_S                   */
   int pmax;         /* interpolation truncation: at most pmax weights per row  */
                     /* (largest |w|, row sums kept); default 4, 0 = off, <=16 */
+  int smoother_S;   /* -1 same as smoother, 0 l1-Jacobi (default), 1 Chebyshev */
 } tp_precond_opts;
 
 typedef struct {

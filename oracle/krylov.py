@@ -164,20 +164,22 @@ def assemble(prob, p=None, T=None):
 def solve(prob, rtol=1e-8, maxit=300, restart=30, theta=0.25, seed=0,
           variant="full", smoother="l1jacobi", nu_pre=2, nu_post=2,
           coarse_size=64, p=None, T=None, schur="plain", interp="ext+i",
-          interp_S="classical", cheb_degree=2, pmax=4):
+          interp_S="classical", cheb_degree=2, pmax=4, smoother_S="l1jacobi"):
     """Assemble, build the block preconditioner with one V-cycle per
     approximate inverse, and solve with FGMRES(restart) in the scaled
     system. A_pp's hierarchy uses `interp` (extended+i by default: the
     elliptic pressure block), S~_T's uses `interp_S` (classical by default:
     under the gravity-driven upwind advection of S~_T extended+i produces
-    weights above one and indefinite coarse operators). Returns the FGMRES
-    dict plus the pieces it used."""
+    weights above one and indefinite coarse operators). `smoother` is A_pp's
+    smoother, `smoother_S` S~_T's (l1-Jacobi by default: Chebyshev on
+    D^{-1} S~_T, whose spectrum is not real for the advective S~_T, can
+    amplify). Returns the FGMRES dict plus the pieces it used."""
     sys, bp, bT, S = assemble(prob, p, T)
     if schur == "att":
         S = sys.ATT
     h_pp = amg.setup(sys.App, theta, seed, coarse_size, smoother=smoother,
                      interp=interp, cheb_degree=cheb_degree, pmax=pmax)
-    h_S = amg.setup(S, theta, seed, coarse_size, smoother=smoother,
+    h_S = amg.setup(S, theta, seed, coarse_size, smoother=smoother_S,
                     interp=interp_S, cheb_degree=cheb_degree, pmax=pmax)
     sm, se = sys.s_m, sys.s_e
     V_pp = lambda r: amg.vcycle(h_pp, r, 0, nu_pre, nu_post)

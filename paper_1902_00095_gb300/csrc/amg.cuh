@@ -14,6 +14,21 @@
 
 namespace tp {
 
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  // splitmix64 output for state x (Steele, Lea, Flood 2014)
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// tie-break hash of row i: upper 32 bits of splitmix64(seed xor i)
+__device__ __forceinline__ unsigned int pmis_hash(unsigned long long seed, int i) {
+  return (unsigned int)(splitmix64(seed ^ (unsigned long long)(long long)i) >> 32);
+}
+
+constexpr int kMaxChebDegree = 4;
+
 struct AmgOpts {
   int interp = 1;        // 0 classical, 1 extended+i
   int smoother = 0;      // 0 l1-Jacobi, 1 Chebyshev
@@ -56,7 +71,13 @@ struct Level {
   DevCSR AP;         // A P (kept for numeric-only refreshes)
   double* dinv = nullptr;   // smoother scaling (l1 or plain diagonal), FP64
   float* dinvf = nullptr;
-  double cheb_lo = 0.0, cheb_hi = 0.0;
+  // Chebyshev: coefficients (FP64 [2 deg - 1], then the power-iteration
+  // scale and lambda_max at [2 kMaxChebDegree], [2 kMaxChebDegree + 1]),
+  // FP32 copy, power-iteration vectors and the recurrence work vectors
+  double* cheb = nullptr;
+  float* chebf = nullptr;
+  double *pw0 = nullptr, *pw1 = nullptr;
+  void *cw = nullptr, *cd0 = nullptr, *cd1 = nullptr, *cr = nullptr;
   // V-cycle work vectors, in the hierarchy precision (double* or float*)
   void* b = nullptr;
   void* x = nullptr;
@@ -107,12 +128,23 @@ class Hierarchy {
   // transpose, Galerkin products, smoother scaling + coarse inverse
   double phase_ms[5] = {0, 0, 0, 0, 0};
   int* err = nullptr;
+  double* cheb_partials = nullptr;   // norm partial sums of the power iteration
 
  private:
   void finish_levels(cudaStream_t s, bool allocate);
   void vcycle_fp64(cudaStream_t s);
   void vcycle_fp32(cudaStream_t s);
 };
+
+// Chebyshev smoother (chebyshev.cu): plain-diagonal scaling, lambda_max by
+// power iteration and the recurrence coefficients, all on the device.
+void chebyshev_setup(Level& v, Pool& pool, int degree, unsigned long long seed,
+                     double* partials, int* err, bool allocate, cudaStream_t s);
+int chebyshev_norm_parts();
+// xout = Chebyshev(degree) applied to A x = b from xin (zero when null)
+template <class TV, class TB, class TO>
+void chebyshev_apply(const Level& v, const TV* val, const TV* dinv, int degree, const TB* b,
+                     const TV* xin, TO* xout, cudaStream_t s);
 
 // Standalone sparse helpers reused by the solver.
 void csr_transpose_positions(const DevCSR& A, int* tpos, int* err, cudaStream_t s);

@@ -18,18 +18,6 @@ namespace {
 
 constexpr signed char kC = 1, kF = -1, kU = 0;
 
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
-  // splitmix64 output for state x (Steele, Lea, Flood 2014)
-  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ unsigned int pmis_hash(unsigned long long seed, int i) {
-  return (unsigned int)(splitmix64(seed ^ (unsigned long long)(long long)i) >> 32);
-}
-
 // index of key in a[lo, hi) (ascending), or -1
 __device__ __forceinline__ int find_in(const int* __restrict__ a, int lo, int hi, int key) {
   int h = hi;
@@ -1308,6 +1296,8 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
 void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
   const bool f32 = opts.precision == 1;
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  if (opts.smoother == 1 && allocate)
+    cheb_partials = pool.alloc<double>(2 * chebyshev_norm_parts());
   for (size_t l = 0; l < L.size(); ++l) {
     Level& v = L[l];
     const int n = v.A.n;
@@ -1315,9 +1305,13 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
       v.dinv = pool.alloc<double>(n);
       v.dinvf = f32 ? pool.alloc<float>(n) : nullptr;
     }
-    k_l1_dinv<<<grid_for(n), kBlock, 0, s>>>(n, v.A.rowptr, v.A.col, v.A.val, v.dinv, v.dinvf,
-                                             err);
-    TP_LAUNCH_CHECK();
+    if (opts.smoother == 1 && l + 1 < L.size()) {
+      chebyshev_setup(v, pool, opts.cheb_degree, opts.seed, cheb_partials, err, allocate, s);
+    } else {
+      k_l1_dinv<<<grid_for(n), kBlock, 0, s>>>(n, v.A.rowptr, v.A.col, v.A.val, v.dinv,
+                                               v.dinvf, err);
+      TP_LAUNCH_CHECK();
+    }
     if (f32) {
       if (allocate) v.A.valf = pool.alloc<float>(v.A.nnz);
       k_to_float<<<grid_for(v.A.nnz), kBlock, 0, s>>>(v.A.nnz, v.A.val, v.A.valf);
@@ -1357,12 +1351,22 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
       v.x = pool.alloc<char>(es * (n + 1));
       v.t = pool.alloc<char>(es * (n + 1));
       v.r = pool.alloc<char>(es * (n + 1));
+      if (opts.smoother == 1) {
+        v.cw = pool.alloc<char>(es * (n + 1));
+        v.cd0 = pool.alloc<char>(es * (n + 1));
+        v.cd1 = pool.alloc<char>(es * (n + 1));
+        v.cr = pool.alloc<char>(es * (n + 1));
+      }
       v.lanes_A = pick_lanes(v.A);
       v.lanes_P = v.P.nnz ? pick_lanes(v.P) : 1;
       v.lanes_R = v.R.nnz ? pick_lanes(v.R) : 1;
     }
   }
-  if (read_int(err, s) & 4) fail(TP_SETUP_FAILED, "AMG: empty or non-finite row");
+  {
+    const int e = read_int(err, s);
+    if (e & 4) fail(TP_SETUP_FAILED, "AMG: empty, zero-diagonal or non-finite row");
+    if (e & 8) fail(TP_SETUP_FAILED, "AMG: Chebyshev power iteration broke down");
+  }
   // coarsest level: explicit inverse by Gauss-Jordan with partial pivoting
   Level& cl = L.back();
   if (allocate) {

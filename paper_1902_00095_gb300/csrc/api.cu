@@ -95,7 +95,9 @@ void check_opts(const tp_precond_opts& o) {
   if (o.variant != 0 && o.variant != 1) fail(TP_EINVAL, "variant must be 0 or 1");
   if (o.precision != 0 && o.precision != 1) fail(TP_EINVAL, "precision must be 0 or 1");
   if (o.interp != 0 && o.interp != 1) fail(TP_EINVAL, "interp must be 0 or 1");
-  if (o.smoother != 0) fail(TP_EINVAL, "smoother must be 0 (l1-Jacobi)");
+  if (o.smoother != 0 && o.smoother != 1) fail(TP_EINVAL, "smoother must be 0 or 1");
+  if (o.smoother_S < -1 || o.smoother_S > 1) fail(TP_EINVAL, "smoother_S must be -1, 0 or 1");
+  if (o.cheb_degree < 1 || o.cheb_degree > 4) fail(TP_EINVAL, "cheb_degree must be in 1..4");
   if (o.nu_pre < 1 || o.nu_post < 1 || o.nu_pre > 8 || o.nu_post > 8)
     fail(TP_EINVAL, "nu_pre and nu_post must be in 1..8");
   if (!(o.theta > 0.0 && o.theta < 1.0)) fail(TP_EINVAL, "theta must be in (0, 1)");
@@ -190,6 +192,7 @@ void tp_default_opts(tp_precond_opts* o) {
   o->max_levels_S = 0;
   o->nu_S = 0;
   o->pmax = 4;
+  o->smoother_S = 0;
 }
 
 const char* tp_status_string(int st) {
@@ -1019,6 +1022,7 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
   if (o.interp_S >= 0) aS.interp = o.interp_S;
   if (o.max_levels_S > 0) aS.max_levels = o.max_levels_S;
   if (o.nu_S > 0) aS.nu_pre = aS.nu_post = o.nu_S;
+  if (o.smoother_S >= 0) aS.smoother = o.smoother_S;
   c->hpp->setup(App, ao, s);
   c->hS->setup(S, aS, s);
   c->hpp->probe = c->probe_which == 0 ? &c->probe : nullptr;

@@ -371,9 +371,26 @@ void sweep_probed(Probe* pr, const Level& v, const TV* dinv, const TB* b, const 
   if (pr) pr->after(s, sweep_bytes<TV, TB, TO>(v.A));
 }
 
+// smoother selection of one V-cycle: 0 l1-Jacobi, 1 Chebyshev of `degree`
+struct Smooth {
+  int kind = 0, degree = 2;
+};
+
+// one smoothing step xin -> xout (xin null: zero initial guess, Chebyshev only)
+template <class TV, class TB, class TO>
+void smooth_step(const Smooth& sm, Probe* pr, const Level& v, const TV* dinv, const TB* b,
+                 const TV* xin, TO* xout, cudaStream_t s) {
+  if (sm.kind == 1) {
+    chebyshev_apply<TV, TB, TO>(v, Vals<TV>::A(v), dinv, sm.degree, b, xin, xout, s);
+  } else {
+    sweep_probed<TV, TB, TO>(pr, v, dinv, b, xin, xout, s);
+  }
+}
+
 template <class TV, class TB, class TO>
 TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, TO* final_out,
-              int nu_pre, int nu_post, cudaStream_t s, Probe* probe = nullptr) {
+              int nu_pre, int nu_post, const Smooth& sm, cudaStream_t s,
+              Probe* probe = nullptr) {
   Level& v = L[l];
   const int n = v.A.n;
   TV* x = static_cast<TV*>(v.x);
@@ -387,19 +404,22 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     return x;
   }
   const TV* dinv = Vals<TV>::dinv(v);
-  // pre-smoothing from a zero guess (the first two sweeps fused)
+  Probe* pr = (l == 0) ? probe : nullptr;
   TV* cur = x;
   TV* oth = t;
   int done = 1;
-  if (nu_pre >= 2) {
+  if (sm.kind == 1) {
+    // pre-smoothing from a zero guess
+    smooth_step<TV, TB, TV>(sm, nullptr, v, dinv, b, (const TV*)nullptr, x, s);
+  } else if (nu_pre >= 2) {
+    // the first two l1-Jacobi sweeps from a zero guess fused
     level_two_sweeps_from_zero<TV, TB>(v, dinv, b, x, s);
     done = 2;
   } else {
     launch_pdl(k_jacobi0<TV, TB>, grid_for(n), kBlock, s, n, dinv, b, x);
   }
-  Probe* pr = (l == 0) ? probe : nullptr;
   for (int k = done; k < nu_pre; ++k) {
-    sweep_probed<TV, TB, TV>(pr, v, dinv, b, cur, oth, s);
+    smooth_step<TV, TB, TV>(sm, pr, v, dinv, b, cur, oth, s);
     std::swap(cur, oth);
   }
   // coarse-grid correction
@@ -408,15 +428,15 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   Level& c = L[l + 1];
   TV* bc = static_cast<TV*>(c.b);
   spmv<TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
-  TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, s);
+  TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s);
   prolong<TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
   // post-smoothing
   for (int k = 1; k <= nu_post; ++k) {
     if (k == nu_post && final_out) {
-      sweep_probed<TV, TB, TO>(pr, v, dinv, b, cur, final_out, s);
+      smooth_step<TV, TB, TO>(sm, pr, v, dinv, b, cur, final_out, s);
       return nullptr;
     }
-    sweep_probed<TV, TB, TV>(pr, v, dinv, b, cur, oth, s);
+    smooth_step<TV, TB, TV>(sm, pr, v, dinv, b, cur, oth, s);
     std::swap(cur, oth);
   }
   return cur;
@@ -430,12 +450,14 @@ void Hierarchy::vcycle(cudaStream_t s) {
 }
 
 void Hierarchy::vcycle_fp64(cudaStream_t s) {
-  run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s,
+  Smooth sm{opts.smoother, opts.cheb_degree};
+  run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                     probe);
 }
 
 void Hierarchy::vcycle_fp32(cudaStream_t s) {
-  run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, s,
+  Smooth sm{opts.smoother, opts.cheb_degree};
+  run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                    probe);
 }
 

@@ -136,6 +136,38 @@ def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax
     g.close()
 
 
+@pytest.mark.parametrize("name,degree,nu", [("iid16", 2, 1), ("mid", 2, 2), ("ragged", 3, 1),
+                                             ("iid16", 1, 2)])
+def test_chebyshev_vcycle_matches_oracle(name, degree, nu):
+    """Chebyshev smoothing on D^{-1} A_pp (lambda_max by power iteration on
+    both sides): one V-cycle agrees with the oracle's to rounding in FP64
+    and to FP32 accuracy with the FP32 hierarchy."""
+    prob, p, T = problem(name)
+    osys, *_ = okry.assemble(prob, p, T)
+    A = osys.App
+    oh = oamg.setup(A, seed=5, smoother="chebyshev", cheb_degree=degree)
+    b = np.random.default_rng(11).standard_normal(A[0].size - 1)
+    xo = oamg.vcycle(oh, b, 0, nu, nu)
+    for precision, tol in ((0, 1e-10), (1, 1e-4)):
+        g = thermo.AMG(*A, seed=5, smoother=1, cheb_degree=degree, nu_pre=nu, nu_post=nu,
+                       precision=precision)
+        xg = g.vcycle(b)
+        assert np.max(np.abs(xg - xo)) <= tol * np.max(np.abs(xo)), precision
+        g.close()
+
+
+def test_chebyshev_solve_matches_direct_solution_and_oracle_iterations():
+    prob, p, T = problem("iid16")
+    s, _, (osys, obp, obT, oS) = assemble_both(prob, p, T)
+    s.build(smoother=1, nu_pre=1, nu_post=1)
+    xp, xT, info = s.solve(rtol=1e-10)
+    assert info["status"] == 0
+    rp, rT = okry.direct_solution(osys, obp, obT)
+    assert _errors(xp, xT, rp, rT)[0] <= 1e-6
+    o = okry.solve(prob, rtol=1e-10, p=p, T=T, smoother="chebyshev", nu_pre=1, nu_post=1)
+    assert abs(info["iters"] - o["iters"]) <= 2, (info["iters"], o["iters"])
+
+
 def test_amg_setup_is_deterministic():
     prob, p, T = problem("iid16")
     osys, *_ = okry.assemble(prob, p, T)

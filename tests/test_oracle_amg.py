@@ -264,3 +264,59 @@ def test_truncated_hierarchy_still_contracts():
     for _ in range(20):
         x = x + amg.vcycle(h, b - amg.spmv(A, x))
     assert np.linalg.norm(b - amg.spmv(A, x)) < 1e-3 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+def test_chebyshev_matches_the_chebyshev_polynomial_on_a_diagonal_matrix(degree):
+    """For A = diag(t) (D = I) one Chebyshev application from x = 0 leaves the
+    error e = p(t) x* with p(t) = T_k((theta - t)/delta) / T_k(theta/delta),
+    T_k the Chebyshev polynomial of the first kind (T_1 = y, T_2 = 2y^2 - 1,
+    T_3 = 4y^3 - 3y, T_4 = 8y^4 - 8y^2 + 1), the minimax polynomial of
+    degree k with p(0) = 1 on [lo, hi]."""
+    T = {1: lambda y: y, 2: lambda y: 2 * y * y - 1, 3: lambda y: 4 * y ** 3 - 3 * y,
+         4: lambda y: 8 * y ** 4 - 8 * y * y + 1}[degree]
+    t = np.linspace(0.05, 2.0, 40)
+    A = csr(np.diag(t))
+    lo, hi = 0.1, 2.1
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    b = np.random.default_rng(degree).standard_normal(t.size)
+    x = amg.chebyshev(A, np.ones(t.size), b, None, lo, hi, degree)
+    xs = b / t
+    p = T((theta - t) / delta) / T(theta / delta)
+    assert np.max(np.abs(x - xs * (1.0 - p))) <= 1e-12 * np.max(np.abs(xs))
+    # the error is damped by at most 1 / T_k(theta/delta) on [lo, hi]
+    inside = (t >= lo) & (t <= hi)
+    assert np.all(np.abs(p[inside]) <= 1.0 / abs(T(theta / delta)) + 1e-14)
+
+
+def test_chebyshev_bounds_power_iteration():
+    """lambda_max of D^{-1} A: for the Dirichlet 1D Laplacian the eigenvalues
+    of D^{-1} A are 1 - cos(k pi / (n + 1)); ten power iterations from a
+    positive start vector give an estimate at most the largest one (the
+    quotient ||M y|| / ||y|| of a symmetric M never exceeds its spectral
+    radius) and, with a start vector that is an eigenvector, exactly it."""
+    n = 30
+    A = lap1d(n, neumann=False)
+    lo, hi, d = amg.chebyshev_bounds(A, seed=0)
+    lam_max = 1.0 + np.cos(np.pi / (n + 1))
+    lam = hi / 1.1
+    assert lam <= lam_max * (1 + 1e-12) and lam > 0.5 * lam_max
+    assert abs(lo - lam / 30.0) <= 1e-15 * lam and np.array_equal(d, np.full(n, 2.0))
+    # 3 I: D^{-1} A = I and every start vector is an eigenvector of eigenvalue 1
+    _, hiB, dB = amg.chebyshev_bounds(csr(np.diag(np.full(7, 3.0))), 0)
+    assert abs(hiB / 1.1 - 1.0) <= 1e-14 and np.array_equal(dB, np.full(7, 3.0))
+
+
+def test_chebyshev_vcycle_converges():
+    """V(1,1) cycles with degree-2 Chebyshev smoothing as a stationary
+    iteration on a 2D Laplacian: the residual falls by at least 0.7 per
+    cycle (measured about 0.55)."""
+    A = lap2d(12, neumann=False, ay=0.5)
+    h = amg.setup(A, coarse_size=20, smoother="chebyshev", cheb_degree=2)
+    rng = np.random.default_rng(4)
+    n = A[0].size - 1
+    b = rng.standard_normal(n)
+    x = np.zeros(n)
+    for _ in range(20):
+        x = x + amg.vcycle(h, b - amg.spmv(A, x), 0, 1, 1)
+    assert np.linalg.norm(b - amg.spmv(A, x)) < 0.7 ** 20 * np.linalg.norm(b)
