@@ -85,7 +85,9 @@ typedef struct {
   int variant;      /* 0: full five-step apply (Sec. 3.2); 1: block lower     */
                     /*    triangular (steps 1-3, delta_p = x_p)               */
   int precision;    /* 0: FP64 hierarchy; 1: FP32 hierarchy values, smoothers */
-                    /*    and V-cycles inside FP64 FGMRES (coarsest LU FP64)  */
+                    /*    and V-cycles inside FP64 FGMRES (coarsest LU FP64); */
+                    /* 2: as 1 with P and R values stored in BF16 (FP32       */
+                    /*    accumulation)                                       */
   int interp;       /* 0: classical (Ruge-Stueben, modified); 1: extended+i   */
                     /*    (default 1 for A_pp; S~ uses interp_S, default 0)  */
   int smoother;     /* 0: l1-Jacobi; 1: Chebyshev on D^-1 A, D = diag(A),     */

@@ -10,6 +10,7 @@
 // Solve: one V-cycle from a zero guess, FP64 or FP32 values/vectors, replayable
 // as a CUDA graph.
 #pragma once
+#include <cuda_bf16.h>
 #include "common.cuh"
 
 namespace tp {
@@ -36,7 +37,7 @@ struct AmgOpts {
   double theta = 0.25;
   int max_levels = 25, coarse_size = 64, max_coarse_dense = 2048;
   unsigned long long seed = 0;
-  int precision = 0;     // 0 FP64, 1 FP32 hierarchy
+  int precision = 0;     // 0 FP64, 1 FP32 hierarchy, 2 FP32 + BF16 P and R
   int max_pmis_rounds = 64;
   int pmax = 0;          // interpolation truncation (0 = off)
 };
@@ -69,6 +70,8 @@ struct Level {
   int pmis_rounds = 0;
   DevCSR P, R;       // P: n x nc, R: nc x n
   DevCSR AP;         // A P (kept for numeric-only refreshes)
+  __nv_bfloat16* Ph = nullptr;   // BF16 copies of the P and R values
+  __nv_bfloat16* Rh = nullptr;   // (precision 2)
   double* dinv = nullptr;   // smoother scaling (l1 or plain diagonal), FP64
   float* dinvf = nullptr;
   // Chebyshev: coefficients (FP64 [2 deg - 1], then the power-iteration

@@ -933,6 +933,13 @@ __global__ void k_to_float(long long n, const double* __restrict__ a, float* __r
   if (i < n) b[i] = (float)a[i];
 }
 
+// round to nearest even BF16 (interpolation weights of precision 2)
+__global__ void k_to_bf16(long long n, const double* __restrict__ a,
+                          __nv_bfloat16* __restrict__ b) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn((float)a[i]);
+}
+
 // --------------------------------------------------------------- ELL copy
 __global__ void k_max_row(int n, const int* __restrict__ rp, int* __restrict__ mx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1294,7 +1301,8 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
 // smoother scaling, FP32 copies, work vectors (allocate = first setup) and
 // the coarsest-level inverse
 void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
-  const bool f32 = opts.precision == 1;
+  const bool f32 = opts.precision >= 1;
+  const bool bf16 = opts.precision == 2;
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   if (opts.smoother == 1 && allocate)
     cheb_partials = pool.alloc<double>(2 * chebyshev_norm_parts());
@@ -1324,6 +1332,15 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
         k_to_float<<<grid_for(v.P.nnz), kBlock, 0, s>>>(v.P.nnz, v.P.val, v.P.valf);
         k_to_float<<<grid_for(v.R.nnz), kBlock, 0, s>>>(v.R.nnz, v.R.val, v.R.valf);
         TP_LAUNCH_CHECK();
+        if (bf16) {
+          if (allocate) {
+            v.Ph = pool.alloc<__nv_bfloat16>(v.P.nnz);
+            v.Rh = pool.alloc<__nv_bfloat16>(v.R.nnz);
+          }
+          k_to_bf16<<<grid_for(v.P.nnz), kBlock, 0, s>>>(v.P.nnz, v.P.val, v.Ph);
+          k_to_bf16<<<grid_for(v.R.nnz), kBlock, 0, s>>>(v.R.nnz, v.R.val, v.Rh);
+          TP_LAUNCH_CHECK();
+        }
       }
     }
     // ELL copy for short-row levels (the 7-point finest level)

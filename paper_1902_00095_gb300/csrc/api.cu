@@ -93,7 +93,7 @@ tp::AmgOpts amg_opts(const tp_precond_opts& o) {
 void check_opts(const tp_precond_opts& o) {
   if (o.schur < 0 || o.schur > 2) fail(TP_EINVAL, "schur must be 0 (S~_T), 1 (learned) or 2 (A_TT)");
   if (o.variant != 0 && o.variant != 1) fail(TP_EINVAL, "variant must be 0 or 1");
-  if (o.precision != 0 && o.precision != 1) fail(TP_EINVAL, "precision must be 0 or 1");
+  if (o.precision < 0 || o.precision > 2) fail(TP_EINVAL, "precision must be 0, 1 or 2");
   if (o.interp != 0 && o.interp != 1) fail(TP_EINVAL, "interp must be 0 or 1");
   if (o.smoother != 0 && o.smoother != 1) fail(TP_EINVAL, "smoother must be 0 or 1");
   if (o.smoother_S < -1 || o.smoother_S > 1) fail(TP_EINVAL, "smoother_S must be -1, 0 or 1");

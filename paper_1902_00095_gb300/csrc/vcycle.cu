@@ -12,6 +12,20 @@ namespace tp {
 
 namespace {
 
+// value conversion (BF16 interpolation weights are widened to the vector type)
+template <class TV, class TP>
+__device__ __forceinline__ TV widen(TP v) {
+  return (TV)v;
+}
+template <>
+__device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ double widen<double, __nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+
 template <int LANES, class T>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
@@ -20,14 +34,15 @@ __device__ __forceinline__ T group_sum(T v) {
 }
 
 // row dot sum_j a_ij x_j for the row owned by this thread group
-template <int LANES, class TV, class TX>
+template <int LANES, class TV, class TX, class TP = TV>
 __device__ __forceinline__ TV row_dot(const int* __restrict__ rp, const int* __restrict__ col,
-                                      const TV* __restrict__ val, const TX* __restrict__ x,
+                                      const TP* __restrict__ val, const TX* __restrict__ x,
                                       int row, bool valid, int lane) {
   TV acc = TV(0);
   if (valid) {
     const int e1 = rp[row + 1];
-    for (int e = rp[row] + lane; e < e1; e += LANES) acc += val[e] * (TV)x[col[e]];
+    for (int e = rp[row] + lane; e < e1; e += LANES)
+      acc += widen<TV, TP>(val[e]) * (TV)x[col[e]];
   }
   return group_sum<LANES>(acc);
 }
@@ -170,33 +185,33 @@ __global__ void __launch_bounds__(256) k_residual(int n, const int* __restrict__
   if (valid && lane == 0) r[row] = (TV)b[row] - ax;
 }
 
-// y = A x (restriction with R)
-template <int LANES, class TV>
+// y = R x (restriction; R values of type TP)
+template <int LANES, class TP, class TV>
 __global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
                                               const int* __restrict__ col,
-                                              const TV* __restrict__ val,
+                                              const TP* __restrict__ val,
                                               const TV* __restrict__ x, TV* __restrict__ y) {
   pdl_wait();
   pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
-  TV ax = row_dot<LANES, TV, TV>(rp, col, val, x, row, valid, lane);
+  TV ax = row_dot<LANES, TV, TV, TP>(rp, col, val, x, row, valid, lane);
   if (valid && lane == 0) y[row] = ax;
 }
 
-// x += P e (prolongation)
-template <int LANES, class TV>
+// x += P e (prolongation; P values of type TP)
+template <int LANES, class TP, class TV>
 __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ rp,
                                                  const int* __restrict__ col,
-                                                 const TV* __restrict__ val,
+                                                 const TP* __restrict__ val,
                                                  const TV* __restrict__ e, TV* __restrict__ x) {
   pdl_wait();
   pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
-  TV pe = row_dot<LANES, TV, TV>(rp, col, val, e, row, valid, lane);
+  TV pe = row_dot<LANES, TV, TV, TP>(rp, col, val, e, row, valid, lane);
   if (valid && lane == 0) x[row] += pe;
 }
 
@@ -263,13 +278,13 @@ void residual(int lanes, const DevCSR& A, const TV* val, const TB* b, const TV* 
   TP_LAUNCH_CHECK();
 }
 
-template <class TV>
-void spmv(int lanes, const DevCSR& A, const TV* val, const TV* x, TV* y, cudaStream_t s) {
+template <class TP, class TV>
+void spmv(int lanes, const DevCSR& A, const TP* val, const TV* x, TV* y, cudaStream_t s) {
   const int g = grid_for((long long)A.n * lanes);
   switch (lanes) {
-#define TP_CASE(L)                                                              \
-  case L:                                                                       \
-    launch_pdl(k_spmv<L, TV>, g, kBlock, s, A.n, A.rowptr, A.col, val, x, y);   \
+#define TP_CASE(L)                                                                  \
+  case L:                                                                           \
+    launch_pdl(k_spmv<L, TP, TV>, g, kBlock, s, A.n, A.rowptr, A.col, val, x, y);   \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -277,13 +292,13 @@ void spmv(int lanes, const DevCSR& A, const TV* val, const TV* x, TV* y, cudaStr
   TP_LAUNCH_CHECK();
 }
 
-template <class TV>
-void prolong(int lanes, const DevCSR& P, const TV* val, const TV* e, TV* x, cudaStream_t s) {
+template <class TP, class TV>
+void prolong(int lanes, const DevCSR& P, const TP* val, const TV* e, TV* x, cudaStream_t s) {
   const int g = grid_for((long long)P.n * lanes);
   switch (lanes) {
-#define TP_CASE(L)                                                              \
-  case L:                                                                       \
-    launch_pdl(k_prolong<L, TV>, g, kBlock, s, P.n, P.rowptr, P.col, val, e, x);  \
+#define TP_CASE(L)                                                                      \
+  case L:                                                                               \
+    launch_pdl(k_prolong<L, TP, TV>, g, kBlock, s, P.n, P.rowptr, P.col, val, e, x);    \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -427,9 +442,11 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   level_residual<TV, TB>(v, b, cur, r, s);
   Level& c = L[l + 1];
   TV* bc = static_cast<TV*>(c.b);
-  spmv<TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
+  if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s);
+  else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
   TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s);
-  prolong<TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
+  if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
+  else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
   // post-smoothing
   for (int k = 1; k <= nu_post; ++k) {
     if (k == nu_post && final_out) {
@@ -445,7 +462,7 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
 }  // namespace
 
 void Hierarchy::vcycle(cudaStream_t s) {
-  if (opts.precision == 1) vcycle_fp32(s);
+  if (opts.precision >= 1) vcycle_fp32(s);
   else vcycle_fp64(s);
 }
 

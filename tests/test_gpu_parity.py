@@ -190,6 +190,11 @@ def test_fp32_vcycle_close_to_fp64():
     b = np.random.default_rng(5).standard_normal(A[0].size - 1)
     x64, x32 = g64.vcycle(b), g32.vcycle(b)
     assert np.max(np.abs(x32 - x64)) <= 1e-4 * np.max(np.abs(x64))
+    # BF16 interpolation weights (8 significant bits): a nearby V-cycle
+    g16 = thermo.AMG(*A, precision=2)
+    x16 = g16.vcycle(b)
+    assert np.linalg.norm(x16 - x64) <= 2e-2 * np.linalg.norm(x64)
+    assert not np.array_equal(x16.astype(np.float32), x32.astype(np.float32))
 
 
 @pytest.mark.parametrize("variant", [0, 1])
@@ -226,7 +231,7 @@ def _oracle_scaled_residual(osys, obp, obT, xp, xT):
 
 
 @pytest.mark.parametrize("name", ["iid16", "ragged", "thin"])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_matches_direct_solution(name, precision):
     prob, p, T = problem(name)
     s, _, (osys, obp, obT, oS) = assemble_both(prob, p, T)
