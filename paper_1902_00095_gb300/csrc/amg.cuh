@@ -126,6 +126,7 @@ class Hierarchy {
   double* coarse_inv = nullptr;   // [nc*nc] row-major inverse of the coarsest A
   int nc = 0;
   Pool pool;
+  Pool scratch;   // setup temporaries (rewound after every level)
   double* coarse_dense = nullptr;   // [nc*nc] work for the inverse
   // host wall time of the setup phases (ms): strength + PMIS, interpolation,
   // transpose, Galerkin products, smoother scaling + coarse inverse

@@ -1079,12 +1079,14 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   k_spgemm_rows<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col,
                                                  B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
-  static int num_sms = 0;
-  if (!num_sms) {
-    int dev = 0;
+  // SM count and the big-row kernel's shared-memory opt-in, once per process
+  // (thread-safe static initialisation; hierarchies are set up concurrently)
+  static const int num_sms = []() {
+    int dev = 0, v = 0;
     TP_CUDA_TRY(cudaGetDevice(&dev));
-    TP_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+    TP_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    return v;
+  }();
   {
     long long blocks = (n + kSpWarps - 1) / kSpWarps;
     if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
@@ -1092,12 +1094,12 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
                                                              B.col, B.val, off, ub, ccol, cval, cnt);
   }
   TP_LAUNCH_CHECK();
-  static bool big_attr = false;
-  if (!big_attr) {
+  static const bool big_attr = []() {
     TP_CUDA_TRY(cudaFuncSetAttribute(k_spgemm_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kSpBigSmem));
-    big_attr = true;
-  }
+    return true;
+  }();
+  (void)big_attr;
   k_spgemm_rows_big<<<n < num_sms ? n : num_sms, kSpBigThreads, kSpBigSmem, s>>>(
       n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
@@ -1171,9 +1173,10 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
   for (double& x : phase_ms) x = 0.0;
   PhaseClock clk;
   pool.release();
+  scratch.release();
   L.clear();
   coarse_inv = nullptr;
-  Pool scratch;
+  cheb_partials = nullptr;
   err = pool.alloc<int>(2);
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   L.emplace_back();

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <thread>
 #include "solver.cuh"
 
 using tp::Error;
@@ -115,6 +116,9 @@ tp_ctx::~tp_ctx() {
   hpp.reset();
   hS.reset();
   if (host_est) cudaFreeHost(host_est);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (s2) cudaStreamDestroy(s2);
 }
 
 struct tp_amg {
@@ -1015,16 +1019,49 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
   DevCSR App{c->N, c->N, c->nnzb, c->rowptr, c->col, c->App, nullptr};
   DevCSR S{c->N, c->N, c->nnzb, c->rowptr, c->col, c->S_active, nullptr};
   c->opts = o;
-  c->hpp.reset(new Hierarchy());
-  c->hS.reset(new Hierarchy());
+  // the hierarchies are reused: their memory pools keep their chunks
+  if (!c->hpp) c->hpp.reset(new Hierarchy());
+  if (!c->hS) c->hS.reset(new Hierarchy());
   AmgOpts ao = amg_opts(o);
   AmgOpts aS = ao;
   if (o.interp_S >= 0) aS.interp = o.interp_S;
   if (o.max_levels_S > 0) aS.max_levels = o.max_levels_S;
   if (o.nu_S > 0) aS.nu_pre = aS.nu_post = o.nu_S;
   if (o.smoother_S >= 0) aS.smoother = o.smoother_S;
-  c->hpp->setup(App, ao, s);
-  c->hS->setup(S, aS, s);
+  // The two hierarchies are independent: S~'s is set up by a second host
+  // thread on a second stream while this thread sets up A_pp's (both setups
+  // are chains of small kernels with host round trips, so they overlap).
+  if (!c->s2) {
+    TP_CUDA_TRY(cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking));
+    TP_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    TP_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
+  TP_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+  TP_CUDA_TRY(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
+  Error terr{TP_OK, ""};
+  bool tfail = false;
+  std::thread th([&]() {
+    try {
+      TP_CUDA_TRY(cudaSetDevice(c->device));
+      c->hS->setup(S, aS, c->s2);
+    } catch (const Error& e) {
+      terr = e;
+      tfail = true;
+    } catch (...) {
+      terr = Error{TP_ECUDA, "Schur hierarchy setup failed"};
+      tfail = true;
+    }
+  });
+  try {
+    c->hpp->setup(App, ao, s);
+  } catch (...) {
+    th.join();
+    throw;
+  }
+  th.join();
+  if (tfail) throw terr;
+  TP_CUDA_TRY(cudaEventRecord(c->ev_join, c->s2));
+  TP_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   c->hpp->probe = c->probe_which == 0 ? &c->probe : nullptr;
   c->hS->probe = c->probe_which == 1 ? &c->probe : nullptr;
   if (o.use_graphs) {

@@ -37,32 +37,64 @@ extern thread_local bool g_capturing;
 inline void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 
 // ------------------------------------------------------------- allocation
-// Owns every device allocation of one object; freed together.
+// Owns the device memory of one object as a chain of chunks handed out by a
+// bump pointer (256-byte aligned). release() only rewinds: the chunks stay
+// allocated and the next build that allocates in the same order gets the
+// same addresses, so repeated setups make no cudaMalloc/cudaFree calls (a
+// cudaFree synchronises the device). Reuse is safe because every user
+// allocates and consumes on one stream, in order. The destructor frees.
 class Pool {
  public:
   Pool() = default;
   Pool(const Pool&) = delete;
   Pool& operator=(const Pool&) = delete;
-  ~Pool() { release(); }
+  ~Pool() { free_all(); }
   template <class T>
   T* alloc(size_t count) {
     if (count == 0) count = 1;
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      fail(TP_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes");
+    const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    while (cur_ < chunks_.size() && chunks_[cur_].used + bytes > chunks_[cur_].size) ++cur_;
+    if (cur_ == chunks_.size()) {
+      size_t want = next_ < bytes ? bytes : next_;
+      void* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, want);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(TP_ENOMEM, "cudaMalloc of " + std::to_string(want) + " bytes");
+      }
+      chunks_.push_back(Chunk{static_cast<char*>(p), want, 0});
+      if (next_ < (size_t(256) << 20)) next_ *= 2;
     }
-    ptrs_.push_back(p);
-    return static_cast<T*>(p);
+    Chunk& c = chunks_[cur_];
+    void* out = c.base + c.used;
+    c.used += bytes;
+    return static_cast<T*>(out);
   }
+  // rewind: every pointer handed out so far becomes invalid, memory is kept
   void release() {
-    for (void* p : ptrs_) cudaFree(p);
-    ptrs_.clear();
+    for (Chunk& c : chunks_) c.used = 0;
+    cur_ = 0;
+  }
+  void free_all() {
+    for (Chunk& c : chunks_) cudaFree(c.base);
+    chunks_.clear();
+    cur_ = 0;
+  }
+  size_t reserved() const {
+    size_t t = 0;
+    for (const Chunk& c : chunks_) t += c.size;
+    return t;
   }
 
  private:
-  std::vector<void*> ptrs_;
+  struct Chunk {
+    char* base;
+    size_t size;
+    size_t used;
+  };
+  std::vector<Chunk> chunks_;
+  size_t cur_ = 0;
+  size_t next_ = size_t(4) << 20;  // first chunk 4 MiB, doubling up to 256 MiB
 };
 
 // ---------------------------------------------------------------- CSR

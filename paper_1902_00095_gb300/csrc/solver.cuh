@@ -42,6 +42,8 @@ struct tp_ctx {
   // preconditioner
   tp_precond_opts opts{};
   std::unique_ptr<tp::Hierarchy> hpp, hS;
+  cudaStream_t s2 = nullptr;   // second stream: S~ hierarchy setup
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* S_active = nullptr;  // values of the Schur approximation used
   double *bp_s = nullptr, *bT_s = nullptr;
   bool built = false;
