@@ -44,12 +44,15 @@ struct AmgOpts {
 
 // CUDA-event timing of one kernel class inside the timed region: events are
 // recorded around each launch (as external event nodes when captured into a
-// graph) and read back after the host syncs the solver already does.
+// graph) and read back once the host has waited for them. Two event sets
+// alternate between consecutive solver iterations, so an iteration can be
+// enqueued while the previous one's events are read.
 struct Probe {
   static constexpr int kMaxPairs = 64;
-  cudaEvent_t ev[2 * kMaxPairs] = {};
+  cudaEvent_t ev[2][2 * kMaxPairs] = {};
   double bytes[kMaxPairs] = {};
-  int npairs = 0;
+  int npairs = 0;   // pairs per recorded sequence (the same for both sets)
+  int active = 0;   // set that before()/after() record into
   bool created = false;
   // accumulated over reads
   double total_ms = 0.0, total_bytes = 0.0;
@@ -58,7 +61,7 @@ struct Probe {
   void destroy();
   void before(cudaStream_t s);
   void after(cudaStream_t s, double algorithmic_bytes);
-  void read_and_accumulate();   // after a stream sync
+  void read_and_accumulate(int set);   // after the set's last event completed
 };
 
 struct Level {

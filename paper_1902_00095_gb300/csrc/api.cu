@@ -112,11 +112,14 @@ void check_opts(const tp_precond_opts& o) {
 
 tp_ctx::~tp_ctx() {
   if (pc_graph) cudaGraphExecDestroy(pc_graph);
+  if (pc_graph_tmpl) cudaGraphDestroy(pc_graph_tmpl);
   probe.destroy();
   hpp.reset();
   hS.reset();
   if (host_est) cudaFreeHost(host_est);
   if (ev_fork) cudaEventDestroy(ev_fork);
+  for (cudaEvent_t e : ev_est)
+    if (e) cudaEventDestroy(e);
   if (ev_join) cudaEventDestroy(ev_join);
   if (s2) cudaStreamDestroy(s2);
 }
@@ -270,7 +273,9 @@ int tp_create(tp_ctx** out, const tp_grid* grid, const tp_fluid* fluid, void* cu
   TP_CUDA_TRY(cudaMemcpyAsync(c->ones, one2, sizeof(one2), cudaMemcpyHostToDevice, s));
   c->nparts = std::max(1, std::min(2 * c->num_sms, (n + 255) / 256));
   c->partials = P.alloc<double>(c->nparts + 1);
-  TP_CUDA_TRY(cudaMallocHost(&c->host_est, 16 * sizeof(double)));
+  TP_CUDA_TRY(cudaMallocHost(&c->host_est, 32 * sizeof(double)));
+  for (int q = 0; q < 2; ++q)
+    TP_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_est[q], cudaEventDisableTiming));
   tp_default_opts(&c->opts);
   TP_CUDA_TRY(cudaStreamSynchronize(s));
   *out = c;
@@ -1007,6 +1012,12 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
     cudaGraphExecDestroy(c->pc_graph);
     c->pc_graph = nullptr;
   }
+  if (c->pc_graph_tmpl) {
+    cudaGraphDestroy(c->pc_graph_tmpl);
+    c->pc_graph_tmpl = nullptr;
+  }
+  c->probe_nodes.clear();
+  c->probe_set = 0;
   c->built = false;
   launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
   launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
@@ -1080,13 +1091,29 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
     TP_CUDA_TRY(cudaStreamEndCapture(s, &graph));
     size_t nodes = 0;
     TP_CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nodes));
-    c->pc_graph_kernels = (long long)nodes;
+    std::vector<cudaGraphNode_t> list(nodes);
+    if (nodes) TP_CUDA_TRY(cudaGraphGetNodes(graph, list.data(), &nodes));
+    long long kernels = 0;
+    for (cudaGraphNode_t nd : list) {
+      cudaGraphNodeType ty;
+      TP_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+      if (ty == cudaGraphNodeTypeKernel) ++kernels;
+      if (ty == cudaGraphNodeTypeEventRecord) {
+        cudaEvent_t ev = nullptr;
+        TP_CUDA_TRY(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        for (int k = 0; k < 2 * tp::Probe::kMaxPairs; ++k)
+          if (c->probe.created && c->probe.ev[0][k] == ev) c->probe_nodes.push_back({nd, k});
+      }
+    }
+    c->pc_graph_kernels = kernels;
     cudaError_t e = cudaGraphInstantiate(&c->pc_graph, graph, 0);
-    cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
       c->pc_graph = nullptr;
+      c->probe_nodes.clear();
       fail(TP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
+    c->pc_graph_tmpl = graph;
   }
   TP_CUDA_TRY(cudaStreamSynchronize(s));
   c->built = true;

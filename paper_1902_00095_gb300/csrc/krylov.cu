@@ -17,6 +17,7 @@ namespace tp {
 namespace {
 
 constexpr int kDotV = 8;  // vectors per multi-dot pass
+constexpr int kEstSlot = 16;  // pinned-buffer offset of the two convergence-estimate slots
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -132,36 +133,53 @@ __global__ void k_reduce_rows(int count, int B, const double* __restrict__ parti
   block_sum_store(v, &out[k]);
 }
 
-// w -= sum_k h_k V_k; optionally per-block partial sums of w^2
+// w -= sum_k h_k V_k; optionally per-block partial sums of w^2. Grid-stride
+// over elements (fixed grid, so the partition of the partial sums is fixed);
+// the k loop is unrolled by 8 so every thread keeps 8 independent loads of
+// V in flight.
 __global__ void __launch_bounds__(256) k_orth_update(long long n2, const double* __restrict__ V,
                                                      long long stride, int count,
                                                      const double* __restrict__ h,
                                                      double* __restrict__ w,
                                                      double* __restrict__ norm_partials) {
-  long long lo, hi;
-  chunk_of(n2, lo, hi);
+  const long long step = (long long)gridDim.x * blockDim.x;
   double nrm = 0.0;
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += step) {
     double a = w[i];
-    for (int k = 0; k < count; ++k) a -= h[k] * V[(long long)k * stride + i];
+    int k = 0;
+    for (; k + 8 <= count; k += 8) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = V[(long long)(k + q) * stride + i];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a -= h[k + q] * v[q];
+    }
+    for (; k < count; ++k) a -= h[k] * V[(long long)k * stride + i];
     w[i] = a;
     nrm += a * a;
   }
   if (norm_partials) block_sum_store(nrm, &norm_partials[blockIdx.x]);
 }
 
-// Arnoldi column j: H(:, j) = h1 + h2, H(j+1, j) = ||w||, Givens update.
-__global__ void k_arnoldi(int j, int ldh, double* __restrict__ H, double* __restrict__ cs,
-                          double* __restrict__ sn, double* __restrict__ g,
-                          const double* __restrict__ h1, const double* __restrict__ h2,
-                          const double* __restrict__ npart, int B, double* __restrict__ hn_out,
-                          double* __restrict__ est) {
+// Arnoldi column j: H(:, j) = h1 + h2, H(j+1, j) = ||w|| (the block sums the
+// B norm partials in a fixed tree order), Givens update by thread 0.
+__global__ void __launch_bounds__(256) k_arnoldi(int j, int ldh, double* __restrict__ H,
+                                                 double* __restrict__ cs,
+                                                 double* __restrict__ sn,
+                                                 double* __restrict__ g,
+                                                 const double* __restrict__ h1,
+                                                 const double* __restrict__ h2,
+                                                 const double* __restrict__ npart, int B,
+                                                 double* __restrict__ hn_out,
+                                                 double* __restrict__ est) {
+  __shared__ double tot;
+  double part = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) part += npart[b];
+  block_sum_store(part, &tot);
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* Hj = H + (long long)j * ldh;
   for (int k = 0; k <= j; ++k) Hj[k] = h1[k] + h2[k];
-  double s = 0.0;
-  for (int b = 0; b < B; ++b) s += npart[b];
-  const double hn = sqrt(s);
+  const double hn = sqrt(tot);
   Hj[j + 1] = hn;
   for (int k = 0; k < j; ++k) {
     const double t = cs[k] * Hj[k] + sn[k] * Hj[k + 1];
@@ -317,6 +335,14 @@ void mdot_all(long long n2, const double* V, long long stride, int count, const 
   TP_LAUNCH_CHECK();
 }
 
+// grid of k_orth_update: enough blocks for 8 resident per SM, at most one
+// element per thread
+int orth_grid(const tp_ctx* c, long long n) {
+  const long long want = (n + 255) / 256;
+  const long long cap = 8ll * c->num_sms;
+  return (int)std::max(1ll, std::min(want, cap));
+}
+
 double read_double(const double* d, double* host_pinned, cudaStream_t s) {
   TP_CUDA_TRY(cudaMemcpyAsync(host_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, s));
   TP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -342,6 +368,7 @@ void ensure_workspace(tp_ctx* c, int restart) {
   c->est = c->kpool.alloc<double>(4);
   c->h2 = c->kpool.alloc<double>(2 * (restart + 2));
   c->kparts = c->kpool.alloc<double>((size_t)(restart + 2) * 4 * c->nparts + 16);
+  c->oparts = c->kpool.alloc<double>((size_t)orth_grid(c, 2ll * c->N) + 16);
   c->restart_alloc = restart;
 }
 
@@ -463,15 +490,15 @@ int scalar_fgmres(tp_ctx* c, Hierarchy& h, const DevCSR& A, const double* b, dou
       TP_LAUNCH_CHECK();
       double* h1 = c->h2;
       double* h2 = c->h2 + (restart + 2);
+      const int G = orth_grid(c, n);
       mdot_all(n, c->Vb, n, j + 1, c->w, c->kparts, B, h1, s);
-      k_orth_update<<<B, 256, 0, s>>>(n, c->Vb, n, j + 1, h1, c->w, nullptr);
+      k_orth_update<<<G, 256, 0, s>>>(n, c->Vb, n, j + 1, h1, c->w, nullptr);
       TP_LAUNCH_CHECK();
       mdot_all(n, c->Vb, n, j + 1, c->w, c->kparts, B, h2, s);
-      double* npart = c->kparts + (long long)(restart + 2) * B;
-      k_orth_update<<<B, 256, 0, s>>>(n, c->Vb, n, j + 1, h2, c->w, npart);
+      k_orth_update<<<G, 256, 0, s>>>(n, c->Vb, n, j + 1, h2, c->w, c->oparts);
       TP_LAUNCH_CHECK();
-      k_arnoldi<<<1, 32, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, npart, B, c->hn,
-                                 c->est);
+      k_arnoldi<<<1, 256, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, c->oparts, G, c->hn,
+                                  c->est);
       TP_LAUNCH_CHECK();
       TP_CUDA_TRY(cudaMemcpyAsync(hp_host, c->est, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
       TP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -550,15 +577,24 @@ void precond_record(tp_ctx* c, cudaStream_t s) {
 }
 
 void precond_apply(tp_ctx* c, const double* vp, const double* vT, const double* scales,
-                   cudaStream_t s) {
+                   cudaStream_t s, int set) {
   const int N = c->N;
   k_precond_in<<<grid_for(N), kBlock, 0, s>>>(N, vp, vT, scales, c->bp_s, c->bT_s, c->hpp->in);
   TP_LAUNCH_CHECK();
   if (c->pc_graph) {
+    // point the graph's probe event nodes at this iteration's event set
+    if (!c->probe_nodes.empty() && c->probe_set != set) {
+      for (const auto& pn : c->probe_nodes)
+        TP_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(c->pc_graph, pn.first,
+                                                         c->probe.ev[set][pn.second]));
+      c->probe_set = set;
+    }
     TP_CUDA_TRY(cudaGraphLaunch(c->pc_graph, s));
     count_launch(c->pc_graph_kernels);
   } else {
+    c->probe.active = set;
     precond_record(c, s);
+    c->probe.active = 0;
   }
 }
 
@@ -617,50 +653,73 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
       if (its >= maxit || breakdown) break;
       k_start_cycle<<<grid_for(n2), kBlock, 0, s>>>(n2, r, c->hn, c->Vb, c->g, restart);
       TP_LAUNCH_CHECK();
+      // Iteration j is enqueued before the host looks at iteration j - 1's
+      // convergence estimate (copied to pinned memory behind an event), so
+      // the GPU never idles on the host; an iteration enqueued past the
+      // stopping point is discarded (m counts checked columns only, and it
+      // touches nothing that columns < m use).
       int m = 0;
-      for (int j = 0; j < restart; ++j) {
+      auto enqueue = [&](int j) {
         double* vj = c->Vb + (long long)j * n2;
         double* zj = c->Zb + (long long)j * n2;
-        precond_apply(c, vj, vj + N, c->scales, s);
+        precond_apply(c, vj, vj + N, c->scales, s, j & 1);
         const bool probe_spmv = c->probe_which == 2;
         if (probe_spmv) {
           c->probe.npairs = 0;
+          c->probe.active = j & 1;
           c->probe.before(s);
         }
         k_block_spmv<<<grid_for(N), kBlock, 0, s>>>(
             N, c->rowptr, c->col, reinterpret_cast<const double4_32a*>(c->bval), c->hpp->out,
             c->hS->out, zj, zj + N, c->w, c->w + N, c->scales);
         TP_LAUNCH_CHECK();
-        if (probe_spmv)
+        if (probe_spmv) {
           c->probe.after(s, 36.0 * c->nnzb + 4.0 * (N + 1) + 48.0 * N);
+          c->probe.active = 0;
+        }
         // CGS2 against V_0..V_j
         double* h1 = c->h2;
         double* h2 = c->h2 + (restart + 2);
+        const int G = orth_grid(c, n2);
         mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h1, s);
-        k_orth_update<<<B, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h1, c->w, nullptr);
+        k_orth_update<<<G, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h1, c->w, nullptr);
         TP_LAUNCH_CHECK();
         mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h2, s);
-        double* npart = c->kparts + (long long)(restart + 2) * B;
-        k_orth_update<<<B, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h2, c->w, npart);
+        k_orth_update<<<G, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h2, c->w, c->oparts);
         TP_LAUNCH_CHECK();
-        k_arnoldi<<<1, 32, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, npart, B, c->hn,
-                                   c->est);
+        k_arnoldi<<<1, 256, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, c->oparts, G,
+                                    c->hn, c->est);
         TP_LAUNCH_CHECK();
-        TP_CUDA_TRY(cudaMemcpyAsync(hp_host, c->est, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        TP_CUDA_TRY(cudaStreamSynchronize(s));
-        if (c->probe_which >= 0) c->probe.read_and_accumulate();
-        const double est = hp_host[0], hnv = hp_host[1], den = hp_host[2];
+        TP_CUDA_TRY(cudaMemcpyAsync(hp_host + kEstSlot + 4 * (j & 1), c->est, 3 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+        TP_CUDA_TRY(cudaEventRecord(c->ev_est[j & 1], s));
+        if (j + 1 < restart) {
+          k_normalize<<<grid_for(n2), kBlock, 0, s>>>(n2, c->w, c->hn,
+                                                      c->Vb + (long long)(j + 1) * n2);
+          TP_LAUNCH_CHECK();
+        }
+      };
+      // returns true when the cycle stops after column j (m set)
+      auto check = [&](int j) {
+        TP_CUDA_TRY(cudaEventSynchronize(c->ev_est[j & 1]));
+        if (c->probe_which >= 0) c->probe.read_and_accumulate(j & 1);
+        const double* e = hp_host + kEstSlot + 4 * (j & 1);
+        const double est = e[0], hnv = e[1], den = e[2];
         ++its;
         m = j + 1;
         if (!std::isfinite(est) || !std::isfinite(hnv) || !(den > 0.0)) {
           breakdown = true;  // drop the singular or non-finite column j
           m = j;
-          break;
+          return true;
         }
-        if (est <= rtol * bnorm || its >= maxit) break;
-        if (hnv == 0.0) break;  // happy breakdown: the solution is in the space
-        k_normalize<<<grid_for(n2), kBlock, 0, s>>>(n2, c->w, c->hn, c->Vb + (long long)(j + 1) * n2);
-        TP_LAUNCH_CHECK();
+        if (est <= rtol * bnorm || its >= maxit) return true;
+        if (hnv == 0.0) return true;  // happy breakdown: the solution is in the space
+        return false;
+      };
+      for (int j = 0; j < restart; ++j) {
+        if (j == 0) enqueue(0);
+        if (j + 1 < restart && its + 1 < maxit) enqueue(j + 1);
+        if (check(j)) break;
       }
       if (m > 0) {
         k_hsolve<<<1, 32, 0, s>>>(m, ldh, c->H, c->g, c->yv);

@@ -48,6 +48,11 @@ struct tp_ctx {
   double *bp_s = nullptr, *bT_s = nullptr;
   bool built = false;
   cudaGraphExec_t pc_graph = nullptr;
+  cudaGraph_t pc_graph_tmpl = nullptr;   // kept: its event nodes are re-pointed per launch
+  // probe event-record nodes of the preconditioner graph and the event index
+  // (within a probe set) each one records; probe_set = set they point at
+  std::vector<std::pair<cudaGraphNode_t, int>> probe_nodes;
+  int probe_set = 0;
   long long pc_graph_kernels = 0;
   // timing probe: -1 off, 0 finest A_pp sweeps, 1 finest S~ sweeps, 2 block SpMV
   int probe_which = -1;
@@ -58,7 +63,9 @@ struct tp_ctx {
   double *Vb = nullptr, *Zb = nullptr, *w = nullptr, *xs = nullptr, *bs = nullptr;
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
          *hn = nullptr, *est = nullptr, *kparts = nullptr, *h2 = nullptr;
-  double* host_est = nullptr;  // pinned
+  double* oparts = nullptr;    // norm partials of the orthogonalisation update
+  double* host_est = nullptr;  // pinned [32]
+  cudaEvent_t ev_est[2] = {nullptr, nullptr};  // convergence estimates of iterations j, j+1
   // learned Schur correction
   struct tp_mlp* model = nullptr;
   tp::Pool lpool;
@@ -82,7 +89,7 @@ long long launches_total();
 // z = M^{-1} D^{-1} v with D = diag(scales); result left in hpp->out, hS->out.
 void precond_record(tp_ctx* c, cudaStream_t s);
 void precond_apply(tp_ctx* c, const double* vp, const double* vT, const double* scales,
-                   cudaStream_t s);
+                   cudaStream_t s, int set = 0);
 int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, double* xT,
                  double rtol, int maxit, int restart, tp_solve_info* info);
 // device-resident steps shared by the C-ABI calls and the Newton driver

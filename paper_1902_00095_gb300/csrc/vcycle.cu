@@ -481,34 +481,38 @@ void Hierarchy::vcycle_fp32(cudaStream_t s) {
 // ------------------------------------------------------------------ probe
 void Probe::create() {
   if (created) return;
-  for (int k = 0; k < 2 * kMaxPairs; ++k) TP_CUDA_TRY(cudaEventCreate(&ev[k]));
+  for (int q = 0; q < 2; ++q)
+    for (int k = 0; k < 2 * kMaxPairs; ++k) TP_CUDA_TRY(cudaEventCreate(&ev[q][k]));
   created = true;
 }
 
 void Probe::destroy() {
   if (!created) return;
-  for (int k = 0; k < 2 * kMaxPairs; ++k) cudaEventDestroy(ev[k]);
+  for (int q = 0; q < 2; ++q)
+    for (int k = 0; k < 2 * kMaxPairs; ++k) cudaEventDestroy(ev[q][k]);
   created = false;
 }
 
 void Probe::before(cudaStream_t s) {
   if (npairs >= kMaxPairs) return;
-  if (g_capturing) TP_CUDA_TRY(cudaEventRecordWithFlags(ev[2 * npairs], s, cudaEventRecordExternal));
-  else TP_CUDA_TRY(cudaEventRecord(ev[2 * npairs], s));
+  cudaEvent_t e = ev[active][2 * npairs];
+  if (g_capturing) TP_CUDA_TRY(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+  else TP_CUDA_TRY(cudaEventRecord(e, s));
 }
 
 void Probe::after(cudaStream_t s, double algorithmic_bytes) {
   if (npairs >= kMaxPairs) return;
-  if (g_capturing) TP_CUDA_TRY(cudaEventRecordWithFlags(ev[2 * npairs + 1], s, cudaEventRecordExternal));
-  else TP_CUDA_TRY(cudaEventRecord(ev[2 * npairs + 1], s));
+  cudaEvent_t e = ev[active][2 * npairs + 1];
+  if (g_capturing) TP_CUDA_TRY(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+  else TP_CUDA_TRY(cudaEventRecord(e, s));
   bytes[npairs] = algorithmic_bytes;
   ++npairs;
 }
 
-void Probe::read_and_accumulate() {
+void Probe::read_and_accumulate(int set) {
   for (int k = 0; k < npairs; ++k) {
     float ms = 0.f;
-    TP_CUDA_TRY(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+    TP_CUDA_TRY(cudaEventElapsedTime(&ms, ev[set][2 * k], ev[set][2 * k + 1]));
     total_ms += ms;
     total_bytes += bytes[k];
     ++launches;
