@@ -51,6 +51,7 @@ struct Probe {
   static constexpr int kMaxPairs = 64;
   cudaEvent_t ev[2][2 * kMaxPairs] = {};
   double bytes[kMaxPairs] = {};
+  int nlaunch[kMaxPairs] = {};   // kernel launches between the two events of a pair
   int npairs = 0;   // pairs per recorded sequence (the same for both sets)
   int active = 0;   // set that before()/after() record into
   bool created = false;
@@ -60,7 +61,7 @@ struct Probe {
   void create();
   void destroy();
   void before(cudaStream_t s);
-  void after(cudaStream_t s, double algorithmic_bytes);
+  void after(cudaStream_t s, double algorithmic_bytes, int launches_in_span = 1);
   void read_and_accumulate(int set);   // after the set's last event completed
 };
 

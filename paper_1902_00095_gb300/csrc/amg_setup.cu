@@ -1051,10 +1051,24 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ A, double* __restrict
   }
 }
 
+// threads per CSR row in the V-cycle kernels: a power of two giving each
+// lane about 4 entries (fewer lanes mean fewer shuffle steps per row, more
+// mean more parallelism on short coarse levels), halved while the launch
+// would exceed four waves of resident threads (FGMRES time per iteration on
+// the 64x64x32 / 128x128x64 hierarchies, against 4 entries per lane without
+// the cap: 2 entries +1 % / +18 %, 8 entries +8 % / -7 %)
 int pick_lanes(const DevCSR& A) {
-  double avg = A.n > 0 ? (double)A.nnz / A.n : 1.0;
+  static const long long resident = []() {
+    int dev = 0, sms = 0, thr = 0;
+    TP_CUDA_TRY(cudaGetDevice(&dev));
+    TP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TP_CUDA_TRY(cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    return (long long)sms * thr;
+  }();
+  const double avg = A.n > 0 ? (double)A.nnz / A.n : 1.0;
   int l = 1;
-  while (l * 2 <= avg && l < 32) l *= 2;
+  while (l * 4.0 <= avg && l < 32) l *= 2;
+  while (l > 1 && (long long)A.n * l > 4 * resident) l /= 2;
   return l;
 }
 

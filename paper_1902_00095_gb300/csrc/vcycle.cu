@@ -447,15 +447,23 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s);
   if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
   else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
-  // post-smoothing
+  // post-smoothing; on the probed level one event pair spans all sweeps
+  // (one pair per launch would put an event node between every two kernels)
+  Probe* span = (pr && sm.kind == 0) ? pr : nullptr;
+  double span_bytes = 0.0;
+  if (span) span->before(s);
   for (int k = 1; k <= nu_post; ++k) {
     if (k == nu_post && final_out) {
-      smooth_step<TV, TB, TO>(sm, pr, v, dinv, b, cur, final_out, s);
+      smooth_step<TV, TB, TO>(sm, nullptr, v, dinv, b, cur, final_out, s);
+      span_bytes += sweep_bytes<TV, TB, TO>(v.A);
+      if (span) span->after(s, span_bytes, nu_post);
       return nullptr;
     }
-    smooth_step<TV, TB, TV>(sm, pr, v, dinv, b, cur, oth, s);
+    smooth_step<TV, TB, TV>(sm, nullptr, v, dinv, b, cur, oth, s);
+    span_bytes += sweep_bytes<TV, TB, TV>(v.A);
     std::swap(cur, oth);
   }
+  if (span) span->after(s, span_bytes, nu_post);
   return cur;
 }
 
@@ -500,12 +508,13 @@ void Probe::before(cudaStream_t s) {
   else TP_CUDA_TRY(cudaEventRecord(e, s));
 }
 
-void Probe::after(cudaStream_t s, double algorithmic_bytes) {
+void Probe::after(cudaStream_t s, double algorithmic_bytes, int launches_in_span) {
   if (npairs >= kMaxPairs) return;
   cudaEvent_t e = ev[active][2 * npairs + 1];
   if (g_capturing) TP_CUDA_TRY(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
   else TP_CUDA_TRY(cudaEventRecord(e, s));
   bytes[npairs] = algorithmic_bytes;
+  nlaunch[npairs] = launches_in_span;
   ++npairs;
 }
 
@@ -515,7 +524,7 @@ void Probe::read_and_accumulate(int set) {
     TP_CUDA_TRY(cudaEventElapsedTime(&ms, ev[set][2 * k], ev[set][2 * k + 1]));
     total_ms += ms;
     total_bytes += bytes[k];
-    ++launches;
+    launches += nlaunch[k];
   }
 }
 
