@@ -81,7 +81,10 @@ typedef struct {
 
 /* Preconditioner options (defaults from tp_default_opts). */
 typedef struct {
-  int schur;        /* 0: S~_T of Eq. Se; 2: S~_ATT = A_TT (Sec. 3.3)          */
+  int schur;        /* 0: S~_T of Eq. Se; 1: S~_T with the learned correction */
+                    /* (tp_set_schur_model); 2: S~_ATT = A_TT; 3: S~_diag =   */
+                    /* A_TT - A_Tp diag(A_pp)^-1 A_pT on its 25-point pattern */
+                    /* (Sec. 3.3)                                              */
   int variant;      /* 0: full five-step apply (Sec. 3.2); 1: block lower     */
                     /*    triangular (steps 1-3, delta_p = x_p)               */
   int precision;    /* 0: FP64 hierarchy; 1: FP32 hierarchy values, smoothers */

@@ -177,6 +177,8 @@ def solve(prob, rtol=1e-8, maxit=300, restart=30, theta=0.25, seed=0,
     sys, bp, bT, S = assemble(prob, p, T)
     if schur == "att":
         S = sys.ATT
+    elif schur == "diag":
+        S = physics.schur_diag_sparse(sys.rowptr, sys.col, sys.val)
     h_pp = amg.setup(sys.App, theta, seed, coarse_size, smoother=smoother,
                      interp=interp, cheb_degree=cheb_degree, pmax=pmax)
     h_S = amg.setup(S, theta, seed, coarse_size, smoother=smoother_S,

@@ -359,6 +359,39 @@ def schur_att(val):
     return val[:, 1, 1].copy()
 
 
+def schur_diag_sparse(rowptr, col, val):
+    """S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3) as CSR on the
+    structural pattern of A_Tp A_pT (the 25-point stencil, which contains
+    A_TT's 7 points). Evaluation order: b_kj = (A_pT)_kj / (A_pp)_kk, one
+    division per entry; (A_Tp B)_ij = 0.0 + sum over k ascending of
+    (A_Tp)_ik b_kj, one rounded product and one rounded sum at a time;
+    S_ij = (A_TT)_ij - (A_Tp B)_ij, or -(A_Tp B)_ij off A_TT's pattern.
+    Returns (rowptr, col, values)."""
+    N = rowptr.size - 1
+    dpos = block_positions(rowptr, col, np.arange(N), np.arange(N))
+    App = val[dpos, 0, 0]
+    B = val[:, 0, 1].copy()
+    for k in range(N):
+        for e in range(rowptr[k], rowptr[k + 1]):
+            B[e] = val[e, 0, 1] / App[k]
+    rows = []
+    for i in range(N):
+        acc = {}
+        for e in range(rowptr[i], rowptr[i + 1]):
+            k = col[e]
+            a = val[e, 1, 0]
+            for f in range(rowptr[k], rowptr[k + 1]):
+                j = int(col[f])
+                acc[j] = acc.get(j, 0.0) + a * B[f]
+        att = {int(col[e]): val[e, 1, 1] for e in range(rowptr[i], rowptr[i + 1])}
+        rows.append([(j, att[j] - c if j in att else -c) for j, c in sorted(acc.items())])
+    S_rp = np.zeros(N + 1, np.int64)
+    S_rp[1:] = np.cumsum([len(r) for r in rows])
+    S_c = np.array([j for r in rows for (j, _) in r], dtype=np.int64)
+    S_v = np.array([v for r in rows for (_, v) in r], dtype=np.float64)
+    return S_rp, S_c, S_v
+
+
 def schur_diag(rowptr, col, val):
     """S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3). With a 7-point
     A_Tp and A_pT the product has a wider pattern; it is returned as a dense

@@ -155,6 +155,11 @@ void chebyshev_apply(const Level& v, const TV* val, const TV* dinv, int degree, 
                      const TV* xin, TO* xout, cudaStream_t s);
 
 // Standalone sparse helpers reused by the solver.
+// C = A B in the hierarchy's canonical summation order (C's arrays from
+// `pool`), and the numeric-only recomputation of C's values on its pattern.
+DevCSR csr_product(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch,
+                   cudaStream_t s);
+void csr_product_numeric(const DevCSR& A, const DevCSR& B, const DevCSR& C, cudaStream_t s);
 void csr_transpose_positions(const DevCSR& A, int* tpos, int* err, cudaStream_t s);
 
 }  // namespace tp

@@ -1155,6 +1155,17 @@ DevCSR transpose(const DevCSR& P, Pool& pool, Pool& scratch, cudaStream_t s) {
 
 }  // namespace
 
+DevCSR csr_product(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch,
+                   cudaStream_t s) {
+  return spgemm(A, B, pool, scratch, s);
+}
+
+void csr_product_numeric(const DevCSR& A, const DevCSR& B, const DevCSR& C, cudaStream_t s) {
+  k_spgemm_numeric<<<grid_for(A.n, 128), 128, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr,
+                                                      B.col, B.val, C.rowptr, C.col, C.val);
+  TP_LAUNCH_CHECK();
+}
+
 void csr_transpose_positions(const DevCSR& A, int* tpos, int* err, cudaStream_t s) {
   k_transpose_pos<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, tpos, err);
   TP_LAUNCH_CHECK();

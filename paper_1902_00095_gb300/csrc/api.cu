@@ -92,7 +92,8 @@ tp::AmgOpts amg_opts(const tp_precond_opts& o) {
 }
 
 void check_opts(const tp_precond_opts& o) {
-  if (o.schur < 0 || o.schur > 2) fail(TP_EINVAL, "schur must be 0 (S~_T), 1 (learned) or 2 (A_TT)");
+  if (o.schur < 0 || o.schur > 3)
+    fail(TP_EINVAL, "schur must be 0 (S~_T), 1 (learned), 2 (A_TT) or 3 (S~_diag)");
   if (o.variant != 0 && o.variant != 1) fail(TP_EINVAL, "variant must be 0 or 1");
   if (o.precision < 0 || o.precision > 2) fail(TP_EINVAL, "precision must be 0, 1 or 2");
   if (o.interp != 0 && o.interp != 1) fail(TP_EINVAL, "interp must be 0 or 1");
@@ -1006,6 +1007,60 @@ void learned_schur_values(tp_ctx* c) {
   c->learned_global_fallback = 4ll * c->learned_fallback_rows > c->N;
 }
 
+namespace {
+// b_e = (A_pT)_e / (A_pp)_kk over row k (one correctly rounded division)
+__global__ void k_scale_by_diag(int N, const int* __restrict__ rowptr,
+                                const int* __restrict__ dpos, const double* __restrict__ App,
+                                const double* __restrict__ ApT, double* __restrict__ B) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const double d = App[dpos[k]];
+  for (int e = rowptr[k]; e < rowptr[k + 1]; ++e) B[e] = __ddiv_rn(ApT[e], d);
+}
+
+// S = A_TT - C on C's pattern (A_TT's 7-point pattern is contained in it)
+__global__ void k_schur_diag_merge(int N, const int* __restrict__ Crp, const int* __restrict__ Ccol,
+                                   const double* __restrict__ Cval, const int* __restrict__ rowptr,
+                                   const int* __restrict__ col, const double* __restrict__ ATT,
+                                   double* __restrict__ S) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int q = rowptr[i];
+  const int q1 = rowptr[i + 1];
+  for (int e = Crp[i]; e < Crp[i + 1]; ++e) {
+    const int j = Ccol[e];
+    while (q < q1 && col[q] < j) ++q;
+    S[e] = (q < q1 && col[q] == j) ? __dsub_rn(ATT[q], Cval[e]) : -Cval[e];
+  }
+}
+}  // namespace
+
+// S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3) on the 25-point
+// product pattern; `symbolic` rebuilds the pattern, else only the values
+void schur_diag_values(tp_ctx* c, bool symbolic) {
+  cudaStream_t s = c->s;
+  const int N = c->N;
+  if (symbolic) {
+    c->dpool.release();
+    c->dscratch.release();
+    c->Bd = c->dpool.alloc<double>(c->nnzb);
+  }
+  k_scale_by_diag<<<grid_for(N), kBlock, 0, s>>>(N, c->rowptr, c->dpos, c->App, c->ApT, c->Bd);
+  TP_LAUNCH_CHECK();
+  DevCSR ATp{N, N, c->nnzb, c->rowptr, c->col, c->ATp, nullptr};
+  DevCSR B{N, N, c->nnzb, c->rowptr, c->col, c->Bd, nullptr};
+  if (symbolic) {
+    c->Cd = csr_product(ATp, B, c->dpool, c->dscratch, s);
+    c->Sd = c->Cd;
+    c->Sd.val = c->dpool.alloc<double>(c->Cd.nnz);
+  } else {
+    csr_product_numeric(ATp, B, c->Cd, s);
+  }
+  k_schur_diag_merge<<<grid_for(N), kBlock, 0, s>>>(N, c->Cd.rowptr, c->Cd.col, c->Cd.val,
+                                                    c->rowptr, c->col, c->ATT, c->Sd.val);
+  TP_LAUNCH_CHECK();
+}
+
 void build_device(tp_ctx* c, const tp_precond_opts& o) {
   cudaStream_t s = c->s;
   if (c->pc_graph) {
@@ -1029,6 +1084,11 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
   }
   DevCSR App{c->N, c->N, c->nnzb, c->rowptr, c->col, c->App, nullptr};
   DevCSR S{c->N, c->N, c->nnzb, c->rowptr, c->col, c->S_active, nullptr};
+  if (o.schur == 3) {
+    schur_diag_values(c, true);
+    S = c->Sd;
+    c->S_active = c->Sd.val;
+  }
   c->opts = o;
   // the hierarchies are reused: their memory pools keep their chunks
   if (!c->hpp) c->hpp.reset(new Hierarchy());
@@ -1129,6 +1189,7 @@ void refresh_device(tp_ctx* c) {
       TP_CUDA_TRY(cudaMemcpyAsync(c->S_learned, c->Sval, sizeof(double) * c->nnzb,
                                   cudaMemcpyDeviceToDevice, s));
   }
+  if (c->opts.schur == 3) schur_diag_values(c, false);
   c->hpp->refresh(s);
   c->hS->refresh(s);
 }

@@ -42,6 +42,10 @@ struct tp_ctx {
   // preconditioner
   tp_precond_opts opts{};
   std::unique_ptr<tp::Hierarchy> hpp, hS;
+  // S~_diag (schur = 3): B = diag(A_pp)^-1 A_pT, C = A_Tp B, S = A_TT - C
+  tp::Pool dpool, dscratch;
+  double* Bd = nullptr;
+  tp::DevCSR Cd, Sd;
   cudaStream_t s2 = nullptr;   // second stream: S~ hierarchy setup
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* S_active = nullptr;  // values of the Schur approximation used

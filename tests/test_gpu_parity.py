@@ -390,3 +390,41 @@ def test_newton_line_search_matches_oracle():
     assert info["line_search_halvings"] == halvings
     assert np.linalg.norm(p - po) <= 1e-6 * np.linalg.norm(po - prob["p_n"])
     assert np.linalg.norm(T - To) <= 1e-6 * np.linalg.norm(To - prob["T_n"])
+
+
+@pytest.mark.parametrize("name", ["iid16", "ragged"])
+def test_schur_diag_matches_oracle(name):
+    """S~_diag (schur = 3): the GPU's 25-point matrix (level 0 of its Schur
+    hierarchy) has the oracle's pattern exactly and its values to rounding
+    (each side assembled its own Jacobian), and the block-preconditioned
+    solve reaches the direct solution with the oracle's iteration count."""
+    prob, p, T = problem(name)
+    s, _, (osys, obp, obT, oS) = assemble_both(prob, p, T)
+    s.build(schur=3)
+    g = s.export_level(1, 0)
+    rp, c, v = ophys.schur_diag_sparse(osys.rowptr, osys.col, osys.val)
+    assert np.array_equal(g["A"][0], rp) and np.array_equal(g["A"][1], c)
+    assert np.max(np.abs(g["A"][2] - v)) <= 1e-11 * np.max(np.abs(v))
+    xp, xT, info = s.solve(rtol=1e-10, maxit=400)
+    assert info["status"] == 0
+    rpv, rTv = okry.direct_solution(osys, obp, obT)
+    assert _errors(xp, xT, rpv, rTv)[0] <= 1e-6
+    o = okry.solve(prob, rtol=1e-10, p=p, T=T, schur="diag")
+    assert abs(info["iters"] - o["iters"]) <= 2, (info["iters"], o["iters"])
+
+
+def test_schur_diag_newton_refresh_matches_rebuild():
+    """Newton with structure reuse refreshes S~_diag's values in place: two
+    Newton iterations with and without reuse end at the same state."""
+    prob = make_problem("tiny", shape=(12, 10, 6), seed=5, dt_days=0.5)
+    prob["wells"][0]["value"] = 2e-4
+    prob["wells"][1]["value"] = 14.8e6
+    out = []
+    for reuse in (False, True):
+        s = gpu_solver(prob)
+        p, T, info = s.newton_step(prob["p_n"], prob["T_n"], prob["dt"], max_newton=2,
+                                   tol_f=0.0, tol_dx=0.0, rtol=1e-11, reuse=reuse, schur=3)
+        assert info["last_linear_status"] == 0
+        out.append((p, T))
+    assert np.linalg.norm(out[0][0] - out[1][0]) <= 1e-8 * np.linalg.norm(out[0][0] - prob["p_n"])
+    assert np.linalg.norm(out[0][1] - out[1][1]) <= 1e-8 * np.linalg.norm(out[0][1] - prob["T_n"])

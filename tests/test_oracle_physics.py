@@ -200,3 +200,25 @@ def test_block_pattern_is_seven_point_and_sorted():
     for i in range(N):
         c = col[rowptr[i]:rowptr[i + 1]]
         assert np.all(np.diff(c) > 0) and i in c
+
+
+def test_sparse_schur_diag_equals_the_dense_formula():
+    """S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3): the sparse
+    evaluation on the 25-point pattern equals the dense matrix product, and
+    its pattern is the product pattern of two 7-point stencils (offsets
+    with |dx| + |dy| + |dz| <= 2)."""
+    prob = tiny((5, 4, 3))
+    p, T = perturbed_state(prob, seed=2)
+    rowptr, col, val = physics.jacobian(prob, p, T)
+    rp, c, v = physics.schur_diag_sparse(rowptr, col, val)
+    D = physics.schur_diag(rowptr, col, val)
+    N = rowptr.size - 1
+    S = np.zeros((N, N))
+    rows = np.repeat(np.arange(N), np.diff(rp))
+    S[rows, c] = v
+    assert np.max(np.abs(S - D)) <= 1e-13 * np.max(np.abs(D))
+    nx, ny = prob["nx"], prob["ny"]
+    xyz = lambda i: np.array([i % nx, (i // nx) % ny, i // (nx * ny)])
+    for i in range(N):
+        want = [j for j in range(N) if np.abs(xyz(i) - xyz(j)).sum() <= 2]
+        assert list(c[rp[i]:rp[i + 1]]) == want
