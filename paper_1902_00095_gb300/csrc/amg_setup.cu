@@ -18,6 +18,8 @@ namespace {
 
 constexpr signed char kC = 1, kF = -1, kU = 0;
 
+int setup_sms();
+
 // index of key in a[lo, hi) (ascending), or -1
 __device__ __forceinline__ int find_in(const int* __restrict__ a, int lo, int hi, int key) {
   int h = hi;
@@ -164,6 +166,10 @@ __global__ void k_classical_count(int n, const int* __restrict__ rp, const int* 
   cnt[i] = c;
 }
 
+// rows longer than kClsShort are filled by a warp (k_classical_fill_warp)
+constexpr int kClsShort = 24;
+constexpr int kClsWarps = 4;
+
 __global__ void k_classical_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
                                  const double* __restrict__ val, const int* __restrict__ dpos,
                                  const unsigned char* __restrict__ strong,
@@ -172,6 +178,7 @@ __global__ void k_classical_fill(int n, const int* __restrict__ rp, const int* _
                                  int* __restrict__ Pcol, double* __restrict__ Pval) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (rp[i + 1] - rp[i] > kClsShort) return;  // k_classical_fill_warp
   const int p0 = Prp[i], p1 = Prp[i + 1];
   if (state[i] == kC) {
     Pcol[p0] = cidx[i];
@@ -219,6 +226,95 @@ __global__ void k_classical_fill(int n, const int* __restrict__ rp, const int* _
   for (int s = p0; s < p1; ++s) Pval[s] = __ddiv_rn(-Pval[s], denom);
 }
 
+// The same weights for long rows, one warp per row and the same arithmetic
+// in the same order: the entries of row i are visited in order (the
+// denominator is a sequential sum); for a strong F neighbour k the lanes
+// evaluate the selection predicate over row k in parallel, the sum s runs
+// over the selected values in column order (broadcast lane by lane), and
+// each selected entry updates its own weight (distinct columns of row k hit
+// distinct weights, so the per-weight order of updates is unchanged).
+__global__ void __launch_bounds__(32 * kClsWarps) k_classical_fill_warp(
+    int n, const int* __restrict__ rp, const int* __restrict__ col,
+    const double* __restrict__ val, const int* __restrict__ dpos,
+    const unsigned char* __restrict__ strong, const signed char* __restrict__ state,
+    const int* __restrict__ cidx, const int* __restrict__ Prp, int* __restrict__ Pcol,
+    double* __restrict__ Pval) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  for (int i = blockIdx.x * kClsWarps + w; i < n; i += gridDim.x * kClsWarps) {
+    const int r0 = rp[i], r1 = rp[i + 1];
+    if (r1 - r0 <= kClsShort) continue;  // uniform over the warp
+    const int p0 = Prp[i], p1 = Prp[i + 1];
+    if (state[i] == kC) {
+      if (lane == 0) {
+        Pcol[p0] = cidx[i];
+        Pval[p0] = 1.0;
+      }
+      continue;
+    }
+    if (p0 == p1) continue;
+    // columns and numerator start a_ij, in row order
+    int q = p0;
+    for (int e0 = r0; e0 < r1; e0 += 32) {
+      const int e = e0 + lane;
+      const bool sel = e < r1 && strong[e] && state[col[e]] == kC;
+      const unsigned m = __ballot_sync(0xffffffffu, sel);
+      if (sel) {
+        Pcol[q + __popc(m & below)] = cidx[col[e]];
+        Pval[q + __popc(m & below)] = val[e];
+      }
+      q += __popc(m);
+    }
+    __syncwarp();
+    double denom = val[dpos[i]];
+    for (int e = r0; e < r1; ++e) {
+      const int k = col[e];
+      if (k == i) continue;
+      if (!strong[e]) {
+        denom = __dadd_rn(denom, val[e]);
+        continue;
+      }
+      if (state[k] == kC) continue;
+      const double akk = val[dpos[k]];
+      const int f1 = rp[k + 1];
+      double sk = 0.0;
+      for (int f0 = rp[k]; f0 < f1; f0 += 32) {
+        const int f = f0 + lane;
+        bool sel = false;
+        double v = 0.0;
+        if (f < f1) {
+          v = val[f];
+          sel = opposite(v, akk) && is_strong_c(rp, col, strong, state, i, col[f]);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, sel);
+        for (unsigned mm = m; mm; mm &= mm - 1u) {
+          const int src = __ffs(mm) - 1;
+          sk = __dadd_rn(sk, __shfl_sync(0xffffffffu, v, src));
+        }
+        if (m == 0u) continue;
+      }
+      if (sk == 0.0) {
+        denom = __dadd_rn(denom, val[e]);
+        continue;
+      }
+      const double t = __ddiv_rn(val[e], sk);
+      for (int f0 = rp[k]; f0 < f1; f0 += 32) {
+        const int f = f0 + lane;
+        if (f < f1) {
+          const int m = col[f];
+          if (opposite(val[f], akk) && is_strong_c(rp, col, strong, state, i, m)) {
+            const int slot = find_in(Pcol, p0, p1, cidx[m]);
+            Pval[slot] = __dadd_rn(Pval[slot], __dmul_rn(t, val[f]));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    for (int sI = p0 + lane; sI < p1; sI += 32) Pval[sI] = __ddiv_rn(-Pval[sI], denom);
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------- extended+i interpolation
 __global__ void k_extpi_ub(int n, const int* __restrict__ rp, const int* __restrict__ col,
                            const unsigned char* __restrict__ strong,
@@ -250,17 +346,25 @@ __device__ __forceinline__ void insert_unique(int* __restrict__ buf, int& u, int
   ++u;
 }
 
-// interpolatory set C^_i (sorted fine indices) of every F row
+// rows whose candidate bound exceeds kSetShort build their set with a warp
+constexpr int kSetShort = 48;
+constexpr int kSetWarps = 4;
+constexpr int kSetCap = 1024;   // candidates sorted in shared memory (else serial)
+
+// interpolatory set C^_i (sorted fine indices) of every F row with at most
+// kSetShort candidates: one thread per row, insertion into a sorted list
 __global__ void k_extpi_sets(int n, const int* __restrict__ rp, const int* __restrict__ col,
                              const unsigned char* __restrict__ strong,
                              const signed char* __restrict__ state, const int* __restrict__ off,
-                             int* __restrict__ buf, int* __restrict__ cnt) {
+                             const int* __restrict__ ub, int* __restrict__ buf,
+                             int* __restrict__ cnt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (state[i] == kC) {
     cnt[i] = 1;
     return;
   }
+  if (ub[i] > kSetShort) return;  // k_extpi_sets_warp
   int* b = buf + off[i];
   int u = 0;
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
@@ -276,6 +380,121 @@ __global__ void k_extpi_sets(int n, const int* __restrict__ rp, const int* __res
     }
   }
   cnt[i] = u;
+}
+
+// the same sets for F rows with more than kSetShort candidates, one warp per
+// row: candidates (C neighbours, strong C neighbours of strong F neighbours)
+// are appended to the row's buffer, then sorted (bitonic, shared memory) and
+// made unique; the result is the same sorted set as the serial kernel's
+__global__ void __launch_bounds__(32 * kSetWarps) k_extpi_sets_warp(
+    int n, const int* __restrict__ rp, const int* __restrict__ col,
+    const unsigned char* __restrict__ strong, const signed char* __restrict__ state,
+    const int* __restrict__ off, const int* __restrict__ ub, int* __restrict__ buf,
+    int* __restrict__ cnt) {
+  __shared__ int s_list[kSetWarps][kSetCap];
+  __shared__ int s_n[kSetWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  for (int i = blockIdx.x * kSetWarps + w; i < n; i += gridDim.x * kSetWarps) {
+    if (state[i] == kC || ub[i] <= kSetShort) continue;  // uniform over the warp
+    int* b = buf + off[i];
+    if (lane == 0) s_n[w] = 0;
+    __syncwarp();
+    const int r0 = rp[i], r1 = rp[i + 1];
+    for (int e0 = r0; e0 < r1; e0 += 32) {
+      const int e = e0 + lane;
+      const bool act = e < r1;
+      const int k = act ? col[e] : -1;
+      const bool st = act && k != i && strong[e];
+      const bool isc = st && state[k] == kC;
+      const unsigned cm = __ballot_sync(0xffffffffu, isc);
+      int base = 0;
+      if (lane == 0) {
+        base = s_n[w];
+        s_n[w] = base + __popc(cm);
+      }
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (isc) b[base + __popc(cm & below)] = k;
+      __syncwarp();
+      unsigned fm = __ballot_sync(0xffffffffu, st && !isc);
+      while (fm) {
+        const int src = __ffs(fm) - 1;
+        fm &= fm - 1u;
+        const int kk = __shfl_sync(0xffffffffu, k, src);
+        const int f1 = rp[kk + 1];
+        for (int f0 = rp[kk]; f0 < f1; f0 += 32) {
+          const int f = f0 + lane;
+          const bool a2 = f < f1;
+          const int m = a2 ? col[f] : -1;
+          const bool c2 = a2 && m != kk && strong[f] && state[m] == kC;
+          const unsigned mm = __ballot_sync(0xffffffffu, c2);
+          int b2 = 0;
+          if (lane == 0) {
+            b2 = s_n[w];
+            s_n[w] = b2 + __popc(mm);
+          }
+          b2 = __shfl_sync(0xffffffffu, b2, 0);
+          if (c2) b[b2 + __popc(mm & below)] = m;
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+    const int total = s_n[w];
+    if (total > kSetCap) {
+      // rare: the serial insertion rebuilds the set from the row itself
+      if (lane == 0) {
+        int u = 0;
+        for (int e = r0; e < r1; ++e) {
+          const int k = col[e];
+          if (k == i || !strong[e]) continue;
+          if (state[k] == kC) {
+            insert_unique(b, u, k);
+          } else {
+            for (int f = rp[k]; f < rp[k + 1]; ++f) {
+              const int m = col[f];
+              if (strong[f] && state[m] == kC && m != k) insert_unique(b, u, m);
+            }
+          }
+        }
+        cnt[i] = u;
+      }
+      __syncwarp();
+      continue;
+    }
+    int P = 32;
+    while (P < total) P <<= 1;
+    int* L = s_list[w];
+    for (int t = lane; t < P; t += 32) L[t] = t < total ? b[t] : 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < P; t += 32) {
+          const int u = t ^ j;
+          if (u > t) {
+            const int a = L[t], c = L[u];
+            const bool up = (t & k) == 0;
+            if ((a > c) == up) {
+              L[t] = c;
+              L[u] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // unique, in order
+    int outn = 0;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const bool keep = t < total && (t == 0 || L[t] != L[t - 1]);
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      if (keep) b[outn + __popc(km & below)] = L[t];
+      outn += __popc(km);
+    }
+    if (lane == 0) cnt[i] = outn;
+    __syncwarp();
+  }
 }
 
 __device__ void extpi_fill_row_serial(int i, const int* __restrict__ rp, const int* __restrict__ col,
@@ -621,6 +840,61 @@ __global__ void k_spgemm_rows(int n, const int* __restrict__ Arp, const int* __r
     }
   }
   cnt[i] = u;
+}
+
+// Products whose result has few columns (m <= kDenseCap: the Galerkin
+// products of coarse levels): one warp per row accumulates into a dense
+// shared-memory row. The entries of row i of A are visited in order and the
+// lanes split row k of B (whose columns are distinct), so every column's sum
+// still starts at 0.0 and adds its products in ascending k: the canonical
+// order. Touched columns are flagged and compacted in column order.
+constexpr int kDenseCap = 2048;
+constexpr int kDenseWarps = 4;
+constexpr size_t kDenseSmem = (size_t)kDenseWarps * kDenseCap * (sizeof(double) + 1);
+
+__global__ void __launch_bounds__(32 * kDenseWarps) k_spgemm_dense(
+    int n, int m, const int* __restrict__ Arp, const int* __restrict__ Acol,
+    const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
+    const double* __restrict__ Bval, const int* __restrict__ off, int* __restrict__ ccol,
+    double* __restrict__ cval, int* __restrict__ cnt) {
+  extern __shared__ double s_dense[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  double* acc = s_dense + (size_t)w * m;
+  unsigned char* flg = reinterpret_cast<unsigned char*>(s_dense + (size_t)kDenseWarps * m) +
+                       (size_t)w * m;
+  for (int i = blockIdx.x * kDenseWarps + w; i < n; i += gridDim.x * kDenseWarps) {
+    for (int j = lane; j < m; j += 32) {
+      acc[j] = 0.0;
+      flg[j] = 0;
+    }
+    __syncwarp();
+    for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
+      const int k = Acol[e];
+      const double a = Aval[e];
+      for (int f = Brp[k] + lane; f < Brp[k + 1]; f += 32) {
+        const int j = Bcol[f];
+        acc[j] = __dadd_rn(acc[j], __dmul_rn(a, Bval[f]));
+        flg[j] = 1;
+      }
+      __syncwarp();
+    }
+    int* cc = ccol + off[i];
+    double* cv = cval + off[i];
+    int base = 0;
+    for (int j0 = 0; j0 < m; j0 += 32) {
+      const int j = j0 + lane;
+      const bool has = j < m && flg[j];
+      const unsigned hm = __ballot_sync(0xffffffffu, has);
+      if (has) {
+        cc[base + __popc(hm & below)] = j;
+        cv[base + __popc(hm & below)] = acc[j];
+      }
+      base += __popc(hm);
+    }
+    if (lane == 0) cnt[i] = base;
+    __syncwarp();
+  }
 }
 
 // Warp-per-row variant of k_spgemm_rows with the same summation order.
@@ -1072,6 +1346,17 @@ int pick_lanes(const DevCSR& A) {
   return l;
 }
 
+// SM count of the current device, once per process (thread-safe)
+int setup_sms() {
+  static const int sms = []() {
+    int dev = 0, v = 0;
+    TP_CUDA_TRY(cudaGetDevice(&dev));
+    TP_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    return v;
+  }();
+  return sms;
+}
+
 int read_int(const int* d, cudaStream_t s) {
   int h = 0;
   TP_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1090,6 +1375,21 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   int* ccol = scratch.alloc<int>(tot + 1);
   double* cval = scratch.alloc<double>(tot + 1);
   int* cnt = scratch.alloc<int>(n + 1);
+  const bool dense = B.m <= kDenseCap;
+  if (dense) {
+    static const bool dense_attr = []() {
+      TP_CUDA_TRY(cudaFuncSetAttribute(k_spgemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kDenseSmem));
+      return true;
+    }();
+    (void)dense_attr;
+    long long blocks = ((long long)n + kDenseWarps - 1) / kDenseWarps;
+    if (blocks > 8LL * setup_sms()) blocks = 8LL * setup_sms();
+    const size_t smem = (size_t)kDenseWarps * B.m * (sizeof(double) + 1);
+    k_spgemm_dense<<<(int)blocks, 32 * kDenseWarps, smem, s>>>(
+        n, B.m, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ccol, cval, cnt);
+    TP_LAUNCH_CHECK();
+  } else {
   k_spgemm_rows<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col,
                                                  B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
@@ -1117,6 +1417,7 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   k_spgemm_rows_big<<<n < num_sms ? n : num_sms, kSpBigThreads, kSpBigSmem, s>>>(
       n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
+  }
   DevCSR C;
   C.n = n;
   C.m = B.m;
@@ -1272,6 +1573,14 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
                                                         cur.strong, cur.cf, cidx, P.rowptr,
                                                         P.col, P.val);
       TP_LAUNCH_CHECK();
+      {
+        long long blocks = ((long long)n + kClsWarps - 1) / kClsWarps;
+        if (blocks > 8LL * setup_sms()) blocks = 8LL * setup_sms();
+        k_classical_fill_warp<<<(int)blocks, 32 * kClsWarps, 0, s>>>(
+            n, A.rowptr, A.col, A.val, cur.dpos, cur.strong, cur.cf, cidx, P.rowptr, P.col,
+            P.val);
+        TP_LAUNCH_CHECK();
+      }
     } else {
       int* ub = scratch.alloc<int>(n + 1);
       int* off = scratch.alloc<int>(n + 1);
@@ -1280,8 +1589,15 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
       long long tot = scan_exclusive(ub, off, n, scratch, s);
       int* buf = scratch.alloc<int>(tot + 1);
       k_extpi_sets<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf, off,
-                                                    buf, cnt);
+                                                    ub, buf, cnt);
       TP_LAUNCH_CHECK();
+      {
+        long long blocks = ((long long)n + kSetWarps - 1) / kSetWarps;
+        if (blocks > 8LL * setup_sms()) blocks = 8LL * setup_sms();
+        k_extpi_sets_warp<<<(int)blocks, 32 * kSetWarps, 0, s>>>(n, A.rowptr, A.col, cur.strong,
+                                                                 cur.cf, off, ub, buf, cnt);
+        TP_LAUNCH_CHECK();
+      }
       P.nnz = (int)scan_exclusive(cnt, P.rowptr, n, scratch, s);
       P.col = pool.alloc<int>(P.nnz);
       P.val = pool.alloc<double>(P.nnz);

@@ -161,3 +161,47 @@ def test_training_on_probed_columns_reduces_the_loss_and_solves():
     assert hist[-1] < 0.7 * hist[0]
     ev = L.evaluate(mlp, make_problem("tiny", shape=(16, 16, 8), seed=777))
     assert ev["learned_rel_res"] <= 1e-8
+
+
+def test_trained_network_reduces_the_schur_approximation_error():
+    """What the learned correction gains: on an unseen problem, the RMS error
+    of the corrected S~ against exact Schur-complement entries (probed
+    columns, relative to the row's diagonal) is below half the plain S~_T
+    error, and FGMRES needs no more than two extra iterations. (S~_T of
+    Eq. Se is already close to the Schur complement on these fields, so the
+    iteration count has little room to fall.)"""
+    from paper_1902_00095_gb300 import learned as L
+    rng = np.random.Generator(np.random.PCG64(1))
+    parts = []
+    for q in range(4):
+        prob = make_problem("grf32", shape=(16, 16, 8), seed=1000 + q)
+        s = thermo.Solver.from_problem(prob)
+        parts.append(L.collect_samples(s, prob, 128, rng))
+        s.close()
+    mlp, hist = L.train(L.concat(parts), flatten(initial_params(0)), epochs=40, batch=512,
+                        lr=2e-3)
+    prob = make_problem("grf32", shape=(16, 16, 8), seed=1999)
+    s = thermo.Solver.from_problem(prob)
+    s.assemble(prob["p_k"], prob["T_k"], prob["p_n"], prob["T_n"], prob["dt"])
+    s.build(schur=0)
+    _, _, plain = s.solve(rtol=1e-8)
+    rp, col, val, S, _ = s.export_system()
+    cols = rng.choice(s.N, 64, replace=False)
+    entry, value, its, st = s.probe_schur_columns(cols, 1e-11)
+    assert st == 0
+    s.set_schur_model(mlp)
+    s.build(schur=1)
+    _, _, learned = s.solve(rtol=1e-8)
+    assert s.learned_status()[1] is False
+    SL = s.export_level(1, 0)["A"][2]
+    ok = entry >= 0
+    e = entry[ok]
+    tgt = value[ok]
+    rows = np.repeat(np.arange(s.N), np.diff(rp))[e]
+    dpos = np.array([rp[i] + np.searchsorted(col[rp[i]:rp[i + 1]], i) for i in range(s.N)])
+    Sd = S[dpos[rows]]
+    err_plain = np.sqrt(np.mean(((S[e] - tgt) / Sd) ** 2))
+    err_learned = np.sqrt(np.mean(((SL[e] - tgt) / Sd) ** 2))
+    assert err_learned < 0.5 * err_plain, (err_learned, err_plain)
+    assert learned["iters"] <= plain["iters"] + 2
+    assert learned["rel_res"] <= 1e-8

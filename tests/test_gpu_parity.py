@@ -397,7 +397,8 @@ def test_schur_diag_matches_oracle(name):
     """S~_diag (schur = 3): the GPU's 25-point matrix (level 0 of its Schur
     hierarchy) has the oracle's pattern exactly and its values to rounding
     (each side assembled its own Jacobian), and the block-preconditioned
-    solve reaches the direct solution with the oracle's iteration count."""
+    solve behaves as the oracle's: the direct solution with the same
+    iteration count where the oracle converges, a stall where it stalls."""
     prob, p, T = problem(name)
     s, _, (osys, obp, obT, oS) = assemble_both(prob, p, T)
     s.build(schur=3)
@@ -406,11 +407,19 @@ def test_schur_diag_matches_oracle(name):
     assert np.array_equal(g["A"][0], rp) and np.array_equal(g["A"][1], c)
     assert np.max(np.abs(g["A"][2] - v)) <= 1e-11 * np.max(np.abs(v))
     xp, xT, info = s.solve(rtol=1e-10, maxit=400)
-    assert info["status"] == 0
-    rpv, rTv = okry.direct_solution(osys, obp, obT)
-    assert _errors(xp, xT, rpv, rTv)[0] <= 1e-6
-    o = okry.solve(prob, rtol=1e-10, p=p, T=T, schur="diag")
-    assert abs(info["iters"] - o["iters"]) <= 2, (info["iters"], o["iters"])
+    o = okry.solve(prob, rtol=1e-10, maxit=400, p=p, T=T, schur="diag")
+    if o["status"] == "converged":
+        assert info["status"] == 0
+        rpv, rTv = okry.direct_solution(osys, obp, obT)
+        assert _errors(xp, xT, rpv, rTv)[0] <= 1e-6
+        assert abs(info["iters"] - o["iters"]) <= 2, (info["iters"], o["iters"])
+    else:
+        # S~_diag can fail where S~_T converges (the paper reports such a
+        # case, Sec. 4.3): on this perturbed state both sides stall
+        assert info["status"] == thermo.TP_NOT_CONVERGED and info["iters"] == 400
+        s.build(schur=0)
+        _, _, plain = s.solve(rtol=1e-10, maxit=400)
+        assert plain["status"] == 0 and plain["iters"] < 30
 
 
 def test_schur_diag_newton_refresh_matches_rebuild():
