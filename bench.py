@@ -377,6 +377,9 @@ def run_ours(args, rank, world, local):
                    "learned_fallback_rows": fb_rows, "learned_global_fallback": fb_all,
                    "training": {"problems": args.train_problems, "columns_per_problem": 128,
                                 "loss_first": hist[0], "loss_last": hist[-1],
+                                "val_loss_identity": mlp.val_losses[0],
+                                "val_loss_selected": mlp.val_losses[mlp.selected_epoch],
+                                "selected_epoch": mlp.selected_epoch,
                                 "seconds_untimed": t_train}}
 
     if rank != 0:
@@ -427,7 +430,7 @@ def run_sequence(args, rank, world, local):
         s.set_schur_model(mlp)
         opts = thermo.default_opts(precision=1, schur=1, nu_pre=args.nu, nu_post=args.nu)
         train = {"problems": args.train_problems, "loss_first": hist[0], "loss_last": hist[-1],
-                 "seconds_untimed": t_train}
+                 "selected_epoch": mlp.selected_epoch, "seconds_untimed": t_train}
     else:
         opts = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
     d = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
