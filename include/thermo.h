@@ -108,6 +108,10 @@ typedef struct {
   int pmax;         /* interpolation truncation: at most pmax weights per row  */
                     /* (largest |w|, row sums kept); default 4, 0 = off, <=16 */
   int smoother_S;   /* -1 same as smoother, 0 l1-Jacobi (default), 1 Chebyshev */
+  int tail_rows;    /* coarse levels (below level 0) with at most tail_rows    */
+                    /* rows run as one thread-block-cluster kernel per V-cycle */
+                    /* (l1-Jacobi only); default 12288, 0 = one kernel per     */
+                    /* phase on every level                                   */
 } tp_precond_opts;
 
 typedef struct {

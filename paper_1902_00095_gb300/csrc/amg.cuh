@@ -40,7 +40,30 @@ struct AmgOpts {
   int precision = 0;     // 0 FP64, 1 FP32 hierarchy, 2 FP32 + BF16 P and R
   int max_pmis_rounds = 64;
   int pmax = 0;          // interpolation truncation (0 = off)
+  int tail_rows = 12288;  // coarse levels with at most this many rows: one cluster kernel (0 off)
 };
+
+// Device descriptor of one level for the cluster kernel of the V-cycle's
+// coarse tail (vcycle_tail.cu): values and vectors in the hierarchy's
+// precision, P and R optionally BF16.
+struct TailLevel {
+  int n, nnext;  // rows of A and of the next level
+  const int *Arp, *Acol;
+  const void *Aval, *dinv;
+  const int *Prp, *Pcol;
+  const void* Pval;
+  const __nv_bfloat16* Ph;
+  const int *Rrp, *Rcol;
+  const void* Rval;
+  const __nv_bfloat16* Rh;
+  void *b, *x, *t, *r;
+};
+constexpr int kMaxTailLevels = 32;
+// cluster size the tail kernel launches with (16 or 8), 0 if unavailable
+int tail_cluster_size();
+template <class TV>
+void launch_vcycle_tail(const TailLevel* desc, int first, int last, const double* cinv, int nc,
+                        int nu_pre, int nu_post, int cluster, cudaStream_t s);
 
 // CUDA-event timing of one kernel class inside the timed region: events are
 // recorded around each launch (as external event nodes when captured into a
@@ -137,9 +160,15 @@ class Hierarchy {
   double phase_ms[5] = {0, 0, 0, 0, 0};
   int* err = nullptr;
   double* cheb_partials = nullptr;   // norm partial sums of the power iteration
+  // coarse tail run as one cluster kernel: levels tail_first..L.size()-1
+  // (-1: every level has its own kernels)
+  int tail_first = -1, tail_cluster = 0;
+  TailLevel* tail_desc = nullptr;
+  std::vector<TailLevel> tail_host;
 
  private:
   void finish_levels(cudaStream_t s, bool allocate);
+  void plan_tail(cudaStream_t s);
   void vcycle_fp64(cudaStream_t s);
   void vcycle_fp32(cudaStream_t s);
 };

@@ -1503,6 +1503,7 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
   L.clear();
   coarse_inv = nullptr;
   cheb_partials = nullptr;
+  tail_first = -1;
   err = pool.alloc<int>(2);
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   L.emplace_back();
@@ -1745,8 +1746,58 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
   if (allocate) {
     in = pool.alloc<double>(n0 + 1);
     out = pool.alloc<double>(n0 + 1);
+    plan_tail(s);
   }
   TP_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+// Coarse tail: from the first level below level 0 with at most
+// opts.tail_rows rows down to the coarsest, when at least one smoothing
+// level is in it, the smoother is l1-Jacobi and clusters can be launched.
+// The descriptors point at the level buffers, which keep their addresses
+// under refresh().
+void Hierarchy::plan_tail(cudaStream_t s) {
+  tail_first = -1;
+  const int nl = (int)L.size();
+  if (opts.tail_rows <= 0 || opts.smoother != 0 || nl < 3) return;
+  int f = -1;
+  for (int l = 1; l < nl - 1; ++l)
+    if (L[l].A.n <= opts.tail_rows) {
+      f = l;
+      break;
+    }
+  if (f < 0 || nl - f > kMaxTailLevels) return;
+  const int cluster = tail_cluster_size();
+  if (cluster == 0) return;
+  const bool f32 = opts.precision >= 1;
+  tail_host.assign(nl, TailLevel{});
+  for (int l = 0; l < nl; ++l) {
+    const Level& v = L[l];
+    TailLevel& d = tail_host[l];
+    d.n = v.A.n;
+    d.nnext = (l + 1 < nl) ? L[l + 1].A.n : 0;
+    d.Arp = v.A.rowptr;
+    d.Acol = v.A.col;
+    d.Aval = f32 ? (const void*)v.A.valf : (const void*)v.A.val;
+    d.dinv = f32 ? (const void*)v.dinvf : (const void*)v.dinv;
+    d.Prp = v.P.rowptr;
+    d.Pcol = v.P.col;
+    d.Pval = f32 ? (const void*)v.P.valf : (const void*)v.P.val;
+    d.Ph = v.Ph;
+    d.Rrp = v.R.rowptr;
+    d.Rcol = v.R.col;
+    d.Rval = f32 ? (const void*)v.R.valf : (const void*)v.R.val;
+    d.Rh = v.Rh;
+    d.b = v.b;
+    d.x = v.x;
+    d.t = v.t;
+    d.r = v.r;
+  }
+  tail_desc = pool.alloc<TailLevel>(nl);
+  TP_CUDA_TRY(cudaMemcpyAsync(tail_desc, tail_host.data(), sizeof(TailLevel) * nl,
+                              cudaMemcpyHostToDevice, s));
+  tail_first = f;
+  tail_cluster = cluster;
 }
 
 void Hierarchy::refresh(cudaStream_t s) {

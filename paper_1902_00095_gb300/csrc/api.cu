@@ -88,6 +88,7 @@ tp::AmgOpts amg_opts(const tp_precond_opts& o) {
   a.seed = o.seed;
   a.precision = o.precision;
   a.pmax = o.pmax;
+  a.tail_rows = o.tail_rows;
   return a;
 }
 
@@ -107,6 +108,7 @@ void check_opts(const tp_precond_opts& o) {
   if (o.interp_S < -1 || o.interp_S > 1 || o.max_levels_S < 0 || o.nu_S < 0 || o.nu_S > 8)
     fail(TP_EINVAL, "bad Schur-hierarchy override");
   if (o.pmax < 0 || o.pmax > 16) fail(TP_EINVAL, "pmax must be in 0..16");
+  if (o.tail_rows < 0) fail(TP_EINVAL, "tail_rows must be >= 0");
 }
 
 }  // namespace
@@ -201,6 +203,7 @@ void tp_default_opts(tp_precond_opts* o) {
   o->nu_S = 0;
   o->pmax = 4;
   o->smoother_S = 0;
+  o->tail_rows = 12288;
 }
 
 const char* tp_status_string(int st) {

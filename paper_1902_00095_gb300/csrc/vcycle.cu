@@ -386,9 +386,12 @@ void sweep_probed(Probe* pr, const Level& v, const TV* dinv, const TB* b, const 
   if (pr) pr->after(s, sweep_bytes<TV, TB, TO>(v.A));
 }
 
-// smoother selection of one V-cycle: 0 l1-Jacobi, 1 Chebyshev of `degree`
+// smoother selection of one V-cycle: 0 l1-Jacobi, 1 Chebyshev of `degree`;
+// tail_first >= 0: levels from tail_first down run as one cluster kernel
 struct Smooth {
   int kind = 0, degree = 2;
+  int tail_first = -1, tail_cluster = 0, nc = 0;
+  const TailLevel* tail_desc = nullptr;
 };
 
 // one smoothing step xin -> xout (xin null: zero initial guess, Chebyshev only)
@@ -417,6 +420,17 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     }
     coarse<TB, TV>(n, cinv, b, x, s);
     return x;
+  }
+  if ((int)l == sm.tail_first && !final_out) {
+    // the whole coarse tail in one cluster kernel; the result buffer follows
+    // the same ping-pong of x and t as the per-kernel path below
+    launch_vcycle_tail<TV>(sm.tail_desc, (int)l, (int)L.size() - 1, cinv, sm.nc, nu_pre, nu_post,
+                           sm.tail_cluster, s);
+    TV* cur = x;
+    TV* oth = t;
+    for (int k = (nu_pre >= 2 ? 2 : 1); k < nu_pre; ++k) std::swap(cur, oth);
+    for (int k = 1; k <= nu_post; ++k) std::swap(cur, oth);
+    return cur;
   }
   const TV* dinv = Vals<TV>::dinv(v);
   Probe* pr = (l == 0) ? probe : nullptr;
@@ -475,13 +489,13 @@ void Hierarchy::vcycle(cudaStream_t s) {
 }
 
 void Hierarchy::vcycle_fp64(cudaStream_t s) {
-  Smooth sm{opts.smoother, opts.cheb_degree};
+  Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc};
   run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                     probe);
 }
 
 void Hierarchy::vcycle_fp32(cudaStream_t s) {
-  Smooth sm{opts.smoother, opts.cheb_degree};
+  Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc};
   run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                    probe);
 }

@@ -168,6 +168,36 @@ def test_chebyshev_solve_matches_direct_solution_and_oracle_iterations():
     assert abs(info["iters"] - o["iters"]) <= 2, (info["iters"], o["iters"])
 
 
+@pytest.mark.parametrize("name,which", [("mid", "App"), ("mid", "S"), ("ragged", "App"),
+                                        ("iid16", "S")])
+def test_cluster_tail_matches_per_kernel_vcycle(name, which):
+    """The coarse tail run as one cluster kernel computes the same V-cycle as
+    one kernel per phase (summation order within a row differs: 8 lanes per
+    row instead of the per-level lane count), in FP64, FP32 and FP32 with
+    BF16 P/R, with one and two sweeps."""
+    prob, p, T = problem(name)
+    osys, _, _, oS = okry.assemble(prob, p, T)
+    A = osys.App if which == "App" else oS
+    interp = 1 if which == "App" else 0
+    b = np.random.default_rng(9).standard_normal(A[0].size - 1)
+    for precision, tol in ((0, 1e-12), (1, 1e-5), (2, 1e-5)):
+        for nu in (1, 2):
+            kw = dict(interp=interp, precision=precision, nu_pre=nu, nu_post=nu)
+            g0 = thermo.AMG(*A, tail_rows=0, **kw)
+            g1 = thermo.AMG(*A, **kw)
+            n, _ = g1.info()
+            assert len(n) >= 3
+            l0 = thermo.kernel_launches()
+            x0 = g0.vcycle(b)
+            l1 = thermo.kernel_launches()
+            x1 = g1.vcycle(b)
+            l2 = thermo.kernel_launches()
+            assert l2 - l1 < l1 - l0  # the tail replaced per-phase kernels
+            assert np.max(np.abs(x1 - x0)) <= tol * np.max(np.abs(x0)), (precision, nu)
+            g0.close()
+            g1.close()
+
+
 def test_amg_setup_is_deterministic():
     prob, p, T = problem("iid16")
     osys, *_ = okry.assemble(prob, p, T)
