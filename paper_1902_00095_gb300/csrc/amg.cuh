@@ -40,7 +40,7 @@ struct AmgOpts {
   int precision = 0;     // 0 FP64, 1 FP32 hierarchy, 2 FP32 + BF16 P and R
   int max_pmis_rounds = 64;
   int pmax = 0;          // interpolation truncation (0 = off)
-  int tail_rows = 12288;  // coarse levels with at most this many rows: one cluster kernel (0 off)
+  int tail_rows = 0;      // coarse levels with at most this many rows: one cluster kernel (0 off)
 };
 
 // Device descriptor of one level for the cluster kernel of the V-cycle's

@@ -203,7 +203,7 @@ void tp_default_opts(tp_precond_opts* o) {
   o->nu_S = 0;
   o->pmax = 4;
   o->smoother_S = 0;
-  o->tail_rows = 12288;
+  o->tail_rows = 0;
 }
 
 const char* tp_status_string(int st) {

@@ -12,6 +12,15 @@
 // split over groups of 8 lanes; the ping-pong order of the work vectors is
 // the same, so the result lands in the buffer the host expects.
 //
+// Measured on GB300 (FGMRES time per iteration, 64x64x32 and 128x128x64
+// hierarchies): slower than the per-phase kernels replayed in a CUDA graph
+// with programmatic dependent launches at every threshold tried (levels of
+// at most 256 rows: +4 % / +1 %; 12288 rows: +50 % / +11 %), because one
+// cluster of 16 SMs streams the larger levels far slower than the whole GPU
+// and even the tiny levels gain nothing over back-to-back dependent
+// launches. It is therefore off by default (tail_rows = 0) and kept as an
+// option.
+//
 // Vectors written inside the kernel are read with ld.global.cg (L2, never a
 // stale L1 line) and written with st.global.cg; matrix values are
 // read-only. Every thread of every CTA executes the same sequence of
@@ -25,8 +34,9 @@ namespace {
 constexpr int kTailThreads = 1024;
 constexpr int kTailLanes = 8;
 
+// arrive.release / wait.acquire order every thread's global writes before
+// the barrier with every thread's reads after it, at cluster scope
 __device__ __forceinline__ void cluster_barrier() {
-  __threadfence();
   asm volatile(
       "barrier.cluster.arrive.release;\n"
       "barrier.cluster.wait.acquire;\n" ::: "memory");
