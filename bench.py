@@ -64,6 +64,9 @@ def parse():
                          "layered256) instead of the single-system benchmark")
     ap.add_argument("--max-newton", type=int, default=4,
                     help="Newton iterations per time step in --sequence mode")
+    ap.add_argument("--max-cuts", type=int, default=3,
+                    help="--sequence: a step whose Newton iteration fails is repeated as two "
+                         "halves, at most this many times")
     ap.add_argument("--sequence-variant", action="store_true",
                     help="--sequence with FP32 hierarchies + learned S~ (trained untimed)")
     ap.add_argument("--probe", type=int, default=0,
@@ -415,8 +418,9 @@ def run_ours(args, rank, world, local):
 def run_sequence(args, rank, world, local):
     """Backward-Euler time steps, each solved by Newton with line search (at
     most --max-newton linear solves, AMG structure reused between Newton
-    iterations) on one GPU; with --sequence-variant the hierarchies run in
-    FP32 with the learned Schur correction."""
+    iterations, a failed step repeated as two halves up to --max-cuts times)
+    on one GPU; with --sequence-variant the hierarchies run in FP32 with the
+    learned Schur correction."""
     import torch
     from paper_1902_00095_gb300 import thermo
     torch.cuda.set_device(local)
@@ -435,14 +439,22 @@ def run_sequence(args, rank, world, local):
         opts = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
     d = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
     p, T = d(prob["p_n"]), d(prob["T_n"])
+    from paper_1902_00095_gb300.timestep import advance
     steps = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.sequence):
-        p, T, info = s.newton_step(p, T, prob["dt"], max_newton=args.max_newton, tol_f=1e-8,
-                                   tol_dx=1e-8, rtol=args.rtol, maxit=args.maxit,
-                                   restart=args.restart, reuse=True, opts=opts)
-        steps.append(info)
+        p, T, rec = advance(s, p, T, prob["dt"], max_cuts=args.max_cuts,
+                            max_newton=args.max_newton, tol_f=1e-8, tol_dx=1e-8, rtol=args.rtol,
+                            maxit=args.maxit, restart=args.restart, reuse=True, opts=opts)
+        acc = [r for r in rec if r["accepted"]]
+        steps.append({"substeps": len(acc), "solves": len(rec),
+                      "converged": all(r["status"] == 0 for r in acc),
+                      "newton_iters": sum(r.get("newton_iters", 0) for r in rec),
+                      "linear_iters": sum(r.get("linear_iters", 0) for r in rec),
+                      "line_search_halvings": sum(r.get("line_search_halvings", 0) for r in rec),
+                      "t_ms": sum(r.get("t_ms", 0.0) for r in rec),
+                      "substep_days": [r["dt"] / 86400.0 for r in acc]})
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if rank != 0:
@@ -455,11 +467,10 @@ def run_sequence(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": f"{args.config}: {WORKLOAD[args.config]}, {args.sequence} steps",
                    "unknowns": 2 * N, "nu": args.nu, "restart": args.restart,
-                   "max_newton": args.max_newton,
+                   "max_newton": args.max_newton, "max_cuts": args.max_cuts,
                    "solver": "fp32 hierarchy + learned S~" if args.sequence_variant else
                              ("fp32 hierarchy" if args.precision else "fp64 plain")},
-        "newton": [{k: st[k] for k in ("newton_iters", "linear_iters", "status", "rel_f", "rel_dx",
-                                       "line_search_halvings", "t_ms")} for st in steps],
+        "steps_detail": steps,
         "learned": (dict(train, fallback=s.learned_status()) if train else None),
         "final_T_range": [float(T.min()), float(T.max())],
         "final_p_range": [float(p.min()), float(p.max())],
