@@ -57,14 +57,21 @@ typedef struct {
 } tp_grid;
 
 /* Fluid and rock constants (SI). Density rho0 exp(c (p-p0)) exp(beta (T-T0))
- * (Sec. 2.1.4); viscosity mu0 exp(-mu_coef (T - T_mu0)); c_v and rock
- * rho_r, c_r of Eq. energy1; k_T = phi kTr + (1-phi) kTf as printed in
- * Sec. 2.1.2 when kT_mix = 0, or (1-phi) kTr + phi kTf when kT_mix = 1. */
+ * (Sec. 2.1.4). Viscosity: mu_law = 0, mu0 exp(-mu_coef (T - T_mu0));
+ * mu_law = 1, the Bennison heavy-oil correlation of Eq. bennison,
+ * mu = 1e-3 10^(A1 api + A2) T_F^(A3 api + A4) Pa s with T_F the
+ * temperature in degrees Fahrenheit, A1..A4 of Table 1 and api the API
+ * gravity (valid for T_F > 0; a non-positive T_F is reported as a
+ * non-finite assembly). c_v and rock rho_r, c_r of Eq. energy1;
+ * k_T = phi kTr + (1-phi) kTf as printed in Sec. 2.1.2 when kT_mix = 0,
+ * or (1-phi) kTr + phi kTf when kT_mix = 1. */
 typedef struct {
   double rho0, c, beta, p0, T0;
   double mu0, T_mu0, mu_coef;
   double cv, rho_r, cr, kTf;
   int kT_mix;
+  int mu_law;
+  double api;
 } tp_fluid;
 
 /* A well or heater completed in cells (i, j, k0..k1) (Sec. 2.1.5).

@@ -33,10 +33,32 @@ def density(p, T, fl):
     return fl["rho0"] * np.exp(fl["c"] * (p - fl["p0"])) * np.exp(fl["beta"] * (T - fl["T0"]))
 
 
+BENNISON = (-0.8021, 23.8765, 0.31458, -9.21592)  # A1..A4 of Table 1
+
+
+def fahrenheit(T):
+    return (T - 273.15) * 9.0 / 5.0 + 32.0
+
+
 def viscosity(T, fl):
-    """mu(T) = mu0 exp(-a (T - T_mu0)) (exponential water law replacing the
-    Bennison correlation of Eq. bennison)."""
+    """mu_law 0: mu(T) = mu0 exp(-a (T - T_mu0)) (an exponential water law);
+    mu_law 1: the Bennison heavy-oil correlation of Eq. bennison,
+    mu = 10^(A1 API + A2) T_F^(A3 API + A4) centipoise with T_F in degrees
+    Fahrenheit (A_i from Table 1), returned in Pa s."""
+    if fl.get("mu_law", 0) == 1:
+        A1, A2, A3, A4 = BENNISON
+        api = fl["api"]
+        return 1e-3 * 10.0 ** (A1 * api + A2) * fahrenheit(T) ** (A3 * api + A4)
     return fl["mu0"] * np.exp(-fl["mu_coef"] * (T - fl["T_mu0"]))
+
+
+def dlog_viscosity_dT(T, fl):
+    """d(ln mu)/dT of `viscosity`: -a for the exponential law,
+    (A3 API + A4) (9/5) / T_F for Bennison."""
+    if fl.get("mu_law", 0) == 1:
+        A1, A2, A3, A4 = BENNISON
+        return (A3 * fl["api"] + A4) * 9.0 / 5.0 / fahrenheit(T)
+    return -fl["mu_coef"] * np.ones_like(T)
 
 
 def cell_props(p, T, fl):
@@ -48,8 +70,8 @@ def cell_props(p, T, fl):
     rho_T = fl["beta"] * rho
     lam = rho / mu
     lam_p = rho_p / mu
-    # d(rho/mu)/dT = rho_T/mu - rho mu_T / mu^2 with mu_T = -a mu
-    lam_T = rho_T / mu + fl["mu_coef"] * lam
+    # d(rho/mu)/dT = rho_T/mu - (rho/mu) d(ln mu)/dT
+    lam_T = rho_T / mu - dlog_viscosity_dT(T, fl) * lam
     return dict(rho=rho, rho_p=rho_p, rho_T=rho_T, mu=mu, lam=lam, lam_p=lam_p, lam_T=lam_T)
 
 

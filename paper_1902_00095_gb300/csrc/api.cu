@@ -248,7 +248,8 @@ int tp_create(tp_ctx** out, const tp_grid* grid, const tp_fluid* fluid, void* cu
   c->grid = {grid->nx, grid->ny, grid->nz, grid->dx, grid->dy, grid->dz, grid->g};
   c->fluid = {fluid->rho0, fluid->c,     fluid->beta,    fluid->p0, fluid->T0,
               fluid->mu0,  fluid->T_mu0, fluid->mu_coef, fluid->cv, fluid->rho_r,
-              fluid->cr,   fluid->kTf,   fluid->kT_mix};
+              fluid->cr,   fluid->kTf,   fluid->kT_mix, fluid->mu_law, fluid->api};
+  if (fluid->mu_law != 0 && fluid->mu_law != 1) fail(TP_EINVAL, "mu_law must be 0 or 1");
   const int n = (int)N;
   c->N = n;
   long long nnzb = N + 2LL * ((long long)(grid->nx - 1) * grid->ny * grid->nz +

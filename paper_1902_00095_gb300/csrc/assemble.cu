@@ -66,6 +66,10 @@ __global__ void k_mix_conductivity(int N, const double* __restrict__ phi,
   kT[i] = (f.kT_mix == 0) ? ph * kTr[i] + (1.0 - ph) * f.kTf : (1.0 - ph) * kTr[i] + ph * f.kTf;
 }
 
+// Bennison heavy-oil viscosity coefficients (Table 1)
+constexpr double kBennA1 = -0.8021, kBennA2 = 23.8765, kBennA3 = 0.31458, kBennA4 = -9.21592;
+constexpr double kLn10 = 2.302585092994046;
+
 // A1: rho, lam = rho/mu and the p/T derivatives of lam per cell.
 __global__ void k_cell_props(int N, const double* __restrict__ p, const double* __restrict__ T,
                              FluidDev f, double* __restrict__ rho, double* __restrict__ lam,
@@ -73,12 +77,23 @@ __global__ void k_cell_props(int N, const double* __restrict__ p, const double* 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double r = density(p[i], T[i], f);
-  double mu = f.mu0 * exp(-f.mu_coef * (T[i] - f.T_mu0));
+  double mu, mlog_T;  // viscosity and d(ln mu)/dT
+  if (f.mu_law == 1) {
+    // Bennison (Eq. bennison, Table 1): mu in cp of T in degrees Fahrenheit
+    const double tf = (T[i] - 273.15) * 1.8 + 32.0;
+    const double ex = kBennA3 * f.api + kBennA4;
+    mu = 1e-3 * exp(kLn10 * (kBennA1 * f.api + kBennA2) + ex * log(tf));
+    mlog_T = ex * 1.8 / tf;
+  } else {
+    mu = f.mu0 * exp(-f.mu_coef * (T[i] - f.T_mu0));
+    mlog_T = -f.mu_coef;
+  }
   double l = r / mu;
   rho[i] = r;
   lam[i] = l;
   lam_p[i] = (f.c * r) / mu;
-  lam_T[i] = (f.beta * r) / mu + f.mu_coef * l;
+  // d(rho/mu)/dT = rho_T/mu - (rho/mu) d(ln mu)/dT
+  lam_T[i] = (f.beta * r) / mu - mlog_T * l;
 }
 
 struct Face {

@@ -8,6 +8,8 @@ namespace tp {
 struct FluidDev {
   double rho0, c, beta, p0, T0, mu0, T_mu0, mu_coef, cv, rho_r, cr, kTf;
   int kT_mix;
+  int mu_law;  // 0 exponential, 1 Bennison (Eq. bennison)
+  double api;
 };
 
 struct GridDev {

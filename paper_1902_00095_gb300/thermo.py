@@ -28,7 +28,8 @@ class Grid(C.Structure):
 
 class Fluid(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("rho0", "c", "beta", "p0", "T0", "mu0", "T_mu0",
-                                          "mu_coef", "cv", "rho_r", "cr", "kTf")] + [("kT_mix", C.c_int)]
+                                          "mu_coef", "cv", "rho_r", "cr", "kTf")] + [
+        ("kT_mix", C.c_int), ("mu_law", C.c_int), ("api", C.c_double)]
 
 
 class Well(C.Structure):
@@ -204,8 +205,10 @@ def default_opts(**kw):
 
 
 def fluid_struct(fl):
-    return Fluid(**{n: float(fl[n]) for n, _ in Fluid._fields_ if n != "kT_mix"},
-                 kT_mix=int(fl.get("kT_mix", 0)))
+    return Fluid(**{n: float(fl[n]) for n, _ in Fluid._fields_
+                    if n not in ("kT_mix", "mu_law", "api")},
+                 kT_mix=int(fl.get("kT_mix", 0)), mu_law=int(fl.get("mu_law", 0)),
+                 api=float(fl.get("api", 0.0)))
 
 
 class Solver:

@@ -58,7 +58,22 @@ def default_fluid(**overrides):
         mu0=1.0e-3, T_mu0=288.7056, mu_coef=0.02,
         cv=4184.0, rho_r=2650.0, cr=920.0, kTf=0.6,
         kT_mix=0,  # 0: k_T = phi*kTr + (1-phi)*kTf as printed; 1: (1-phi)*kTr + phi*kTf
+        mu_law=0,  # 0: exponential law above; 1: Bennison (see bennison_oil)
+        api=0.0,
     )
+    f.update(overrides)
+    return f
+
+
+def bennison_oil(api=12.0, **overrides):
+    """The paper's heavy oil (Sec. 2.1.4, Sec. 4 Table 2): Bennison viscosity
+    with API gravity `api` (the paper's value is not printed; 12 is a heavy
+    oil: about 38 Pa s at 60 F and 2.6 mPa s at 350 F), rho0 = SG x 999 kg/m^3 with
+    SG = 141.5 / (api + 131.5), oil conductivity 0.15 W/m/K, oil heat capacity
+    2093.4 J/kg/K, rock heat capacity 920 J/kg/K. Rock conductivity
+    (1.7295772056 W/m/K in Table 2) is a cell field of the recipe."""
+    sg = 141.5 / (api + 131.5)
+    f = default_fluid(rho0=sg * 999.0, cv=2093.4, kTf=0.15, cr=920.0, mu_law=1, api=api)
     f.update(overrides)
     return f
 

@@ -15,7 +15,7 @@ import pytest
 from oracle import amg as oamg
 from oracle import krylov as okry
 from oracle import physics as ophys
-from synthetic import make_problem
+from synthetic import bennison_oil, make_problem
 from synthetic.recipes import perturbed_state
 
 pytestmark = pytest.mark.gpu
@@ -42,6 +42,8 @@ PROBLEMS = {
     "thin": lambda: (make_problem("tiny", shape=(37, 1, 3), seed=4), 8),
     # more than 4096 cells: the finest level also gets the ELL copy
     "mid": lambda: (make_problem("tiny", shape=(20, 16, 14), seed=6), 9),
+    # the paper's heavy oil: Bennison viscosity (Eq. bennison), Table 2 constants
+    "oil": lambda: (make_problem("tiny", shape=(12, 10, 6), seed=13, fluid=bennison_oil()), 3),
 }
 
 
@@ -260,7 +262,7 @@ def _oracle_scaled_residual(osys, obp, obT, xp, xT):
     return np.linalg.norm(r) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("name", ["iid16", "ragged", "thin"])
+@pytest.mark.parametrize("name", ["iid16", "ragged", "thin", "oil"])
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_matches_direct_solution(name, precision):
     prob, p, T = problem(name)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import physics
-from synthetic import make_problem, default_fluid
+from synthetic import make_problem, default_fluid, bennison_oil
 from synthetic.recipes import perturbed_state
 
 
@@ -32,9 +32,9 @@ def dense_blocks(rowptr, col, val):
     return J
 
 
-@pytest.mark.parametrize("shape", [(4, 3, 3), (3, 5, 2)])
-def test_jacobian_matches_central_differences(shape):
-    prob = tiny(shape)
+@pytest.mark.parametrize("shape,oil", [((4, 3, 3), False), ((3, 5, 2), False), ((4, 3, 3), True)])
+def test_jacobian_matches_central_differences(shape, oil):
+    prob = tiny(shape, fluid=bennison_oil() if oil else None)
     # make the producer active and the injector present; perturb the state
     p, T = perturbed_state(prob, seed=5)
     prob["p_n"] = prob["p_n"] + 1.0e5
@@ -222,3 +222,22 @@ def test_sparse_schur_diag_equals_the_dense_formula():
     for i in range(N):
         want = [j for j in range(N) if np.abs(xyz(i) - xyz(j)).sum() <= 2]
         assert list(c[rp[i]:rp[i + 1]]) == want
+
+
+def test_bennison_viscosity_behaves_as_the_correlation_states():
+    """Eq. bennison is a power law in the Fahrenheit temperature: the ratio
+    of two viscosities is the temperature ratio to the power A3 API + A4
+    (Table 1), here checked between 100 F and 350 F given in kelvin; a
+    heavier oil (lower API) is more viscous at the same temperature; and the
+    result is in Pa s (1 cp = 1e-3 Pa s): a 12-API oil at 60 F is a few tens
+    of Pa s, far above water's 1e-3."""
+    to_k = lambda f: (f - 32.0) * 5.0 / 9.0 + 273.15
+    for api in (8.0, 12.0, 20.0):
+        fl = bennison_oil(api)
+        m = physics.viscosity(np.array([to_k(100.0), to_k(350.0)]), fl)
+        assert abs(m[1] / m[0] - 3.5 ** (0.31458 * api - 9.21592)) <= 1e-12 * (m[1] / m[0])
+    T = np.array([to_k(150.0)])
+    assert physics.viscosity(T, bennison_oil(10.0)) > physics.viscosity(T, bennison_oil(15.0))
+    assert 10.0 < physics.viscosity(np.array([to_k(60.0)]), bennison_oil(12.0))[0] < 100.0
+    fl = bennison_oil(12.0)
+    assert abs(fl["rho0"] / 999.0 - 141.5 / 143.5) < 1e-15
