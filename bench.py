@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--max-cuts", type=int, default=3,
                     help="--sequence: a step whose Newton iteration fails is repeated as two "
                          "halves, at most this many times")
+    ap.add_argument("--scaling2d", action="store_true",
+                    help="run the problem-size scaling study (2D Cases I-V) instead")
+    ap.add_argument("--scaling-sizes", default="20,40,80,160,320")
     ap.add_argument("--sequence-variant", action="store_true",
                     help="--sequence with FP32 hierarchies + learned S~ (trained untimed)")
     ap.add_argument("--probe", type=int, default=0,
@@ -477,6 +480,51 @@ def run_sequence(args, rank, world, local):
     }), flush=True)
 
 
+def run_scaling2d(args, rank, world, local):
+    """Sec. 4.3 problem-size scaling: Cases I-V on n x n grids of the 20 m
+    square (n = 20..320), two time steps each, Newton with line search and
+    FGMRES(30) to the paper's 1e-5, for the Schur approximations S~_T, S~_ATT
+    and S~_diag; reports the average FGMRES iterations per Newton iteration
+    (the quantity of the paper's Tables 7-11) and the wall time."""
+    import torch
+    from paper_1902_00095_gb300 import thermo
+    from synthetic import scaling_case
+    torch.cuda.set_device(local)
+    sizes = [int(v) for v in args.scaling_sizes.split(",")]
+    schurs = {"S_T": 0, "S_ATT": 2, "S_diag": 3}
+    table = {}
+    t0 = time.perf_counter()
+    for case in (1, 2, 3, 4, 5):
+        for name, sc in schurs.items():
+            row = []
+            for n in sizes:
+                prob = scaling_case(case, n)
+                s = thermo.Solver.from_problem(prob)
+                p, T = prob["p_n"], prob["T_n"]
+                newton = lin = 0
+                ok = True
+                for step in range(2):
+                    try:
+                        p, T, info = s.newton_step(p, T, prob["dt"], max_newton=10, tol_f=1e-8,
+                                                   tol_dx=1e-8, rtol=1e-5, maxit=200,
+                                                   restart=30, reuse=True, schur=sc)
+                    except thermo.ThermoError:
+                        ok = False
+                        break
+                    newton += info["newton_iters"]
+                    lin += info["linear_iters"]
+                    ok = ok and info["status"] == 0 and info["last_linear_status"] == 0
+                s.close()
+                row.append({"n": n, "newton": newton, "linear": lin,
+                            "per_newton": (lin / newton) if newton else None, "converged": ok})
+            table[f"case{case}/{name}"] = row
+    wall = time.perf_counter() - t0
+    if rank != 0:
+        return
+    print(json.dumps({"metric": "FGMRES iterations per Newton iteration (Sec. 4.3 scaling study)",
+                      "sizes": sizes, "rtol": 1e-5, "wall_s": wall, "table": table}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -491,6 +539,8 @@ def main():
         run_reference(args, rank, world)
     elif args.sequence > 0:
         run_sequence(args, rank, world, local)
+    elif args.scaling2d:
+        run_scaling2d(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -6,9 +6,9 @@ preconditioning arithmetic; both the CUDA path and the CPU oracle consume
 what it produces.
 """
 from .fields import gaussian_random_field, iid_log_normal, channelised, layered
-from .recipes import make_problem, RECIPE_SHAPES, default_fluid, bennison_oil
+from .recipes import make_problem, RECIPE_SHAPES, default_fluid, bennison_oil, scaling_case
 
 __all__ = [
     "gaussian_random_field", "iid_log_normal", "channelised", "layered",
-    "make_problem", "RECIPE_SHAPES", "default_fluid", "bennison_oil",
+    "make_problem", "RECIPE_SHAPES", "default_fluid", "bennison_oil", "scaling_case",
 ]

@@ -153,3 +153,56 @@ def perturbed_state(prob, seed, dp=2.0e5, dT=5.0):
     p_k = prob["p_n"] + dp * rng.standard_normal(N)
     T_k = prob["T_n"] + dT * rng.standard_normal(N)
     return p_k, T_k
+
+
+# Sec. 4.3 (problem-size scaling): Cases I-V on a 20 m x 20 m square
+SCALING_CASES = {
+    1: dict(aniso=False, sources="heaters", T0=288.706, dt_days=10.0),
+    2: dict(aniso=False, sources="wells", q=5.0e-8, T0=288.706, dt_days=10.0),
+    3: dict(aniso=False, sources="wells", q=1.0e-6, T0=320.0, dt_days=10.0),
+    4: dict(aniso=True, sources="heaters", T0=288.706, dt_days=10.0),
+    5: dict(aniso=True, sources="wells", q=1.0e-6, T0=288.706, dt_days=0.5),
+}
+
+
+def scaling_case(case, n):
+    """Case `case` (1..5) of the paper's problem-size scaling study on an
+    n x n grid of the 20 m square, one 1 m thick layer of cells (the paper's
+    domain is two-dimensional; the thickness is a reading). Homogeneous
+    porosity 0.2 and permeability 3e-13 m^2, K_x = 3e-11 m^2 in the
+    anisotropic Cases IV-V; the heavy oil of Sec. 2.1.4 (bennison_oil) with
+    Table 2's constants (initial pressure 4.1369e5 Pa, rock conductivity
+    1.7295772056 W/m/K); injection and heater temperature 422.039 K; initial
+    temperature 288.706 K (Case III: 320 K); time step 10 days (Case V: 12
+    hours). Sources (their positions are not printed; readings): 6 heaters
+    (U = 5.44409e-6 W/K) at x in {L/4, L/2, 3L/4}, y in {L/3, 2L/3}; or 3 rate
+    injectors at x = L/6 and 3 rate producers at x = 5L/6, y in {L/4, L/2,
+    3L/4}, each at rate q."""
+    c = SCALING_CASES[case]
+    L = 20.0
+    N = n * n
+    dx = L / n
+    cell = lambda fx: min(n - 1, int(fx * n))
+    K = np.full(N, 3.0e-13)
+    Kx = np.full(N, 3.0e-11) if c["aniso"] else K.copy()
+    T_hot = 422.039
+    wells = []
+    if c["sources"] == "heaters":
+        for fx in (0.25, 0.5, 0.75):
+            for fy in (1.0 / 3.0, 2.0 / 3.0):
+                wells.append(dict(i=cell(fx), j=cell(fy), k0=0, k1=0, kind=2, value=0.0,
+                                  T_inj=T_hot, U=5.44409e-6))
+    else:
+        for fy in (0.25, 0.5, 0.75):
+            wells.append(dict(i=cell(1.0 / 6.0), j=cell(fy), k0=0, k1=0, kind=0, value=c["q"],
+                              T_inj=T_hot, U=0.0))
+            wells.append(dict(i=cell(5.0 / 6.0), j=cell(fy), k0=0, k1=0, kind=3, value=c["q"],
+                              T_inj=0.0, U=0.0))
+    p_n = np.full(N, 4.1369e5)
+    T_n = np.full(N, c["T0"])
+    return dict(
+        recipe=f"scaling{case}", nx=n, ny=n, nz=1, dx=dx, dy=dx, dz=1.0, g=9.81,
+        fluid=bennison_oil(), Kx=Kx, Ky=K.copy(), Kz=K.copy(), phi=np.full(N, 0.2),
+        kTr=np.full(N, 1.7295772056), wells=wells, p_n=p_n, T_n=T_n, p_k=p_n.copy(),
+        T_k=T_n.copy(), dt=c["dt_days"] * DAY,
+    )

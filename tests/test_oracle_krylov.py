@@ -181,3 +181,21 @@ def test_line_search_rescues_a_step_where_full_newton_diverges():
     for k, a in enumerate(alphas):
         assert relf[k + 1] <= (1.0 - 1e-4 * a) * relf[k]
     assert relf[-1] <= 1e3 * relf[-2] ** 2
+
+
+@pytest.mark.parametrize("case", [1, 2, 3, 4, 5])
+def test_scaling_cases_are_well_posed(case):
+    """The problem-size scaling Cases I-V (Sec. 4.3) at n = 20: sources
+    inside the square, heaters or 3 + 3 rate wells as stated, and a
+    backward-Euler step that the oracle's Newton with line search solves to
+    the paper's 1e-8 tolerances."""
+    from oracle import newton
+    from synthetic import scaling_case
+    prob = scaling_case(case, 20)
+    kinds = sorted(w["kind"] for w in prob["wells"])
+    assert kinds == ([2] * 6 if case in (1, 4) else [0, 0, 0, 3, 3, 3])
+    assert all(0 <= w["i"] < 20 and 0 <= w["j"] < 20 for w in prob["wells"])
+    assert abs(prob["dx"] * prob["nx"] - 20.0) < 1e-12
+    p, T, hist = newton.newton_step(prob, max_newton=10, tol_f=1e-8, tol_dx=1e-8)
+    assert len(hist) <= 10
+    assert hist[-1][0] <= 1e-8 or hist[-1][1] is not None and hist[-1][1] <= 1e-8
