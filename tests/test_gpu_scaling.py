@@ -3,7 +3,6 @@
 iterations per Newton iteration grow slowly as the mesh is refined, and the
 Schur approximation S~_T needs fewer of them than S~_ATT and S~_diag (the
 ordering of the paper's Table 8)."""
-import numpy as np
 import pytest
 
 from synthetic import scaling_case
