@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-variant", action="store_true",
                     help="skip the FP32-hierarchy + learned-Schur variant")
     ap.add_argument("--train-problems", type=int, default=16)
-    ap.add_argument("--nu", type=int, default=2, help="l1-Jacobi sweeps before and after")
+    ap.add_argument("--nu", type=int, default=3, help="l1-Jacobi sweeps before and after")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--sequence", type=int, default=0,
                     help="run this many backward-Euler steps with Newton (e.g. on "

@@ -33,7 +33,7 @@ constexpr int kMaxChebDegree = 4;
 struct AmgOpts {
   int interp = 1;        // 0 classical, 1 extended+i
   int smoother = 0;      // 0 l1-Jacobi, 1 Chebyshev
-  int nu_pre = 2, nu_post = 2, cheb_degree = 2;
+  int nu_pre = 3, nu_post = 3, cheb_degree = 2;
   double theta = 0.25;
   int max_levels = 25, coarse_size = 64, max_coarse_dense = 2048;
   unsigned long long seed = 0;

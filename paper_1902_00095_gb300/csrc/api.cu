@@ -190,8 +190,8 @@ void tp_default_opts(tp_precond_opts* o) {
   o->precision = 0;
   o->interp = 1;
   o->smoother = 0;
-  o->nu_pre = 2;
-  o->nu_post = 2;
+  o->nu_pre = 3;
+  o->nu_post = 3;
   o->cheb_degree = 2;
   o->theta = 0.25;
   o->max_levels = 25;

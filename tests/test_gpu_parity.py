@@ -133,7 +133,7 @@ def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax
     rng = np.random.default_rng(3)
     b = rng.standard_normal(A[0].size - 1)
     xg = g.vcycle(b)
-    xo = oamg.vcycle(oh, b, 0, 2, 2)
+    xo = oamg.vcycle(oh, b, 0, 3, 3)
     assert np.max(np.abs(xg - xo)) <= 1e-11 * np.max(np.abs(xo))
     g.close()
 
@@ -236,8 +236,8 @@ def test_block_preconditioner_matches_oracle(variant):
     s.build(variant=variant, seed=7)
     oh_pp = oamg.setup(osys.App, seed=7)
     oh_S = oamg.setup(oS, seed=7, interp="classical")
-    M = okry.block_preconditioner(osys, lambda r: oamg.vcycle(oh_pp, r, 0, 2, 2),
-                                  lambda r: oamg.vcycle(oh_S, r, 0, 2, 2),
+    M = okry.block_preconditioner(osys, lambda r: oamg.vcycle(oh_pp, r, 0, 3, 3),
+                                  lambda r: oamg.vcycle(oh_S, r, 0, 3, 3),
                                   "full" if variant == 0 else "lower")
     rng = np.random.default_rng(2)
     vp, vT = rng.standard_normal(s.N), rng.standard_normal(s.N)
