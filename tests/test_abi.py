@@ -38,7 +38,7 @@ def test_binding_signatures_cover_the_header(lib):
 def test_host_only_calls_need_no_gpu(lib):
     from paper_1902_00095_gb300 import thermo
     o = thermo.default_opts()
-    assert o.interp == 1 and o.nu_pre == 2 and abs(o.theta - 0.25) < 1e-15
+    assert o.interp == 1 and o.nu_pre == 3 and abs(o.theta - 0.25) < 1e-15
     assert lib.tp_status_string(-5) == b"AMG setup failed"
     assert lib.tp_status_string(1) == b"not converged"
 
