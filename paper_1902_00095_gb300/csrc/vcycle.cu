@@ -64,39 +64,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, const int* __restrict__ r
   if (valid && lane == 0) xout[row] = (TO)(xin[row] + dinv[row] * ((TV)b[row] - ax));
 }
 
-// Prolongation fused into the first post-smoothing sweep (CSR levels):
-// with xp = x + P e, x_out = xp + dinv (b - A xp); every lane forms xp_j for
-// the columns it visits from P's row j (at most a few weights), so the
-// prolonged vector is never written and one launch replaces two.
-template <int LANES, class TV, class TB, class TO, class TP>
-__global__ void __launch_bounds__(256) k_prolong_jacobi(
-    int n, const int* __restrict__ rp, const int* __restrict__ col, const TV* __restrict__ val,
-    const TV* __restrict__ dinv, const TB* __restrict__ b, const TV* __restrict__ x,
-    const int* __restrict__ Prp, const int* __restrict__ Pcol, const TP* __restrict__ Pval,
-    const TV* __restrict__ e, TO* __restrict__ xout) {
-  pdl_wait();
-  pdl_trigger();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row = t / LANES, lane = t % LANES;
-  const bool valid = row < n;
-  auto xp = [&](int j) {
-    TV v = x[j];
-    for (int q = Prp[j]; q < Prp[j + 1]; ++q) v += widen<TV, TP>(Pval[q]) * e[Pcol[q]];
-    return v;
-  };
-  TV acc = TV(0);
-  if (valid) {
-    const int e1 = rp[row + 1];
-    for (int q = rp[row] + lane; q < e1; q += LANES) acc += val[q] * xp(col[q]);
-  }
-  acc = group_sum<LANES>(acc);
-  if (valid && lane == 0) {
-    const TV xi = xp(row);
-    xout[row] = (TO)(xi + dinv[row] * ((TV)b[row] - acc));
-  }
-}
-
-// x = dinv b (first sweep from a zero guess)// x = dinv b (first sweep from a zero guess)
+// x = dinv b (first sweep from a zero guess)
 template <class TV, class TB>
 __global__ void k_jacobi0(int n, const TV* __restrict__ dinv, const TB* __restrict__ b,
                           TV* __restrict__ x) {
@@ -338,23 +306,6 @@ void prolong(int lanes, const DevCSR& P, const TP* val, const TV* e, TV* x, cuda
   TP_LAUNCH_CHECK();
 }
 
-template <class TV, class TB, class TO, class TP>
-void prolong_sweep(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b,
-                   const TV* x, const DevCSR& P, const TP* pval, const TV* e, TO* xout,
-                   cudaStream_t s) {
-  const int g = grid_for((long long)A.n * lanes);
-  switch (lanes) {
-#define TP_CASE(L)                                                                          \
-  case L:                                                                                   \
-    launch_pdl(k_prolong_jacobi<L, TV, TB, TO, TP>, g, kBlock, s, A.n, A.rowptr, A.col, val, \
-               dinv, b, x, P.rowptr, P.col, pval, e, xout);                                 \
-    break;
-    TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
-#undef TP_CASE
-  }
-  TP_LAUNCH_CHECK();
-}
-
 template <class TB, class TO>
 void coarse(int n, const double* inv, const TB* b, TO* x, cudaStream_t s) {
   launch_pdl(k_coarse<TB, TO>, grid_for((long long)n * 32), kBlock, s, n, inv, b, x);
@@ -508,33 +459,14 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s);
   else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
   TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s);
+  if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
+  else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
   // post-smoothing; on the probed level one event pair spans all sweeps
   // (one pair per launch would put an event node between every two kernels)
   Probe* span = (pr && sm.kind == 0) ? pr : nullptr;
-  // CSR levels (not the probed one) fold the prolongation into the first
-  // post-smoothing sweep; the ELL finest level keeps two streaming kernels
-  const bool fuse = sm.kind == 0 && v.ell_w == 0 && nu_post >= 1 && !span;
-  if (fuse) {
-    TO* fo = (nu_post == 1 && final_out) ? final_out : nullptr;
-    if (fo) {
-      if (v.Ph) prolong_sweep<TV, TB, TO, __nv_bfloat16>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b,
-                                                         cur, v.P, v.Ph, ec, fo, s);
-      else prolong_sweep<TV, TB, TO, TV>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, cur, v.P,
-                                         Vals<TV>::P(v), ec, fo, s);
-      return nullptr;
-    }
-    if (v.Ph) prolong_sweep<TV, TB, TV, __nv_bfloat16>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b,
-                                                       cur, v.P, v.Ph, ec, oth, s);
-    else prolong_sweep<TV, TB, TV, TV>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, cur, v.P,
-                                       Vals<TV>::P(v), ec, oth, s);
-    std::swap(cur, oth);
-  } else {
-    if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
-    else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
-  }
   double span_bytes = 0.0;
   if (span) span->before(s);
-  for (int k = fuse ? 2 : 1; k <= nu_post; ++k) {
+  for (int k = 1; k <= nu_post; ++k) {
     if (k == nu_post && final_out) {
       smooth_step<TV, TB, TO>(sm, nullptr, v, dinv, b, cur, final_out, s);
       span_bytes += sweep_bytes<TV, TB, TO>(v.A);
