@@ -65,9 +65,10 @@ __global__ void k_rhs_minus(int N, const int* __restrict__ rp, const int* __rest
                             const double* __restrict__ x, double* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const double bi = b[i];  // issued before the gathers
   double acc = 0.0;
   for (int e = rp[i]; e < rp[i + 1]; ++e) acc += val[e] * x[col[e]];
-  out[i] = b[i] - acc;
+  out[i] = bi - acc;
 }
 
 // w = D A z (block-CSR, Eq. AXR); optionally stores z into Z_j.
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(256) k_block_spmv(int N, const int* __restrict
                                                     const double* __restrict__ scales) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const double zpi = zp[i], zTi = zT[i];  // issued before the gathers
   double ap = 0.0, aT = 0.0;
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
     const int j = col[e];
@@ -92,8 +94,8 @@ __global__ void __launch_bounds__(256) k_block_spmv(int N, const int* __restrict
     aT += b.z * xp + b.w * xT;
   }
   if (Zp) {
-    Zp[i] = zp[i];
-    ZT[i] = zT[i];
+    Zp[i] = zpi;
+    ZT[i] = zTi;
   }
   const double s0 = scales ? scales[0] : 1.0, s1 = scales ? scales[1] : 1.0;
   wp[i] = s0 * ap;

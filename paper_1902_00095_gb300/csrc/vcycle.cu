@@ -60,8 +60,16 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, const int* __restrict__ r
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
+  // the row's own operands are loaded before the dot so their latency
+  // overlaps the gathers instead of following the reduction
+  TV xi = TV(0), di = TV(0), bi = TV(0);
+  if (valid && lane == 0) {
+    xi = xin[row];
+    di = dinv[row];
+    bi = (TV)b[row];
+  }
   TV ax = row_dot<LANES, TV, TV>(rp, col, val, xin, row, valid, lane);
-  if (valid && lane == 0) xout[row] = (TO)(xin[row] + dinv[row] * ((TV)b[row] - ax));
+  if (valid && lane == 0) xout[row] = (TO)(xi + di * (bi - ax));
 }
 
 // x = dinv b (first sweep from a zero guess)
@@ -87,6 +95,11 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
+  TV d = TV(0), bi = TV(0);
+  if (valid && lane == 0) {
+    d = dinv[row];
+    bi = (TV)b[row];
+  }
   TV acc = TV(0);
   if (valid) {
     const int e1 = rp[row + 1];
@@ -96,10 +109,7 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
     }
   }
   acc = group_sum<LANES>(acc);
-  if (valid && lane == 0) {
-    const TV d = dinv[row], bi = (TV)b[row];
-    x[row] = d * bi + d * (bi - acc);
-  }
+  if (valid && lane == 0) x[row] = d * bi + d * (bi - acc);
 }
 
 // ELL forms (slot-major, one thread per row, coalesced over rows)
@@ -129,8 +139,9 @@ __global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __r
   pdl_trigger();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
+  const TV xi = xin[row], di = dinv[row], bi = (TV)b[row];
   const TV ax = ell_dot<TV, TV>(n, w, ecol, eval, xin, row);
-  xout[row] = (TO)(xin[row] + dinv[row] * ((TV)b[row] - ax));
+  xout[row] = (TO)(xi + di * (bi - ax));
 }
 
 template <class TV, class TB>
@@ -143,7 +154,8 @@ __global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* _
   pdl_trigger();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
-  r[row] = (TV)b[row] - ell_dot<TV, TV>(n, w, ecol, eval, x, row);
+  const TV bi = (TV)b[row];
+  r[row] = bi - ell_dot<TV, TV>(n, w, ecol, eval, x, row);
 }
 
 template <class TV, class TB>
@@ -156,6 +168,7 @@ __global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* _
   pdl_trigger();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
+  const TV d = dinv[row], bi = (TV)b[row];
   TV acc = TV(0);
 #pragma unroll
   for (int k = 0; k < kEllMaxW; ++k) {
@@ -165,7 +178,6 @@ __global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* _
       acc += eval[q] * (dinv[j] * (TV)b[j]);
     }
   }
-  const TV d = dinv[row], bi = (TV)b[row];
   x[row] = d * bi + d * (bi - acc);
 }
 
@@ -181,8 +193,10 @@ __global__ void __launch_bounds__(256) k_residual(int n, const int* __restrict__
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
+  TV bi = TV(0);
+  if (valid && lane == 0) bi = (TV)b[row];
   TV ax = row_dot<LANES, TV, TV>(rp, col, val, x, row, valid, lane);
-  if (valid && lane == 0) r[row] = (TV)b[row] - ax;
+  if (valid && lane == 0) r[row] = bi - ax;
 }
 
 // y = R x (restriction; R values of type TP)
@@ -211,8 +225,10 @@ __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ 
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
+  TV xi = TV(0);
+  if (valid && lane == 0) xi = x[row];
   TV pe = row_dot<LANES, TV, TV, TP>(rp, col, val, e, row, valid, lane);
-  if (valid && lane == 0) x[row] += pe;
+  if (valid && lane == 0) x[row] = xi + pe;
 }
 
 // x = Ainv b on the coarsest level (dense FP64 inverse), one warp per row
