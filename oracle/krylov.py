@@ -218,3 +218,19 @@ def direct_solution(sys, bp, bT):
     A = scipy.sparse.diags(d) @ sys.scipy()
     x = scipy.sparse.linalg.spsolve(A.tocsc(), d * b)
     return x[0::2].copy(), x[1::2].copy()
+
+
+def schur_condition_numbers(prob, p, T):
+    """Sec. 4.2 (Table 4): 2-norm condition numbers of S~^{-1} S for the
+    three Schur approximations (S~_diag, S~_ATT, S~_T) and of A_TT and the
+    exact Schur complement S = A_TT - A_Tp A_pp^{-1} A_pT, all dense (small
+    grids only)."""
+    sys, bp, bT, S = assemble(prob, p, T)
+    dense = lambda A: amg.to_dense(A)
+    App, ApT, ATp, ATT = (dense(x) for x in (sys.App, sys.ApT, sys.ATp, sys.ATT))
+    Sx = ATT - ATp @ np.linalg.solve(App, ApT)
+    St = dense(S)
+    Sd = physics.schur_diag(sys.rowptr, sys.col, sys.val)
+    c = np.linalg.cond
+    return dict(diag=c(np.linalg.solve(Sd, Sx)), att=c(np.linalg.solve(ATT, Sx)),
+                T=c(np.linalg.solve(St, Sx)), ATT=c(ATT), S=c(Sx))

@@ -199,3 +199,40 @@ def test_scaling_cases_are_well_posed(case):
     p, T, hist = newton.newton_step(prob, max_newton=10, tol_f=1e-8, tol_dx=1e-8)
     assert len(hist) <= 10
     assert hist[-1][0] <= 1e-8 or hist[-1][1] is not None and hist[-1][1] <= 1e-8
+
+
+def _table4_case(kind, high_perm, shape=(8, 8, 3)):
+    """Heater (H), well (W) or both on a small heterogeneous grid of the
+    paper's heavy oil, permeability x1000 for the high-permeability cases,
+    evaluated at the state after one backward-Euler step."""
+    from oracle import newton
+    from synthetic import bennison_oil
+    nx, ny, nz = shape
+    prob = make_problem("tiny", shape=shape, seed=8, fluid=bennison_oil(), dt_days=10.0)
+    if high_perm:
+        for k in ("Kx", "Ky", "Kz"):
+            prob[k] = prob[k] * 1000.0
+    wells = []
+    if "W" in kind:
+        wells += [dict(i=0, j=0, k0=0, k1=nz - 1, kind=0, value=1e-3, T_inj=422.039, U=0.0),
+                  dict(i=nx - 1, j=ny - 1, k0=0, k1=nz - 1, kind=3, value=1e-3, T_inj=0.0, U=0.0)]
+    if "H" in kind:
+        wells += [dict(i=nx // 2, j=ny // 2, k0=0, k1=nz - 1, kind=2, value=0.0, T_inj=422.039,
+                       U=5e3)]
+    prob["wells"] = wells
+    p, T, _ = newton.newton_step(prob, max_newton=8)
+    return krylov.schur_condition_numbers(prob, p, T)
+
+
+@pytest.mark.parametrize("kind,high_perm", [("H", False), ("W", False), ("WH", False),
+                                            ("W", True), ("WH", True)])
+def test_table4_ordering_of_schur_approximations(kind, high_perm):
+    """Sec. 4.2 / Table 4, in kind: S~_T^{-1} S stays close to the identity
+    (condition number below 2 here, at most 6 in the paper) in every case,
+    while S~_ATT and S~_diag degrade once wells drive advection (the paper's
+    W and high-permeability columns)."""
+    k = _table4_case(kind, high_perm)
+    assert k["T"] < 2.0, k
+    assert k["T"] <= k["att"] and k["T"] <= k["diag"], k
+    if "W" in kind:
+        assert k["att"] > 5 * k["T"] and k["diag"] > 5 * k["T"], k
