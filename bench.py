@@ -201,10 +201,12 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def train_schur_model(args):
+def train_schur_model(args, after_step=False):
     """Train the learned Schur correction on the GPU (untimed): exact Schur
     columns probed on --train-problems seeded 32x32x16 problems of the
-    64x64x32 recipe, 128 columns each, 40 epochs of Adam."""
+    64x64x32 recipe, 128 columns each, 40 epochs of Adam; with after_step the
+    systems are those at the start of a second time step (behind a
+    temperature front), as in a time-step sequence."""
     from paper_1902_00095_gb300 import learned as L
     from paper_1902_00095_gb300 import thermo
     from synthetic.mlp import flatten, initial_params
@@ -219,6 +221,8 @@ def train_schur_model(args):
         else:
             ts.set_fields(tp["Kx"], tp["Ky"], tp["Kz"], tp["phi"], tp["kTr"])
             ts.set_wells(tp["wells"])
+        if after_step:
+            tp = L.advance_one_step(ts, tp)
         parts.append(L.collect_samples(ts, tp, 128, rng))
     ts.close()
     mlp, hist = L.train(L.concat(parts), flatten(initial_params(0)), epochs=40)
@@ -438,7 +442,7 @@ def run_sequence(args, rank, world, local):
     s = thermo.Solver.from_problem(prob)
     train = None
     if args.sequence_variant:
-        mlp, hist, t_train = train_schur_model(args)
+        mlp, hist, t_train = train_schur_model(args, after_step=True)
         s.set_schur_model(mlp)
         opts = thermo.default_opts(precision=1, schur=1, nu_pre=args.nu, nu_post=args.nu)
         train = {"problems": args.train_problems, "loss_first": hist[0], "loss_last": hist[-1],

@@ -209,3 +209,51 @@ def test_trained_network_never_loses_to_the_plain_approximation():
     assert err_learned <= 1.05 * err_plain + 1e-7, (err_learned, err_plain, mlp.selected_epoch)
     assert learned["iters"] <= plain["iters"] + 2
     assert learned["rel_res"] <= 1e-8
+
+
+def test_learned_correction_gains_at_time_stepping_states():
+    """What the learned correction gains where S~_T is not exact: at the
+    start of a second 30-day step (behind a temperature front) S~_T of
+    Eq. Se differs from the exact Schur complement by under a per cent; a
+    network trained on probed exact entries of six such problems lowers that
+    error on an unseen problem by a sixth or more, and FGMRES needs at most
+    one iteration more than with plain S~_T."""
+    from paper_1902_00095_gb300 import learned as L
+    rng = np.random.Generator(np.random.PCG64(3))
+    shape = (12, 12, 8)
+    parts = []
+    for q in range(6):
+        prob = make_problem("grf32", shape=shape, seed=1000 + q, dt_days=30.0)
+        s = thermo.Solver.from_problem(prob)
+        parts.append(L.collect_samples(s, L.advance_one_step(s, prob), 192, rng))
+        s.close()
+    mlp, hist = L.train(L.concat(parts), flatten(initial_params(0)), epochs=40, batch=512,
+                        lr=1e-3)
+    assert mlp.selected_epoch > 0, mlp.val_losses[:3]
+    prob = make_problem("grf32", shape=shape, seed=1999, dt_days=30.0)
+    s = thermo.Solver.from_problem(prob)
+    nxt = L.advance_one_step(s, prob)
+    s.assemble(nxt["p_k"], nxt["T_k"], nxt["p_n"], nxt["T_n"], nxt["dt"])
+    s.build(schur=0)
+    _, _, plain = s.solve(rtol=1e-8)
+    rp, col, val, S, _ = s.export_system()
+    cols = rng.choice(s.N, 96, replace=False)
+    entry, value, its, st = s.probe_schur_columns(cols, 1e-11)
+    assert st == 0
+    s.set_schur_model(mlp)
+    s.build(schur=1)
+    _, _, learned = s.solve(rtol=1e-8)
+    assert s.learned_status()[1] is False
+    SL = s.export_level(1, 0)["A"][2]
+    ok = entry >= 0
+    e = entry[ok]
+    tgt = value[ok]
+    rows = np.repeat(np.arange(s.N), np.diff(rp))[e]
+    dpos = np.array([rp[i] + np.searchsorted(col[rp[i]:rp[i + 1]], i) for i in range(s.N)])
+    Sd = S[dpos[rows]]
+    err_plain = np.sqrt(np.mean(((S[e] - tgt) / Sd) ** 2))
+    err_learned = np.sqrt(np.mean(((SL[e] - tgt) / Sd) ** 2))
+    assert 1e-4 < err_plain < 5e-2, err_plain
+    assert err_learned < 0.85 * err_plain, (err_learned, err_plain)
+    assert learned["iters"] <= plain["iters"] + 1, (learned["iters"], plain["iters"])
+    assert learned["rel_res"] <= 1e-8
