@@ -1,7 +1,8 @@
-// Learned correction of the Schur approximation: per-cell features, a
-// 24 -> 64 -> 64 -> 8 GELU MLP on BF16 tensor cores (mma.sync m16n8k16,
-// FP32 accumulation) for inference and training, Adam, and the corrected
-// S~_T (Eq. Se) with a per-row guard.
+// Learned correction of the Schur approximation: per-cell features, the
+// training of a 24 -> 64 -> 64 -> 8 GELU MLP (forward and backward of
+// 16-sample warp tiles with mma.sync m16n8k16, BF16 operands, FP32
+// accumulation), Adam, and the corrected S~_T (Eq. Se) with a per-row
+// guard. Inference over all cells runs on tcgen05 (mlp_tc.cu).
 //
 // Row i of S~_T becomes S_ii <- S~_ii exp(o_0) + o_7 S~_ii and
 // S_ij <- S~_ij exp(o_d) for face direction d = 1..6 of neighbour j; the
@@ -136,27 +137,6 @@ __device__ __forceinline__ void mlp_forward_tile(const MlpDev& m, const float* _
     unsigned bb0, bb1;
     load_b(m.W3, kMlpHidden, 0, kc * 16, g, t, bb0, bb1);
     mma16816(T.o, T.h2[kc][0], T.h2[kc][1], T.h2[kc][2], T.h2[kc][3], bb0, bb1);
-  }
-}
-
-// inference: O[n][8] (FP32) for every cell
-__global__ void __launch_bounds__(128) k_mlp_forward(MlpDev m, int n, const float* __restrict__ X,
-                                                     float* __restrict__ O) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int r0 = warp * 16; r0 < n; r0 += nwarps * 16) {
-    Tile T;
-    mlp_forward_tile(m, X, n, r0, g, t, T);
-    const int ra = r0 + g, rb = r0 + g + 8;
-    if (ra < n) {
-      O[(size_t)ra * kMlpOut + 2 * t] = T.o[0];
-      O[(size_t)ra * kMlpOut + 2 * t + 1] = T.o[1];
-    }
-    if (rb < n) {
-      O[(size_t)rb * kMlpOut + 2 * t] = T.o[2];
-      O[(size_t)rb * kMlpOut + 2 * t + 1] = T.o[3];
-    }
   }
 }
 
@@ -453,11 +433,12 @@ void mlp_pack(const MlpDev& m, cudaStream_t s) {
 
 void mlp_forward(const MlpDev& m, int n, const float* X, float* O, cudaStream_t s) {
   if (n <= 0) return;
-  const int tiles = (n + 15) / 16;
-  int blocks = (tiles + 3) / 4;
-  if (blocks > 4096) blocks = 4096;
-  k_mlp_forward<<<blocks, 128, 0, s>>>(m, n, X, O);
-  TP_LAUNCH_CHECK();
+  TP_CUDA_TRY(cudaMemsetAsync(m.err, 0, sizeof(int), s));
+  mlp_forward_tc(m, n, X, O, m.err, s);
+  int h = 0;
+  TP_CUDA_TRY(cudaMemcpyAsync(&h, m.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h != 0) fail(TP_ECUDA, "MLP forward: a tensor-core completion wait timed out");
 }
 
 void mlp_gradient(const MlpDev& m, int B, const float* X, const int* slot, const double* St,

@@ -27,11 +27,15 @@ struct MlpDev {
   __nv_bfloat16* W3 = nullptr;   // [8][64]
   __nv_bfloat16* W2T = nullptr;  // [64][64]
   __nv_bfloat16* W3T = nullptr;  // [64][16]
+  int* err = nullptr;            // tensor-core forward: bit 0 = mbarrier wait timed out
   int step = 0;
 };
 
 void mlp_pack(const MlpDev& m, cudaStream_t s);
+// inference O[n][8] = MLP(X[n][24]) on the tcgen05 tensor cores (mlp_tc.cu);
+// throws if a wait on the tensor cores timed out
 void mlp_forward(const MlpDev& m, int n, const float* X, float* O, cudaStream_t s);
+void mlp_forward_tc(const MlpDev& m, int n, const float* X, float* O, int* err, cudaStream_t s);
 // gradient of the mean squared relative error over B samples into grad
 // (loss in grad[kMlpParams]); partials holds ceil(B/16) * kMlpPartial floats
 void mlp_gradient(const MlpDev& m, int B, const float* X, const int* slot, const double* St,
