@@ -680,6 +680,7 @@ int tp_mlp_create(tp_mlp** out, const double* params, void* cuda_stream) {
   m.W2T = a->pool.alloc<__nv_bfloat16>(tp::kMlpHidden * tp::kMlpHidden);
   m.W3T = a->pool.alloc<__nv_bfloat16>(tp::kMlpHidden * 16);
   m.err = a->pool.alloc<int>(1);
+  m.Wtc = a->pool.alloc<__nv_bfloat16>(tp::kMlpTcWeights);
   TP_CUDA_TRY(cudaMallocHost(&a->host, sizeof(double) * tp::kMlpPartial));
   *out = a;
   int st = tp_mlp_set_params(a, params);

@@ -375,6 +375,21 @@ __global__ void k_mlp_pack(MlpDev m) {
     const int h = p / 16, o = p % 16;
     m.W3T[p] = __float2bfloat16_rn(o < kMlpOut ? P[kOffW3 + o * kMlpHidden + h] : 0.f);
   }
+  // the same weights in the tcgen05 operand layout
+  if (p < kMlpHidden * kMlpInPad) {
+    const int o = p / kMlpInPad, i = p % kMlpInPad;
+    m.Wtc[mlp_core_off(o, i, 32) / 2] =
+        __float2bfloat16_rn(i < kMlpIn ? P[kOffW1 + o * kMlpIn + i] : 0.f);
+  }
+  if (p < kMlpHidden * kMlpHidden) {
+    const int o = p / kMlpHidden, i = p % kMlpHidden;
+    m.Wtc[64 * 32 + mlp_core_off(o, i, 64) / 2] = __float2bfloat16_rn(P[kOffW2 + p]);
+  }
+  if (p < 16 * kMlpHidden) {
+    const int o = p / kMlpHidden, i = p % kMlpHidden;
+    m.Wtc[64 * 32 + 64 * 64 + mlp_core_off(o, i, 64) / 2] =
+        __float2bfloat16_rn(o < kMlpOut ? P[kOffW3 + o * kMlpHidden + i] : 0.f);
+  }
 }
 
 // Row i: S_ii <- S~_ii exp(o_0) + o_7 S~_ii, S_ij <- S~_ij exp(o_d). The row

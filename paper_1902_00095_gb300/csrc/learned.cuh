@@ -16,6 +16,13 @@ constexpr int kOffW3 = kOffB2 + kMlpHidden;
 constexpr int kOffB3 = kOffW3 + kMlpOut * kMlpHidden;
 constexpr int kMlpParams = kOffB3 + kMlpOut;   // 6280
 constexpr int kMlpPartial = kMlpParams + 1;    // + loss
+constexpr int kMlpTcWeights = 64 * 32 + 64 * 64 + 16 * 64;  // bf16 elements of Wtc
+
+// byte offset of element (r, k) of an R x K bf16 tile in the no-swizzle
+// K-major layout of 8-row x 16-byte core matrices used by tcgen05 operands
+__host__ __device__ inline unsigned mlp_core_off(int r, int k, int K) {
+  return (unsigned)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
 
 struct MlpDev {
   float* params = nullptr;  // FP32 master weights [kMlpParams]
@@ -27,6 +34,9 @@ struct MlpDev {
   __nv_bfloat16* W3 = nullptr;   // [8][64]
   __nv_bfloat16* W2T = nullptr;  // [64][64]
   __nv_bfloat16* W3T = nullptr;  // [64][16]
+  // W1 [64 x 32], W2 [64 x 64], W3 padded [16 x 64] back to back in the
+  // tcgen05 shared-memory layout (kMlpTcWeights bf16, copied in one bulk copy)
+  __nv_bfloat16* Wtc = nullptr;
   int* err = nullptr;            // tensor-core forward: bit 0 = mbarrier wait timed out
   int step = 0;
 };

@@ -2,8 +2,10 @@
 // on the fifth-generation tensor cores: tcgen05.mma with BF16 operands in
 // shared memory and FP32 accumulators in tensor memory (TMEM).
 //
-// One CTA of 128 threads takes a tile of 128 cells (the MMA's M). Operands
-// are staged in the no-swizzle K-major layout of 8-row x 16-byte core
+// One CTA of 128 threads takes a tile of 128 cells (the MMA's M). The
+// weights (packed once in the operand layout) and the tile's FP32 features
+// arrive by bulk copy (cp.async.bulk) on an mbarrier; operands are staged in
+// the no-swizzle K-major layout of 8-row x 16-byte core
 // matrices: element (r, k) of an R x K tile sits at byte
 // ((r / 8) * (K / 8) + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2, so core
 // matrices adjacent along K are 128 bytes apart (the descriptor's leading
@@ -32,15 +34,27 @@ constexpr uint32_t kOffH2 = kOffH1 + 128 * 64 * 2;    // [128 x 64]
 constexpr uint32_t kOffW1 = kOffH2 + 128 * 64 * 2;    // [64 x 32]
 constexpr uint32_t kOffW2 = kOffW1 + 64 * 32 * 2;     // [64 x 64]
 constexpr uint32_t kOffW3 = kOffW2 + 64 * 64 * 2;     // [16 x 64]
-constexpr uint32_t kOffBar = kOffW3 + 16 * 64 * 2;    // mbarrier (8 B) + TMEM base (4 B)
-constexpr uint32_t kTcSmemUsed = kOffBar + 16;
+constexpr uint32_t kOffXf = kOffW3 + 16 * 64 * 2;     // [128 x 24] FP32 features (bulk copy)
+constexpr uint32_t kOffBar = kOffXf + 128 * 24 * 4;   // MMA mbarrier, copy mbarrier, TMEM base
+constexpr uint32_t kTcSmemUsed = kOffBar + 32;
+static_assert(kOffW2 - kOffW1 == 64 * 32 * 2 && kOffW3 - kOffW1 == (64 * 32 + 64 * 64) * 2,
+              "weights must be laid out as in MlpDev::Wtc");
 // requested dynamic shared memory: more than a third of the SM's, so at
 // most two CTAs share an SM and their TMEM (2 x 256 of 512 columns)
 constexpr uint32_t kTcSmem = 96 * 1024;
 static_assert(kTcSmemUsed <= kTcSmem, "shared-memory map exceeds the request");
 
-__device__ __forceinline__ uint32_t core_off(int r, int k, int K) {
-  return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+__device__ __forceinline__ uint32_t core_off(int r, int k, int K) { return mlp_core_off(r, k, K); }
+
+// one-dimensional bulk copy global -> shared, completing on an mbarrier
+// (addresses and size multiples of 16 bytes)
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -128,46 +142,48 @@ __device__ __forceinline__ float gelu_tc(float x) {
 
 __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(MlpDev m, int n,
                                                                const float* __restrict__ X,
+                                                               int x_bulk,
                                                                float* __restrict__ O,
                                                                int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-  const uint32_t bar = sbase + kOffBar;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
+  const uint32_t bar = sbase + kOffBar;        // MMA completions
+  const uint32_t cbar = sbase + kOffBar + 8;   // bulk copies
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 16);
+  const int row0 = blockIdx.x * kTcRows;
+  const int rows = min(kTcRows, n - row0);
+  const uint32_t xbytes = x_bulk ? (uint32_t)rows * kMlpIn * 4 : 0u;  // multiple of 16
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(cbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    // weights (already in the operand layout) and this tile's features by
+    // the bulk-copy engine, both completing on cbar
+    const uint32_t wbytes = (uint32_t)kMlpTcWeights * 2;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(cbar),
+                 "r"(wbytes + xbytes)
+                 : "memory");
+    bulk_copy(sbase + kOffW1, m.Wtc, wbytes, cbar);
+    if (xbytes) bulk_copy(sbase + kOffXf, X + (size_t)row0 * kMlpIn, xbytes, cbar);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     sbase + kOffBar + 8),
+                     sbase + kOffBar + 16),
                  "r"(kTcCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  // weights into the core-matrix layout (W3 padded to 16 rows with zeros)
-  __nv_bfloat16* sW1 = reinterpret_cast<__nv_bfloat16*>(smem + kOffW1);
-  __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(smem + kOffW2);
-  __nv_bfloat16* sW3 = reinterpret_cast<__nv_bfloat16*>(smem + kOffW3);
-  for (int p = tid; p < 64 * 32; p += kTcThreads) {
-    const int r = p / 32, k = p % 32;
-    sW1[core_off(r, k, 32) / 2] = m.W1[p];
-  }
-  for (int p = tid; p < 64 * 64; p += kTcThreads) {
-    const int r = p / 64, k = p % 64;
-    sW2[core_off(r, k, 64) / 2] = m.W2[p];
-  }
-  for (int p = tid; p < 16 * 64; p += kTcThreads) {
-    const int r = p / 64, k = p % 64;
-    sW3[core_off(r, k, 64) / 2] = r < kMlpOut ? m.W3[r * 64 + k] : __float2bfloat16_rn(0.f);
-  }
+  __syncthreads();  // barrier initialisation visible before anyone waits on it
+  bar_wait(cbar, 0, err);
   // this thread's cell: features as BF16, K padded to 32 with zeros
-  const int row = blockIdx.x * kTcRows + tid;
+  const int row = row0 + tid;
+  const float* xf = reinterpret_cast<const float*>(smem + kOffXf) + tid * kMlpIn;
   __nv_bfloat16* sX = reinterpret_cast<__nv_bfloat16*>(smem + kOffX);
   for (int k = 0; k < 32; ++k) {
-    const float v = (row < n && k < kMlpIn) ? X[(size_t)row * kMlpIn + k] : 0.f;
+    float v = 0.f;
+    if (row < n && k < kMlpIn) v = x_bulk ? xf[k] : X[(size_t)row * kMlpIn + k];
     sX[core_off(tid, k, 32) / 2] = __float2bfloat16_rn(v);
   }
   fence_async_smem();
@@ -261,7 +277,10 @@ void mlp_forward_tc(const MlpDev& m, int n, const float* X, float* O, int* err, 
   }();
   (void)attr;
   const int blocks = (n + kTcRows - 1) / kTcRows;
-  k_mlp_forward_tc<<<blocks, kTcThreads, kTcSmem, s>>>(m, n, X, O, err);
+  // the features' tile is bulk-copied when X is 16-byte aligned (every
+  // tile then starts on a 96-byte row boundary and spans whole rows)
+  const int x_bulk = (reinterpret_cast<uintptr_t>(X) & 15) == 0 ? 1 : 0;
+  k_mlp_forward_tc<<<blocks, kTcThreads, kTcSmem, s>>>(m, n, X, x_bulk, O, err);
   TP_LAUNCH_CHECK();
 }
 
