@@ -6,6 +6,14 @@
 // On the finest level of an FP32 hierarchy the right-hand side is read in
 // FP64 and the final post-smoothing sweep writes the FP64 result directly,
 // so no conversion passes are needed at the preconditioner boundary.
+//
+// Every kernel is launched as a programmatic dependent launch. The level
+// operators (pattern, values, l1 scaling, coarsest inverse) do not change
+// during a V-cycle, so each kernel loads its share of them before
+// griddepcontrol.wait, while the previous kernel is still running, and only
+// the vectors the previous kernels wrote after it. The first kernel of a
+// V-cycle (level 0 pre-smoothing) waits first: the kernel before it may be a
+// setup kernel that wrote those operators.
 #include "amg.cuh"
 
 namespace tp {
@@ -33,19 +41,50 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
-// row dot sum_j a_ij x_j for the row owned by this thread group
-template <int LANES, class TV, class TX, class TP = TV>
-__device__ __forceinline__ TV row_dot(const int* __restrict__ rp, const int* __restrict__ col,
-                                      const TP* __restrict__ val, const TX* __restrict__ x,
-                                      int row, bool valid, int lane) {
-  TV acc = TV(0);
-  if (valid) {
-    const int e1 = rp[row + 1];
-    for (int e = rp[row] + lane; e < e1; e += LANES)
-      acc += widen<TV, TP>(val[e]) * (TV)x[col[e]];
+// The part of one CSR row a lane owns (entries rp[row] + lane + k LANES):
+// the column indices and values of its first kRowPre entries are held in
+// registers (loaded before the dependency wait), the rest are read in the
+// dot itself. Summation order is the plain lane-strided order.
+constexpr int kRowPre = 4;
+
+template <int LANES, class TP>
+struct RowPre {
+  int e = 0, e1 = 0;
+  int c[kRowPre];
+  TP v[kRowPre];
+
+  __device__ __forceinline__ void load(const int* __restrict__ rp, const int* __restrict__ col,
+                                       const TP* __restrict__ val, int row, bool valid,
+                                       int lane) {
+    if (valid) {
+      e = rp[row] + lane;
+      e1 = rp[row + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < kRowPre; ++k) {
+      const int q = e + k * LANES;
+      c[k] = 0;
+      v[k] = TP{};
+      if (q < e1) {
+        c[k] = col[q];
+        v[k] = val[q];
+      }
+    }
   }
-  return group_sum<LANES>(acc);
-}
+
+  // sum_j a_ij x_j over the lane's entries, reduced over the row's lanes
+  template <class TV, class TX>
+  __device__ __forceinline__ TV dot(const int* __restrict__ col, const TP* __restrict__ val,
+                                    const TX* __restrict__ x) const {
+    TV acc = TV(0);
+#pragma unroll
+    for (int k = 0; k < kRowPre; ++k)
+      if (e + k * LANES < e1) acc += widen<TV, TP>(v[k]) * (TV)x[c[k]];
+    for (int q = e + kRowPre * LANES; q < e1; q += LANES)
+      acc += widen<TV, TP>(val[q]) * (TV)x[col[q]];
+    return group_sum<LANES>(acc);
+  }
+};
 
 // x_out = x_in + dinv (b - A x_in)
 template <int LANES, class TV, class TB, class TO>
@@ -55,31 +94,36 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, const int* __restrict__ r
                                                 const TV* __restrict__ dinv,
                                                 const TB* __restrict__ b,
                                                 const TV* __restrict__ xin, TO* __restrict__ xout) {
-  pdl_wait();
-  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
-  // the row's own operands are loaded before the dot so their latency
+  RowPre<LANES, TV> a;
+  a.load(rp, col, val, row, valid, lane);
+  TV di = TV(0);
+  if (valid && lane == 0) di = dinv[row];
+  pdl_wait();
+  pdl_trigger();
+  // the row's own vector entries are loaded before the dot so their latency
   // overlaps the gathers instead of following the reduction
-  TV xi = TV(0), di = TV(0), bi = TV(0);
+  TV xi = TV(0), bi = TV(0);
   if (valid && lane == 0) {
     xi = xin[row];
-    di = dinv[row];
     bi = (TV)b[row];
   }
-  TV ax = row_dot<LANES, TV, TV>(rp, col, val, xin, row, valid, lane);
+  TV ax = a.template dot<TV, TV>(col, val, xin);
   if (valid && lane == 0) xout[row] = (TO)(xi + di * (bi - ax));
 }
 
 // x = dinv b (first sweep from a zero guess)
 template <class TV, class TB>
 __global__ void k_jacobi0(int n, const TV* __restrict__ dinv, const TB* __restrict__ b,
-                          TV* __restrict__ x) {
+                          TV* __restrict__ x, int first) {
+  if (first) pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const TV d = i < n ? dinv[i] : TV(0);
   pdl_wait();
   pdl_trigger();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = dinv[i] * (TV)b[i];
+  if (i < n) x[i] = d * (TV)b[i];
 }
 
 // two sweeps from a zero guess in one pass:
@@ -89,44 +133,65 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
                                                   const int* __restrict__ col,
                                                   const TV* __restrict__ val,
                                                   const TV* __restrict__ dinv,
-                                                  const TB* __restrict__ b, TV* __restrict__ x) {
-  pdl_wait();
-  pdl_trigger();
+                                                  const TB* __restrict__ b, TV* __restrict__ x,
+                                                  int first) {
+  if (first) pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
-  TV d = TV(0), bi = TV(0);
-  if (valid && lane == 0) {
-    d = dinv[row];
-    bi = (TV)b[row];
-  }
+  RowPre<LANES, TV> a;
+  a.load(rp, col, val, row, valid, lane);
+  TV d = TV(0);
+  if (valid && lane == 0) d = dinv[row];
+  TV dj[kRowPre];
+#pragma unroll
+  for (int k = 0; k < kRowPre; ++k) dj[k] = (a.e + k * LANES < a.e1) ? dinv[a.c[k]] : TV(0);
+  pdl_wait();
+  pdl_trigger();
+  TV bi = TV(0);
+  if (valid && lane == 0) bi = (TV)b[row];
   TV acc = TV(0);
-  if (valid) {
-    const int e1 = rp[row + 1];
-    for (int e = rp[row] + lane; e < e1; e += LANES) {
-      const int j = col[e];
-      acc += val[e] * (dinv[j] * (TV)b[j]);
-    }
+#pragma unroll
+  for (int k = 0; k < kRowPre; ++k)
+    if (a.e + k * LANES < a.e1) acc += a.v[k] * (dj[k] * (TV)b[a.c[k]]);
+  for (int q = a.e + kRowPre * LANES; q < a.e1; q += LANES) {
+    const int j = col[q];
+    acc += val[q] * (dinv[j] * (TV)b[j]);
   }
   acc = group_sum<LANES>(acc);
   if (valid && lane == 0) x[row] = d * bi + d * (bi - acc);
 }
 
-// ELL forms (slot-major, one thread per row, coalesced over rows)
-template <class TV, class TX>
-__device__ __forceinline__ TV ell_dot(int n, int w, const int* __restrict__ ecol,
-                                      const TV* __restrict__ eval, const TX* __restrict__ x,
-                                      int row) {
-  TV acc = TV(0);
+// ELL forms (slot-major, one thread per row, coalesced over rows); a row's
+// slots are held in registers, loaded before the dependency wait
+template <class TV>
+struct EllRow {
+  int c[kEllMaxW];
+  TV v[kEllMaxW];
+
+  __device__ __forceinline__ void load(int n, int w, const int* __restrict__ ecol,
+                                       const TV* __restrict__ eval, int row) {
 #pragma unroll
-  for (int k = 0; k < kEllMaxW; ++k) {
-    if (k < w) {
-      const long long q = (long long)k * n + row;
-      acc += eval[q] * (TV)x[ecol[q]];
+    for (int k = 0; k < kEllMaxW; ++k) {
+      c[k] = 0;
+      v[k] = TV(0);
+      if (k < w) {
+        const long long q = (long long)k * n + row;
+        c[k] = ecol[q];
+        v[k] = eval[q];
+      }
     }
   }
-  return acc;
-}
+
+  template <class TX>
+  __device__ __forceinline__ TV dot(int w, const TX* __restrict__ x) const {
+    TV acc = TV(0);
+#pragma unroll
+    for (int k = 0; k < kEllMaxW; ++k)
+      if (k < w) acc += v[k] * (TV)x[c[k]];
+    return acc;
+  }
+};
 
 template <class TV, class TB, class TO>
 __global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __restrict__ ecol,
@@ -135,12 +200,18 @@ __global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __r
                                                     const TB* __restrict__ b,
                                                     const TV* __restrict__ xin,
                                                     TO* __restrict__ xout) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  EllRow<TV> a;
+  TV di = TV(0);
+  if (row < n) {
+    a.load(n, w, ecol, eval, row);
+    di = dinv[row];
+  }
   pdl_wait();
   pdl_trigger();
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
-  const TV xi = xin[row], di = dinv[row], bi = (TV)b[row];
-  const TV ax = ell_dot<TV, TV>(n, w, ecol, eval, xin, row);
+  const TV xi = xin[row], bi = (TV)b[row];
+  const TV ax = a.dot(w, xin);
   xout[row] = (TO)(xi + di * (bi - ax));
 }
 
@@ -150,12 +221,14 @@ __global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* _
                                                       const TB* __restrict__ b,
                                                       const TV* __restrict__ x,
                                                       TV* __restrict__ r) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  EllRow<TV> a;
+  if (row < n) a.load(n, w, ecol, eval, row);
   pdl_wait();
   pdl_trigger();
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   const TV bi = (TV)b[row];
-  r[row] = bi - ell_dot<TV, TV>(n, w, ecol, eval, x, row);
+  r[row] = bi - a.dot(w, x);
 }
 
 template <class TV, class TB>
@@ -163,21 +236,28 @@ __global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* _
                                                       const TV* __restrict__ eval,
                                                       const TV* __restrict__ dinv,
                                                       const TB* __restrict__ b,
-                                                      TV* __restrict__ x) {
+                                                      TV* __restrict__ x, int first) {
+  if (first) pdl_wait();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  EllRow<TV> a;
+  TV d = TV(0), dj[kEllMaxW];
+#pragma unroll
+  for (int k = 0; k < kEllMaxW; ++k) dj[k] = TV(0);
+  if (row < n) {
+    a.load(n, w, ecol, eval, row);
+    d = dinv[row];
+#pragma unroll
+    for (int k = 0; k < kEllMaxW; ++k)
+      if (k < w) dj[k] = dinv[a.c[k]];
+  }
   pdl_wait();
   pdl_trigger();
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
-  const TV d = dinv[row], bi = (TV)b[row];
+  const TV bi = (TV)b[row];
   TV acc = TV(0);
 #pragma unroll
-  for (int k = 0; k < kEllMaxW; ++k) {
-    if (k < w) {
-      const long long q = (long long)k * n + row;
-      const int j = ecol[q];
-      acc += eval[q] * (dinv[j] * (TV)b[j]);
-    }
-  }
+  for (int k = 0; k < kEllMaxW; ++k)
+    if (k < w) acc += a.v[k] * (dj[k] * (TV)b[a.c[k]]);
   x[row] = d * bi + d * (bi - acc);
 }
 
@@ -188,14 +268,16 @@ __global__ void __launch_bounds__(256) k_residual(int n, const int* __restrict__
                                                   const TV* __restrict__ val,
                                                   const TB* __restrict__ b,
                                                   const TV* __restrict__ x, TV* __restrict__ r) {
-  pdl_wait();
-  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
+  RowPre<LANES, TV> a;
+  a.load(rp, col, val, row, valid, lane);
+  pdl_wait();
+  pdl_trigger();
   TV bi = TV(0);
   if (valid && lane == 0) bi = (TV)b[row];
-  TV ax = row_dot<LANES, TV, TV>(rp, col, val, x, row, valid, lane);
+  TV ax = a.template dot<TV, TV>(col, val, x);
   if (valid && lane == 0) r[row] = bi - ax;
 }
 
@@ -205,12 +287,14 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
                                               const int* __restrict__ col,
                                               const TP* __restrict__ val,
                                               const TV* __restrict__ x, TV* __restrict__ y) {
-  pdl_wait();
-  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
-  TV ax = row_dot<LANES, TV, TV, TP>(rp, col, val, x, row, valid, lane);
+  RowPre<LANES, TP> a;
+  a.load(rp, col, val, row, valid, lane);
+  pdl_wait();
+  pdl_trigger();
+  TV ax = a.template dot<TV, TV>(col, val, x);
   if (valid && lane == 0) y[row] = ax;
 }
 
@@ -220,14 +304,16 @@ __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ 
                                                  const int* __restrict__ col,
                                                  const TP* __restrict__ val,
                                                  const TV* __restrict__ e, TV* __restrict__ x) {
-  pdl_wait();
-  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
+  RowPre<LANES, TP> a;
+  a.load(rp, col, val, row, valid, lane);
+  pdl_wait();
+  pdl_trigger();
   TV xi = TV(0);
   if (valid && lane == 0) xi = x[row];
-  TV pe = row_dot<LANES, TV, TV, TP>(rp, col, val, e, row, valid, lane);
+  TV pe = a.template dot<TV, TV>(col, val, e);
   if (valid && lane == 0) x[row] = xi + pe;
 }
 
@@ -235,13 +321,22 @@ __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ 
 template <class TB, class TO>
 __global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __restrict__ b,
                          TO* __restrict__ x) {
-  pdl_wait();
-  pdl_trigger();
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  double a[kRowPre];
+#pragma unroll
+  for (int k = 0; k < kRowPre; ++k) {
+    const int j = lane + 32 * k;
+    a[k] = (row < n && j < n) ? inv[(long long)row * n + j] : 0.0;
+  }
+  pdl_wait();
+  pdl_trigger();
   if (row >= n) return;
   double acc = 0.0;
-  for (int j = lane; j < n; j += 32) acc += inv[(long long)row * n + j] * (double)b[j];
+#pragma unroll
+  for (int k = 0; k < kRowPre; ++k)
+    if (lane + 32 * k < n) acc += a[k] * (double)b[lane + 32 * k];
+  for (int j = lane + 32 * kRowPre; j < n; j += 32) acc += inv[(long long)row * n + j] * (double)b[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) x[row] = (TO)acc;
@@ -266,12 +361,13 @@ void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB*
 
 template <class TV, class TB>
 void jacobi2z(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b, TV* x,
-              cudaStream_t s) {
+              int first, cudaStream_t s) {
   const int g = grid_for((long long)A.n * lanes);
   switch (lanes) {
-#define TP_CASE(L)                                                                       \
-  case L:                                                                                \
-    launch_pdl(k_jacobi2z<L, TV, TB>, g, kBlock, s, A.n, A.rowptr, A.col, val, dinv, b, x); \
+#define TP_CASE(L)                                                                         \
+  case L:                                                                                  \
+    launch_pdl(k_jacobi2z<L, TV, TB>, g, kBlock, s, A.n, A.rowptr, A.col, val, dinv, b, x, \
+               first);                                                                     \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -376,14 +472,15 @@ void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_
   }
 }
 
+// first: the kernel opens a V-cycle (waits before reading the level operator)
 template <class TV, class TB>
-void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* x,
+void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* x, int first,
                                 cudaStream_t s) {
   if (v.ell_w > 0) {
     launch_pdl(k_jacobi2z_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
-               Vals<TV>::E(v), dinv, b, x);
+               Vals<TV>::E(v), dinv, b, x, first);
   } else {
-    jacobi2z<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, x, s);
+    jacobi2z<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, x, first, s);
   }
 }
 
@@ -458,10 +555,10 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     smooth_step<TV, TB, TV>(sm, nullptr, v, dinv, b, (const TV*)nullptr, x, s);
   } else if (nu_pre >= 2) {
     // the first two l1-Jacobi sweeps from a zero guess fused
-    level_two_sweeps_from_zero<TV, TB>(v, dinv, b, x, s);
+    level_two_sweeps_from_zero<TV, TB>(v, dinv, b, x, l == 0 ? 1 : 0, s);
     done = 2;
   } else {
-    launch_pdl(k_jacobi0<TV, TB>, grid_for(n), kBlock, s, n, dinv, b, x);
+    launch_pdl(k_jacobi0<TV, TB>, grid_for(n), kBlock, s, n, dinv, b, x, l == 0 ? 1 : 0);
   }
   for (int k = done; k < nu_pre; ++k) {
     smooth_step<TV, TB, TV>(sm, pr, v, dinv, b, cur, oth, s);
