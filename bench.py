@@ -489,6 +489,13 @@ def run_sequence(args, rank, world, local):
     }), flush=True)
 
 
+# coarsest AMG grid of the scaling study: at most 64 rows at every size, so
+# that even the 400-cell grid runs multi-level V-cycles, as the paper's hypre
+# setup (coarsening down to a few rows) did; the library default (256) would
+# solve the smallest grids' blocks exactly
+SCALING_COARSE_SIZE = 64
+
+
 def run_scaling2d(args, rank, world, local):
     """Sec. 4.3 problem-size scaling: Cases I-V on n x n grids of the 20 m
     square (n = 20..320), two time steps each, Newton with line search and
@@ -516,7 +523,8 @@ def run_scaling2d(args, rank, world, local):
                     try:
                         p, T, info = s.newton_step(p, T, prob["dt"], max_newton=10, tol_f=1e-8,
                                                    tol_dx=1e-8, rtol=1e-5, maxit=200,
-                                                   restart=30, reuse=True, schur=sc)
+                                                   restart=30, reuse=True, schur=sc,
+                                                   coarse_size=SCALING_COARSE_SIZE)
                     except thermo.ThermoError:
                         ok = False
                         break

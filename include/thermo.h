@@ -105,7 +105,10 @@ typedef struct {
                     /*    iterations (A_pp; S~ uses smoother_S)               */
   int nu_pre, nu_post, cheb_degree;  /* cheb_degree in 1..4                   */
   double theta;     /* strength threshold                                     */
-  int max_levels, coarse_size;
+  int max_levels;   /* at most this many levels (default 25)                  */
+  int coarse_size;  /* coarsening stops at <= coarse_size rows (default 256); */
+                    /* the coarsest level is solved with its explicit inverse */
+                    /* (Gauss-Jordan with partial pivoting; <= 2048 rows)     */
   unsigned long long seed;  /* PMIS tie-break seed                            */
   int use_graphs;   /* 1: replay each V-cycle / preconditioner as a CUDA graph */
   /* overrides for the Schur hierarchy (-1 or 0: same as above) */

@@ -427,7 +427,7 @@ def l1_diag(A):
     return d
 
 
-def setup(A, theta=0.25, seed=0, coarse_size=64, max_levels=25,
+def setup(A, theta=0.25, seed=0, coarse_size=256, max_levels=25,
           max_coarse_dense=4096, smoother="l1jacobi", cheb_degree=2,
           interp="ext+i", pmax=4):
     """Build the hierarchy. Coarsening stops when the level has at most

@@ -35,7 +35,7 @@ struct AmgOpts {
   int smoother = 0;      // 0 l1-Jacobi, 1 Chebyshev
   int nu_pre = 3, nu_post = 3, cheb_degree = 2;
   double theta = 0.25;
-  int max_levels = 25, coarse_size = 64, max_coarse_dense = 2048;
+  int max_levels = 25, coarse_size = 256, max_coarse_dense = 2048;
   unsigned long long seed = 0;
   int precision = 0;     // 0 FP64, 1 FP32 hierarchy, 2 FP32 + BF16 P and R
   int max_pmis_rounds = 64;
@@ -61,6 +61,11 @@ struct TailLevel {
 constexpr int kMaxTailLevels = 32;
 // cluster size the tail kernel launches with (16 or 8), 0 if unavailable
 int tail_cluster_size();
+// Explicit inverse of the dense coarsest operator (n x n row-major) by one
+// thread-block cluster; *err = 1 if it is singular. Returns false (nothing
+// launched) when the matrix does not fit the cluster's shared memory or
+// clusters cannot be launched.
+bool coarse_inverse_cluster(int n, const double* A, double* inv, int* err, cudaStream_t s);
 template <class TV>
 void launch_vcycle_tail(const TailLevel* desc, int first, int last, const double* cinv, int nc,
                         int nu_pre, int nu_post, int cluster, cudaStream_t s);

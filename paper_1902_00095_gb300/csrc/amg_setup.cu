@@ -1740,7 +1740,11 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
   k_to_dense<<<grid_for(nc), kBlock, 0, s>>>(nc, cl.A.rowptr, cl.A.col, cl.A.val, coarse_dense);
   TP_LAUNCH_CHECK();
   TP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  k_gauss_jordan<<<1, 1024, 0, s>>>(nc, coarse_dense, coarse_inv, err);
+  // one cluster holds the matrix in shared memory; the single-CTA kernel
+  // (matrix in global memory) covers sizes beyond the cluster's capacity
+  if (!coarse_inverse_cluster(nc, coarse_dense, coarse_inv, err, s)) {
+    k_gauss_jordan<<<1, 1024, 0, s>>>(nc, coarse_dense, coarse_inv, err);
+  }
   TP_LAUNCH_CHECK();
   if (read_int(err, s) != 0) fail(TP_SETUP_FAILED, "AMG: singular coarsest operator");
   if (allocate) {

@@ -195,7 +195,7 @@ void tp_default_opts(tp_precond_opts* o) {
   o->cheb_degree = 2;
   o->theta = 0.25;
   o->max_levels = 25;
-  o->coarse_size = 64;
+  o->coarse_size = 256;
   o->seed = 0;
   o->use_graphs = 1;
   o->interp_S = 0;

@@ -127,7 +127,7 @@ def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax
     seed = 12345
     iname = "ext+i" if interp == 1 else "classical"
     oh = oamg.setup(A, theta=0.25, seed=seed, coarse_size=64, interp=iname, pmax=pmax)
-    g = thermo.AMG(A[0], A[1], A[2], interp=interp, seed=seed, pmax=pmax)
+    g = thermo.AMG(A[0], A[1], A[2], interp=interp, seed=seed, pmax=pmax, coarse_size=64)
     _compare_hierarchies(g, oh, iname)
     # one V-cycle from zero: same linear operator up to rounding
     rng = np.random.default_rng(3)
@@ -184,7 +184,7 @@ def test_cluster_tail_matches_per_kernel_vcycle(name, which):
     b = np.random.default_rng(9).standard_normal(A[0].size - 1)
     for precision, tol in ((0, 1e-12), (1, 1e-5), (2, 1e-5)):
         for nu in (1, 2):
-            kw = dict(interp=interp, precision=precision, nu_pre=nu, nu_post=nu)
+            kw = dict(interp=interp, precision=precision, nu_pre=nu, nu_post=nu, coarse_size=64)
             g0 = thermo.AMG(*A, tail_rows=0, **kw)
             g1 = thermo.AMG(*A, tail_rows=12288, **kw)
             n, _ = g1.info()
@@ -262,21 +262,30 @@ def _oracle_scaled_residual(osys, obp, obT, xp, xT):
     return np.linalg.norm(r) / np.linalg.norm(b)
 
 
+# relative residual at which the solution error is checked: 1e-8, except on
+# the 37 x 1 x 3 slab, whose scaled matrix has condition number 1.7e11, so
+# a residual of 1e-8 bounds its error only by ~1e3 (one FGMRES iteration
+# with its one-level hierarchies stops at 5e-9 with error 3e-4, in the
+# oracle as on the GPU); its error is checked at 1e-10
+ERROR_RTOL = {"thin": 1e-10}
+
+
 @pytest.mark.parametrize("name", ["iid16", "ragged", "thin", "oil"])
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_matches_direct_solution(name, precision):
     prob, p, T = problem(name)
     s, _, (osys, obp, obT, oS) = assemble_both(prob, p, T)
     s.build(precision=precision)
-    xp, xT, info = s.solve(rtol=1e-8, maxit=400)
+    rtol = ERROR_RTOL.get(name, 1e-8)
+    xp, xT, info = s.solve(rtol=rtol, maxit=400)
     assert info["status"] == 0, info
     rp, rT = okry.direct_solution(osys, obp, obT)
     full, ep, eT = _errors(xp, xT, rp, rT)
     assert full <= 1e-6 and ep <= 1e-6, (full, ep, eT)
     # the residual reported by the GPU and the one the oracle's own matrix
     # gives for the GPU solution both meet the tolerance
-    assert info["rel_res"] <= 1e-8
-    assert _oracle_scaled_residual(osys, obp, obT, xp, xT) <= 1.5e-8
+    assert info["rel_res"] <= rtol
+    assert _oracle_scaled_residual(osys, obp, obT, xp, xT) <= 1.5 * rtol
 
 
 def test_tight_solve_resolves_both_blocks():
