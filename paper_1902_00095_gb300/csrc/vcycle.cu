@@ -42,16 +42,24 @@ __device__ __forceinline__ T group_sum(T v) {
 }
 
 // The part of one CSR row a lane owns (entries rp[row] + lane + k LANES):
-// the column indices and values of its first kRowPre entries are held in
+// the column indices and values of its first K entries are held in
 // registers (loaded before the dependency wait), the rest are read in the
-// dot itself. Summation order is the plain lane-strided order.
-constexpr int kRowPre = 4;
+// dot itself. Summation order is the plain lane-strided order. K is 4 for
+// 8-byte values and 8 for narrower ones (about the same registers; measured
+// on the 64x64x32 and 128x128x64 hierarchies: FP64 sweeps slower with 8,
+// FP32 ones faster).
+
+template <class TP>
+constexpr int row_pre() {
+  return sizeof(TP) >= 8 ? 4 : 8;
+}
 
 template <int LANES, class TP>
 struct RowPre {
+  static constexpr int K = row_pre<TP>();
   int e = 0, e1 = 0;
-  int c[kRowPre];
-  TP v[kRowPre];
+  int c[K];
+  TP v[K];
 
   __device__ __forceinline__ void load(const int* __restrict__ rp, const int* __restrict__ col,
                                        const TP* __restrict__ val, int row, bool valid,
@@ -61,7 +69,7 @@ struct RowPre {
       e1 = rp[row + 1];
     }
 #pragma unroll
-    for (int k = 0; k < kRowPre; ++k) {
+    for (int k = 0; k < K; ++k) {
       const int q = e + k * LANES;
       c[k] = 0;
       v[k] = TP{};
@@ -78,9 +86,9 @@ struct RowPre {
                                     const TX* __restrict__ x) const {
     TV acc = TV(0);
 #pragma unroll
-    for (int k = 0; k < kRowPre; ++k)
+    for (int k = 0; k < K; ++k)
       if (e + k * LANES < e1) acc += widen<TV, TP>(v[k]) * (TV)x[c[k]];
-    for (int q = e + kRowPre * LANES; q < e1; q += LANES)
+    for (int q = e + K * LANES; q < e1; q += LANES)
       acc += widen<TV, TP>(val[q]) * (TV)x[col[q]];
     return group_sum<LANES>(acc);
   }
@@ -143,18 +151,19 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
   a.load(rp, col, val, row, valid, lane);
   TV d = TV(0);
   if (valid && lane == 0) d = dinv[row];
-  TV dj[kRowPre];
+  constexpr int K = RowPre<LANES, TV>::K;
+  TV dj[K];
 #pragma unroll
-  for (int k = 0; k < kRowPre; ++k) dj[k] = (a.e + k * LANES < a.e1) ? dinv[a.c[k]] : TV(0);
+  for (int k = 0; k < K; ++k) dj[k] = (a.e + k * LANES < a.e1) ? dinv[a.c[k]] : TV(0);
   pdl_wait();
   pdl_trigger();
   TV bi = TV(0);
   if (valid && lane == 0) bi = (TV)b[row];
   TV acc = TV(0);
 #pragma unroll
-  for (int k = 0; k < kRowPre; ++k)
+  for (int k = 0; k < K; ++k)
     if (a.e + k * LANES < a.e1) acc += a.v[k] * (dj[k] * (TV)b[a.c[k]]);
-  for (int q = a.e + kRowPre * LANES; q < a.e1; q += LANES) {
+  for (int q = a.e + K * LANES; q < a.e1; q += LANES) {
     const int j = col[q];
     acc += val[q] * (dinv[j] * (TV)b[j]);
   }
@@ -323,9 +332,10 @@ __global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __rest
                          TO* __restrict__ x) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  double a[kRowPre];
+  constexpr int kPre = 4;  // columns j = lane + 32 k, k < kPre, held before the wait
+  double a[kPre];
 #pragma unroll
-  for (int k = 0; k < kRowPre; ++k) {
+  for (int k = 0; k < kPre; ++k) {
     const int j = lane + 32 * k;
     a[k] = (row < n && j < n) ? inv[(long long)row * n + j] : 0.0;
   }
@@ -334,9 +344,9 @@ __global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __rest
   if (row >= n) return;
   double acc = 0.0;
 #pragma unroll
-  for (int k = 0; k < kRowPre; ++k)
+  for (int k = 0; k < kPre; ++k)
     if (lane + 32 * k < n) acc += a[k] * (double)b[lane + 32 * k];
-  for (int j = lane + 32 * kRowPre; j < n; j += 32) acc += inv[(long long)row * n + j] * (double)b[j];
+  for (int j = lane + 32 * kPre; j < n; j += 32) acc += inv[(long long)row * n + j] * (double)b[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) x[row] = (TO)acc;
