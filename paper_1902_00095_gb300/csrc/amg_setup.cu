@@ -56,6 +56,25 @@ __global__ void k_transpose_pos(int n, const int* __restrict__ rp, const int* __
   }
 }
 
+// the same with one warp per row (lanes over the row's entries): for the
+// long rows of coarse Galerkin levels
+__global__ void k_transpose_pos_warp(int n, const int* __restrict__ rp,
+                                     const int* __restrict__ col, int* __restrict__ tpos,
+                                     int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (i >= n) return;
+  for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+    int k = col[e];
+    int p = (k >= 0 && k < n) ? find_in(col, rp[k], rp[k + 1], i) : -1;
+    tpos[e] = p;
+    if (p < 0) atomicOr(err, 2);
+  }
+}
+
+// mean row length from which row-wise setup kernels take one warp per row
+constexpr int kWarpRowMean = 16;
+
 // strong[e] = 1 iff col != i and -a_e >= theta * max_{k != i}(-a_ik) > 0
 __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ col,
                            const double* __restrict__ val, double theta,
@@ -137,6 +156,111 @@ __global__ void k_pmis_update(int n, const int* __restrict__ rp, const int* __re
   atomicAdd(undecided, 1);
 }
 
+// One-warp-per-row forms of the strength and PMIS kernels above, for levels
+// whose mean row length is at least kWarpRowMean: the lanes take the row's
+// entries, the row's decision is a warp reduction (a maximum, a count, an
+// any), so the results are the same bit for bit.
+__device__ __forceinline__ int warp_row(int& lane) {
+  lane = threadIdx.x & 31;
+  return (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+}
+
+__global__ void k_strength_warp(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                const double* __restrict__ val, double theta,
+                                unsigned char* __restrict__ strong) {
+  int lane;
+  const int i = warp_row(lane);
+  if (i >= n) return;
+  const int r0 = rp[i], r1 = rp[i + 1];
+  double mx = -INFINITY;
+  for (int e = r0 + lane; e < r1; e += 32)
+    if (col[e] != i && -val[e] > mx) mx = -val[e];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, mx, o);
+    if (t > mx) mx = t;
+  }
+  if (!(mx > 0.0)) {
+    for (int e = r0 + lane; e < r1; e += 32) strong[e] = 0;
+    return;
+  }
+  const double thr = __dmul_rn(theta, mx);
+  for (int e = r0 + lane; e < r1; e += 32)
+    strong[e] = (col[e] != i && -val[e] >= thr) ? 1 : 0;
+}
+
+__global__ void k_pmis_init_warp(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const unsigned char* __restrict__ strong,
+                                 const int* __restrict__ tpos, int* __restrict__ lam,
+                                 signed char* __restrict__ state) {
+  int lane;
+  const int i = warp_row(lane);
+  if (i >= n) return;
+  int l = 0;
+  for (int e = rp[i] + lane; e < rp[i + 1]; e += 32)
+    if (col[e] != i && strong[tpos[e]]) ++l;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if (lane == 0) {
+    lam[i] = l;
+    state[i] = (l == 0) ? kF : kU;
+  }
+}
+
+__global__ void k_pmis_select_warp(int n, const int* __restrict__ rp,
+                                   const int* __restrict__ col,
+                                   const unsigned char* __restrict__ strong,
+                                   const int* __restrict__ tpos, const int* __restrict__ lam,
+                                   const signed char* __restrict__ state,
+                                   unsigned long long seed, unsigned char* __restrict__ newc) {
+  int lane;
+  const int i = warp_row(lane);
+  if (i >= n) return;
+  if (state[i] != kU) {
+    if (lane == 0) newc[i] = 0;
+    return;
+  }
+  const int li = lam[i];
+  const unsigned int hi = pmis_hash(seed, i);
+  bool bigger = false;
+  for (int e = rp[i] + lane; e < rp[i + 1] && !bigger; e += 32) {
+    const int k = col[e];
+    if (k == i || state[k] != kU) continue;
+    if (!(strong[e] || strong[tpos[e]])) continue;
+    const int lk = lam[k];
+    const unsigned int hk = pmis_hash(seed, k);
+    bigger = (lk > li) || (lk == li && (hk > hi || (hk == hi && k > i)));
+  }
+  const bool any = __any_sync(0xffffffffu, bigger);
+  if (lane == 0) newc[i] = any ? 0 : 1;
+}
+
+__global__ void k_pmis_update_warp(int n, const int* __restrict__ rp,
+                                   const int* __restrict__ col,
+                                   const unsigned char* __restrict__ strong,
+                                   signed char* __restrict__ state,
+                                   const unsigned char* __restrict__ newc,
+                                   int* __restrict__ undecided) {
+  int lane;
+  const int i = warp_row(lane);
+  if (i >= n) return;
+  if (newc[i]) {
+    if (lane == 0) state[i] = kC;
+    return;
+  }
+  if (state[i] != kU) return;
+  bool c = false;
+  for (int e = rp[i] + lane; e < rp[i + 1] && !c; e += 32) {
+    const int k = col[e];
+    c = strong[e] && (newc[k] || state[k] == kC);
+  }
+  const bool any = __any_sync(0xffffffffu, c);
+  if (lane == 0) {
+    if (any) state[i] = kF;
+    else atomicAdd(undecided, 1);
+  }
+}
+
 __global__ void k_cflag(int n, const signed char* __restrict__ state, int* __restrict__ flag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) flag[i] = state[i] == kC ? 1 : 0;
@@ -167,7 +291,7 @@ __global__ void k_classical_count(int n, const int* __restrict__ rp, const int* 
 }
 
 // rows longer than kClsShort are filled by a warp (k_classical_fill_warp)
-constexpr int kClsShort = 24;
+constexpr int kClsShort = 8;
 constexpr int kClsWarps = 4;
 
 __global__ void k_classical_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
@@ -765,22 +889,41 @@ __global__ void k_fill_transpose(int n, const int* __restrict__ rp, const int* _
   }
 }
 
-// sort every row by column (insertion sort; rows are short)
-__global__ void k_sort_rows(int n, const int* __restrict__ rp, int* __restrict__ col,
-                            double* __restrict__ val) {
+// Rows of [rp] with distinct columns, reordered by column from (col, val)
+// into (ocol, oval): each entry goes to its rank, the number of entries of
+// its row with a smaller column. One warp per row of more than 32 entries
+// (the lanes rank the row's entries in parallel), one thread per shorter
+// row.
+__global__ void k_rank_rows(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, int* __restrict__ ocol,
+                            double* __restrict__ oval) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  for (int e = rp[i] + 1; e < rp[i + 1]; ++e) {
-    int c = col[e];
-    double v = val[e];
-    int q = e - 1;
-    while (q >= rp[i] && col[q] > c) {
-      col[q + 1] = col[q];
-      val[q + 1] = val[q];
-      --q;
-    }
-    col[q + 1] = c;
-    val[q + 1] = v;
+  const int r0 = rp[i], r1 = rp[i + 1];
+  if (r1 - r0 > 32) return;  // k_rank_rows_warp
+  for (int e = r0; e < r1; ++e) {
+    const int c = col[e];
+    int rank = 0;
+    for (int f = r0; f < r1; ++f) rank += col[f] < c;
+    ocol[r0 + rank] = c;
+    oval[r0 + rank] = val[e];
+  }
+}
+
+__global__ void k_rank_rows_warp(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const double* __restrict__ val, int* __restrict__ ocol,
+                                 double* __restrict__ oval) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (i >= n) return;
+  const int r0 = rp[i], r1 = rp[i + 1];
+  if (r1 - r0 <= 32) return;  // k_rank_rows
+  for (int e = r0 + lane; e < r1; e += 32) {
+    const int c = col[e];
+    int rank = 0;
+    for (int f = r0; f < r1; ++f) rank += col[f] < c;
+    ocol[r0 + rank] = c;
+    oval[r0 + rank] = val[e];
   }
 }
 
@@ -1446,10 +1589,16 @@ DevCSR transpose(const DevCSR& P, Pool& pool, Pool& scratch, cudaStream_t s) {
   scan_exclusive(cnt, R.rowptr, R.n, scratch, s);
   R.col = pool.alloc<int>(R.nnz + 1);
   R.val = pool.alloc<double>(R.nnz + 1);
+  // atomically placed (unordered) entries, then each row ranked by column
+  int* ucol = scratch.alloc<int>(R.nnz + 1);
+  double* uval = scratch.alloc<double>(R.nnz + 1);
   k_fill_transpose<<<grid_for(P.n), kBlock, 0, s>>>(P.n, P.rowptr, P.col, P.val, R.rowptr,
-                                                    cursor, R.col, R.val);
+                                                    cursor, ucol, uval);
   TP_LAUNCH_CHECK();
-  k_sort_rows<<<grid_for(R.n), kBlock, 0, s>>>(R.n, R.rowptr, R.col, R.val);
+  k_rank_rows<<<grid_for(R.n), kBlock, 0, s>>>(R.n, R.rowptr, ucol, uval, R.col, R.val);
+  TP_LAUNCH_CHECK();
+  k_rank_rows_warp<<<grid_for((long long)R.n * 32), kBlock, 0, s>>>(R.n, R.rowptr, ucol, uval,
+                                                                    R.col, R.val);
   TP_LAUNCH_CHECK();
   return R;
 }
@@ -1468,7 +1617,11 @@ void csr_product_numeric(const DevCSR& A, const DevCSR& B, const DevCSR& C, cuda
 }
 
 void csr_transpose_positions(const DevCSR& A, int* tpos, int* err, cudaStream_t s) {
-  k_transpose_pos<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, tpos, err);
+  if (A.n > 0 && A.nnz >= (long long)kWarpRowMean * A.n)
+    k_transpose_pos_warp<<<grid_for((long long)A.n * 32), kBlock, 0, s>>>(A.n, A.rowptr, A.col,
+                                                                         tpos, err);
+  else
+    k_transpose_pos<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, tpos, err);
   TP_LAUNCH_CHECK();
 }
 
@@ -1519,31 +1672,54 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
     if (read_int(err, s) != 0) fail(TP_EINVAL, "AMG: a row has no diagonal entry");
     if (n <= opts.coarse_size || (int)L.size() >= opts.max_levels) break;
     cur.tpos = pool.alloc<int>(A.nnz);
-    k_transpose_pos<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.tpos, err);
-    TP_LAUNCH_CHECK();
+    csr_transpose_positions(A, cur.tpos, err, s);
     if (read_int(err, s) != 0) fail(TP_EINVAL, "AMG: pattern is not structurally symmetric");
+    // long rows (coarse Galerkin levels): one warp per row
+    const bool wrow = A.nnz >= (long long)kWarpRowMean * n;
+    const int gw = grid_for((long long)n * 32);
     cur.strong = pool.alloc<unsigned char>(A.nnz);
-    k_strength<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, A.val, opts.theta, cur.strong);
+    if (wrow)
+      k_strength_warp<<<gw, kBlock, 0, s>>>(n, A.rowptr, A.col, A.val, opts.theta, cur.strong);
+    else
+      k_strength<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, A.val, opts.theta,
+                                                cur.strong);
     TP_LAUNCH_CHECK();
     // PMIS
     int* lam = scratch.alloc<int>(n);
     unsigned char* newc = scratch.alloc<unsigned char>(n);
     int* undecided = scratch.alloc<int>(1);
     cur.cf = pool.alloc<signed char>(n);
-    k_pmis_init<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos, lam,
-                                               cur.cf);
+    if (wrow)
+      k_pmis_init_warp<<<gw, kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos, lam,
+                                             cur.cf);
+    else
+      k_pmis_init<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos, lam,
+                                                 cur.cf);
     TP_LAUNCH_CHECK();
+    // rounds are enqueued in pairs before the host reads the count of
+    // undecided points: a round after the last is a no-op (no point is
+    // undecided, so nothing is selected or changed)
     int rounds = 0;
     while (true) {
       if (rounds >= opts.max_pmis_rounds) fail(TP_SETUP_FAILED, "PMIS round cap reached");
-      ++rounds;
-      k_pmis_select<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos,
-                                                   lam, cur.cf, opts.seed, newc);
-      TP_LAUNCH_CHECK();
-      TP_CUDA_TRY(cudaMemsetAsync(undecided, 0, sizeof(int), s));
-      k_pmis_update<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf, newc,
+      for (int r = 0; r < 2; ++r) {
+        ++rounds;
+        if (wrow)
+          k_pmis_select_warp<<<gw, kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos, lam,
+                                                   cur.cf, opts.seed, newc);
+        else
+          k_pmis_select<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos,
+                                                       lam, cur.cf, opts.seed, newc);
+        TP_LAUNCH_CHECK();
+        TP_CUDA_TRY(cudaMemsetAsync(undecided, 0, sizeof(int), s));
+        if (wrow)
+          k_pmis_update_warp<<<gw, kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf, newc,
                                                    undecided);
-      TP_LAUNCH_CHECK();
+        else
+          k_pmis_update<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.cf,
+                                                       newc, undecided);
+        TP_LAUNCH_CHECK();
+      }
       if (read_int(undecided, s) == 0) break;
     }
     cur.pmis_rounds = rounds;
