@@ -692,7 +692,7 @@ __device__ void extpi_fill_row_serial(int i, const int* __restrict__ rp, const i
 // ascending. Rows longer than kFillMaxE use the serial form.
 constexpr int kFillMaxE = 256;
 constexpr int kFillWarps = 4;
-constexpr int kFillShort = 16;  // rows up to this length: one thread per row
+constexpr int kFillShort = 8;  // rows up to this length: one thread per row
 
 __global__ void k_extpi_fill_short(int n, const int* __restrict__ rp, const int* __restrict__ col,
                                    const double* __restrict__ val, const int* __restrict__ dpos,
@@ -928,17 +928,14 @@ __global__ void k_rank_rows_warp(int n, const int* __restrict__ rp, const int* _
 }
 
 // ------------------------------------------------------------- SpGEMM C = A B
+// Upper bound (product count) of every row of C = A B; rows too long for
+// the thread-per-row kernel are listed for the warp kernel (kSpShort < ub <=
+// kSpCap) or the block kernel (ub > kSpCap), so those visit only their rows.
+// The list order is not deterministic; each row's result is.
 __global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
-                            const int* __restrict__ Brp, int* __restrict__ ub) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int u = 0;
-  for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
-    int k = Acol[e];
-    u += Brp[k + 1] - Brp[k];
-  }
-  ub[i] = u;
-}
+                            const int* __restrict__ Brp, int* __restrict__ ub,
+                            int* __restrict__ wlist, int* __restrict__ blist,
+                            int* __restrict__ counts);
 
 // Row i of C: products a_ik * b_kj in ascending k (row i of A) then ascending
 // j (row k of B); each column's sum starts at 0.0 and adds them in that
@@ -1047,6 +1044,22 @@ __global__ void __launch_bounds__(32 * kDenseWarps) k_spgemm_dense(
 // products fall back to the serial insertion of k_spgemm_rows (lane 0).
 constexpr int kSpCap = 1024;
 constexpr int kSpWarps = 2;  // 2 x 16 KiB static shared memory per block
+
+__global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
+                            const int* __restrict__ Brp, int* __restrict__ ub,
+                            int* __restrict__ wlist, int* __restrict__ blist,
+                            int* __restrict__ counts) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int u = 0;
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
+    int k = Acol[e];
+    u += Brp[k + 1] - Brp[k];
+  }
+  ub[i] = u;
+  if (u > kSpCap) blist[atomicAdd(&counts[1], 1)] = i;
+  else if (u > kSpShort) wlist[atomicAdd(&counts[0], 1)] = i;
+}
 
 __device__ void spgemm_row_serial(int i, const int* __restrict__ Arp, const int* __restrict__ Acol,
                                   const double* __restrict__ Aval, const int* __restrict__ Brp,
@@ -1169,13 +1182,15 @@ __global__ void __launch_bounds__(32 * kSpWarps) k_spgemm_rows_warp(
     int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
     const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
     const double* __restrict__ Bval, const int* __restrict__ off, const int* __restrict__ ub,
+    const int* __restrict__ wlist, const int* __restrict__ counts,
     int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
   __shared__ unsigned long long s_key[kSpWarps][kSpCap];
   __shared__ double s_val[kSpWarps][kSpCap];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = blockIdx.x * kSpWarps + w; i < n; i += gridDim.x * kSpWarps) {
+  const int count = counts[0];
+  for (int t = blockIdx.x * kSpWarps + w; t < count; t += gridDim.x * kSpWarps) {
+    const int i = wlist[t];
     const int ex = ub[i];
-    if (ex <= kSpShort || ex > kSpCap) continue;
     spgemm_row_warp(i, ex, lane, Arp, Acol, Aval, Brp, Bcol, Bval, s_key[w], s_val[w],
                     ccol + off[i], cval + off[i], cnt);
     __syncwarp();
@@ -1193,14 +1208,16 @@ __global__ void __launch_bounds__(kSpBigThreads) k_spgemm_rows_big(
     int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
     const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
     const double* __restrict__ Bval, const int* __restrict__ off, const int* __restrict__ ub,
+    const int* __restrict__ blist, const int* __restrict__ counts,
     int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
   extern __shared__ unsigned long long s_big[];
   unsigned long long* key = s_big;
   double* val = reinterpret_cast<double*>(s_big + kSpBig);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+  const int count = counts[1];
+  for (int t = blockIdx.x; t < count; t += gridDim.x) {
+    const int i = blist[t];
     const int ex = ub[i];  // uniform over the block
-    if (ex <= kSpCap) continue;
     int* cc = ccol + off[i];
     double* cv = cval + off[i];
     if (ex > kSpBig) {
@@ -1512,7 +1529,12 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   const int n = A.n;
   int* ub = scratch.alloc<int>(n + 1);
   int* off = scratch.alloc<int>(n + 1);
-  k_spgemm_ub<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, B.rowptr, ub);
+  int* wlist = scratch.alloc<int>(n + 1);
+  int* blist = scratch.alloc<int>(n + 1);
+  int* counts = scratch.alloc<int>(2);
+  TP_CUDA_TRY(cudaMemsetAsync(counts, 0, 2 * sizeof(int), s));
+  k_spgemm_ub<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, B.rowptr, ub, wlist, blist,
+                                             counts);
   TP_LAUNCH_CHECK();
   long long tot = scan_exclusive(ub, off, n, scratch, s);
   int* ccol = scratch.alloc<int>(tot + 1);
@@ -1548,7 +1570,8 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
     long long blocks = (n + kSpWarps - 1) / kSpWarps;
     if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
     k_spgemm_rows_warp<<<(int)blocks, 32 * kSpWarps, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr,
-                                                             B.col, B.val, off, ub, ccol, cval, cnt);
+                                                             B.col, B.val, off, ub, wlist, counts,
+                                                             ccol, cval, cnt);
   }
   TP_LAUNCH_CHECK();
   static const bool big_attr = []() {
@@ -1558,7 +1581,7 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   }();
   (void)big_attr;
   k_spgemm_rows_big<<<n < num_sms ? n : num_sms, kSpBigThreads, kSpBigSmem, s>>>(
-      n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, ccol, cval, cnt);
+      n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, blist, counts, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
   }
   DevCSR C;
