@@ -16,7 +16,7 @@ namespace tp {
 
 namespace {
 
-constexpr int kDotV = 8;  // vectors per multi-dot pass
+constexpr int kDotV = 16;  // vectors per multi-dot launch
 constexpr int kEstSlot = 16;  // pinned-buffer offset of the two convergence-estimate slots
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -51,6 +51,8 @@ __device__ __forceinline__ void block_sum_store(double v, double* out) {
 __global__ void k_precond_in(int N, const double* __restrict__ vp, const double* __restrict__ vT,
                              const double* __restrict__ scales, double* __restrict__ bp_s,
                              double* __restrict__ bT_s, double* __restrict__ hin) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double a = vp[i] / scales[0];
@@ -63,6 +65,8 @@ __global__ void k_precond_in(int N, const double* __restrict__ vp, const double*
 __global__ void k_rhs_minus(int N, const int* __restrict__ rp, const int* __restrict__ col,
                             const double* __restrict__ val, const double* __restrict__ b,
                             const double* __restrict__ x, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double bi = b[i];  // issued before the gathers
@@ -82,11 +86,34 @@ __global__ void __launch_bounds__(256) k_block_spmv(int N, const int* __restrict
                                                     double* __restrict__ wp,
                                                     double* __restrict__ wT,
                                                     const double* __restrict__ scales) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // programmatic dependent launch: the row's pattern (the matrix does not
+  // change during the solve) is loaded before the wait; its 2x2 blocks are
+  // not (held in registers they cost occupancy on large grids)
+  constexpr int kPre = 7;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int e0 = 0, e1 = 0;
+  int c[kPre];
+  if (i < N) {
+    e0 = rp[i];
+    e1 = rp[i + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) c[k] = (e0 + k < e1) ? col[e0 + k] : 0;
+  pdl_wait();
+  pdl_trigger();
   if (i >= N) return;
   const double zpi = zp[i], zTi = zT[i];  // issued before the gathers
   double ap = 0.0, aT = 0.0;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) {
+    if (e0 + k < e1) {
+      const double4_32a b = bval[e0 + k];
+      const double xp = zp[c[k]], xT = zT[c[k]];
+      ap += b.x * xp + b.y * xT;
+      aT += b.z * xp + b.w * xT;
+    }
+  }
+  for (int e = e0 + kPre; e < e1; ++e) {
     const int j = col[e];
     const double4_32a b = bval[e];
     const double xp = zp[j], xT = zT[j];
@@ -103,11 +130,17 @@ __global__ void __launch_bounds__(256) k_block_spmv(int N, const int* __restrict
 }
 
 // ------------------------------------------------------------ Gram-Schmidt
+// partial dot products V_k . w, k0 <= k < k0 + nv (nv <= NV), of this
+// block's element chunk: per-thread sums, then warp sums, then the block's
+// warps in order (one barrier)
 template <int NV>
 __global__ void __launch_bounds__(256) k_mdot(long long n2, const double* __restrict__ V,
                                               long long stride, int k0, int nv,
                                               const double* __restrict__ w,
                                               double* __restrict__ partials) {
+  __shared__ double sh[8][NV];
+  pdl_wait();
+  pdl_trigger();
   long long lo, hi;
   chunk_of(n2, lo, hi);
   double acc[NV];
@@ -119,15 +152,27 @@ __global__ void __launch_bounds__(256) k_mdot(long long n2, const double* __rest
     for (int q = 0; q < NV; ++q)
       if (q < nv) acc[q] += wi * V[(long long)(k0 + q) * stride + i];
   }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    if (q < nv) block_sum_store(acc[q], &partials[(long long)(k0 + q) * gridDim.x + blockIdx.x]);
+    if (q < nv) {
+      const double t = warp_sum(acc[q]);
+      if (lane == 0) sh[wid][q] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += sh[u][threadIdx.x];
+    partials[(long long)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
   }
 }
 
 // out[k] = sum_b partials[k * B + b], k < count (fixed order)
 __global__ void k_reduce_rows(int count, int B, const double* __restrict__ partials,
                               double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   const int k = blockIdx.x;
   if (k >= count) return;
   double v = 0.0;
@@ -144,6 +189,8 @@ __global__ void __launch_bounds__(256) k_orth_update(long long n2, const double*
                                                      const double* __restrict__ h,
                                                      double* __restrict__ w,
                                                      double* __restrict__ norm_partials) {
+  pdl_wait();
+  pdl_trigger();
   const long long step = (long long)gridDim.x * blockDim.x;
   double nrm = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += step) {
@@ -175,6 +222,8 @@ __global__ void __launch_bounds__(256) k_arnoldi(int j, int ldh, double* __restr
                                                  double* __restrict__ hn_out,
                                                  double* __restrict__ est) {
   __shared__ double tot;
+  pdl_wait();
+  pdl_trigger();
   double part = 0.0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) part += npart[b];
   block_sum_store(part, &tot);
@@ -208,6 +257,8 @@ __global__ void __launch_bounds__(256) k_arnoldi(int j, int ldh, double* __restr
 
 __global__ void k_normalize(long long n2, const double* __restrict__ w,
                             const double* __restrict__ hn, double* __restrict__ v) {
+  pdl_wait();
+  pdl_trigger();
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n2) v[i] = w[i] / hn[0];
 }
@@ -330,11 +381,9 @@ void mdot_all(long long n2, const double* V, long long stride, int count, const 
               double* partials, int B, double* out, cudaStream_t s) {
   for (int k0 = 0; k0 < count; k0 += kDotV) {
     int nv = count - k0 < kDotV ? count - k0 : kDotV;
-    k_mdot<kDotV><<<B, 256, 0, s>>>(n2, V, stride, k0, nv, w, partials);
-    TP_LAUNCH_CHECK();
+    launch_pdl(k_mdot<kDotV>, B, 256, s, n2, V, stride, k0, nv, w, partials);
   }
-  k_reduce_rows<<<count, 256, 0, s>>>(count, B, partials, out);
-  TP_LAUNCH_CHECK();
+  launch_pdl(k_reduce_rows, count, 256, s, count, B, partials, out);
 }
 
 // grid of k_orth_update: enough blocks for 8 resident per SM, at most one
@@ -566,14 +615,12 @@ void precond_record(tp_ctx* c, cudaStream_t s) {
   Hierarchy& hs = *c->hS;
   const int N = c->N;
   hp.vcycle(s);  // step 1: x_p = V_pp(b_p)
-  k_rhs_minus<<<grid_for(N), kBlock, 0, s>>>(N, c->rowptr, c->col, c->ATp, c->bT_s, hp.out,
-                                             hs.in);  // step 2
-  TP_LAUNCH_CHECK();
+  launch_pdl(k_rhs_minus, grid_for(N), kBlock, s, N, c->rowptr, c->col, c->ATp, c->bT_s, hp.out,
+             hs.in);  // step 2
   hs.vcycle(s);  // step 3: d_T = V_S(bt_T)
   if (c->opts.variant == 0) {
-    k_rhs_minus<<<grid_for(N), kBlock, 0, s>>>(N, c->rowptr, c->col, c->ApT, c->bp_s, hs.out,
-                                               hp.in);  // step 4
-    TP_LAUNCH_CHECK();
+    launch_pdl(k_rhs_minus, grid_for(N), kBlock, s, N, c->rowptr, c->col, c->ApT, c->bp_s,
+               hs.out, hp.in);  // step 4
     hp.vcycle(s);  // step 5: d_p = V_pp(bt_p)
   }
 }
@@ -581,8 +628,8 @@ void precond_record(tp_ctx* c, cudaStream_t s) {
 void precond_apply(tp_ctx* c, const double* vp, const double* vT, const double* scales,
                    cudaStream_t s, int set) {
   const int N = c->N;
-  k_precond_in<<<grid_for(N), kBlock, 0, s>>>(N, vp, vT, scales, c->bp_s, c->bT_s, c->hpp->in);
-  TP_LAUNCH_CHECK();
+  launch_pdl(k_precond_in, grid_for(N), kBlock, s, N, vp, vT, scales, c->bp_s, c->bT_s,
+             c->hpp->in);
   if (c->pc_graph) {
     // point the graph's probe event nodes at this iteration's event set
     if (!c->probe_nodes.empty() && c->probe_set != set) {
@@ -671,10 +718,9 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
           c->probe.active = j & 1;
           c->probe.before(s);
         }
-        k_block_spmv<<<grid_for(N), kBlock, 0, s>>>(
-            N, c->rowptr, c->col, reinterpret_cast<const double4_32a*>(c->bval), c->hpp->out,
-            c->hS->out, zj, zj + N, c->w, c->w + N, c->scales);
-        TP_LAUNCH_CHECK();
+        launch_pdl(k_block_spmv, grid_for(N), kBlock, s, N, c->rowptr, c->col,
+                   reinterpret_cast<const double4_32a*>(c->bval), c->hpp->out, c->hS->out, zj,
+                   zj + N, c->w, c->w + N, c->scales);
         if (probe_spmv) {
           c->probe.after(s, 36.0 * c->nnzb + 4.0 * (N + 1) + 48.0 * N);
           c->probe.active = 0;
@@ -684,21 +730,17 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
         double* h2 = c->h2 + (restart + 2);
         const int G = orth_grid(c, n2);
         mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h1, s);
-        k_orth_update<<<G, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h1, c->w, nullptr);
-        TP_LAUNCH_CHECK();
+        launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h1, c->w, (double*)nullptr);
         mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h2, s);
-        k_orth_update<<<G, 256, 0, s>>>(n2, c->Vb, n2, j + 1, h2, c->w, c->oparts);
-        TP_LAUNCH_CHECK();
-        k_arnoldi<<<1, 256, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, c->oparts, G,
-                                    c->hn, c->est);
-        TP_LAUNCH_CHECK();
+        launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h2, c->w, c->oparts);
+        launch_pdl(k_arnoldi, 1, 256, s, j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, c->oparts, G,
+                   c->hn, c->est);
         TP_CUDA_TRY(cudaMemcpyAsync(hp_host + kEstSlot + 4 * (j & 1), c->est, 3 * sizeof(double),
                                     cudaMemcpyDeviceToHost, s));
         TP_CUDA_TRY(cudaEventRecord(c->ev_est[j & 1], s));
         if (j + 1 < restart) {
-          k_normalize<<<grid_for(n2), kBlock, 0, s>>>(n2, c->w, c->hn,
-                                                      c->Vb + (long long)(j + 1) * n2);
-          TP_LAUNCH_CHECK();
+          launch_pdl(k_normalize, grid_for(n2), kBlock, s, n2, c->w, c->hn,
+                     c->Vb + (long long)(j + 1) * n2);
         }
       };
       // returns true when the cycle stops after column j (m set)

@@ -366,7 +366,6 @@ void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB*
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
   }
-  TP_LAUNCH_CHECK();
 }
 
 template <class TV, class TB>
@@ -382,7 +381,6 @@ void jacobi2z(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const T
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
   }
-  TP_LAUNCH_CHECK();
 }
 
 template <class TV, class TB>
@@ -397,7 +395,6 @@ void residual(int lanes, const DevCSR& A, const TV* val, const TB* b, const TV* 
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
   }
-  TP_LAUNCH_CHECK();
 }
 
 template <class TP, class TV>
@@ -411,7 +408,6 @@ void spmv(int lanes, const DevCSR& A, const TP* val, const TV* x, TV* y, cudaStr
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
   }
-  TP_LAUNCH_CHECK();
 }
 
 template <class TP, class TV>
@@ -425,7 +421,6 @@ void prolong(int lanes, const DevCSR& P, const TP* val, const TV* e, TV* x, cuda
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
   }
-  TP_LAUNCH_CHECK();
 }
 
 template <class TB, class TO>
