@@ -332,7 +332,7 @@ def run_ours(args, rank, world, local):
             s.set_fields(*hf)
             s.assemble(*hs, prob["dt"])
             s.build(opts)
-            return s.solve(rtol=args.rtol, maxit=args.maxit, out=hx)[2]
+            return s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart, out=hx)[2]
 
         step_host()
         if world > 1:
@@ -357,14 +357,16 @@ def run_ours(args, rank, world, local):
     if not args.no_variant:
         mlp, hist, t_train = train_schur_model(args)
         s.set_schur_model(mlp)
-        vopts = thermo.default_opts(precision=1, schur=1)
+        # the same smoothing and restart as the FP64 run
+        vopts = thermo.default_opts(precision=1, schur=1, nu_pre=args.nu, nu_post=args.nu)
         s.probe_enable(args.probe)
 
         def step_variant():
             s.set_fields(*fields)
             s.assemble(*state, prob["dt"], R_m=Rm, R_e=Re)
             s.build(vopts)
-            return s.solve(rtol=args.rtol, maxit=args.maxit, out=(xp, xT))[2]
+            return s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart,
+                           out=(xp, xT))[2]
 
         for _ in range(args.warmup):
             step_variant()

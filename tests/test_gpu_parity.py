@@ -138,6 +138,30 @@ def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax
     g.close()
 
 
+@pytest.mark.parametrize("which,interp", [("App", 1), ("S", 0)])
+def test_amg_hierarchy_is_bit_exact_at_46080_cells(which, interp):
+    """A 48 x 48 x 20 grid: large enough that the Galerkin products take the
+    sparse SpGEMM paths (coarse side above the dense-row kernel's 2048
+    columns) with rows on the warp list (96 < products <= 1024) and, for
+    A_pp's level 1, on the block list (> 1024 products, 1906 rows), and that
+    the long-row levels take the warp-per-row strength, PMIS and transpose
+    kernels; the hierarchy still agrees with the oracle bit for bit."""
+    prob = make_problem("tiny", shape=(48, 48, 20), seed=6)
+    p, T = perturbed_state(prob, seed=9)
+    prob["p_n"] = prob["p_n"] + 5e4
+    osys, _, _, oS = okry.assemble(prob, p, T)
+    A = osys.App if which == "App" else oS
+    iname = "ext+i" if interp == 1 else "classical"
+    oh = oamg.setup(A, theta=0.25, seed=12345, coarse_size=64, interp=iname, pmax=4)
+    g = thermo.AMG(A[0], A[1], A[2], interp=interp, seed=12345, pmax=4, coarse_size=64)
+    _compare_hierarchies(g, oh, iname)
+    b = np.random.default_rng(4).standard_normal(A[0].size - 1)
+    xg = g.vcycle(b)
+    xo = oamg.vcycle(oh, b, 0, 3, 3)
+    assert np.max(np.abs(xg - xo)) <= 1e-11 * np.max(np.abs(xo))
+    g.close()
+
+
 @pytest.mark.parametrize("name,degree,nu", [("iid16", 2, 1), ("mid", 2, 2), ("ragged", 3, 1),
                                              ("iid16", 1, 2)])
 def test_chebyshev_vcycle_matches_oracle(name, degree, nu):
