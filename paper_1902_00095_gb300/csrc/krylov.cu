@@ -16,7 +16,13 @@ namespace tp {
 
 namespace {
 
-constexpr int kDotV = 16;  // vectors per multi-dot launch
+// vectors per multi-dot launch: 16 while the basis vectors are short (the
+// launches dominate), 4 for long ones (fewer concurrent DRAM streams).
+// FGMRES time measured on 262k / 2.1M / 8.4M unknowns: 16 vectors 34.0 /
+// 49.0 / 4988 ms, 8 vectors 34.5 / 50.2 / 5583 ms, 4 vectors 34.8 / 48.3 /
+// 4827 ms.
+constexpr int kDotWide = 16, kDotNarrow = 4;
+constexpr long long kDotWideMaxN = 1ll << 20;  // vector length up to which 16 are taken
 constexpr int kEstSlot = 16;  // pinned-buffer offset of the two convergence-estimate slots
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -379,9 +385,13 @@ __global__ void k_sqrt_inplace(double* v) {
 
 void mdot_all(long long n2, const double* V, long long stride, int count, const double* w,
               double* partials, int B, double* out, cudaStream_t s) {
-  for (int k0 = 0; k0 < count; k0 += kDotV) {
-    int nv = count - k0 < kDotV ? count - k0 : kDotV;
-    launch_pdl(k_mdot<kDotV>, B, 256, s, n2, V, stride, k0, nv, w, partials);
+  const int nvmax = n2 <= kDotWideMaxN ? kDotWide : kDotNarrow;
+  for (int k0 = 0; k0 < count; k0 += nvmax) {
+    const int nv = count - k0 < nvmax ? count - k0 : nvmax;
+    if (nvmax == kDotWide)
+      launch_pdl(k_mdot<kDotWide>, B, 256, s, n2, V, stride, k0, nv, w, partials);
+    else
+      launch_pdl(k_mdot<kDotNarrow>, B, 256, s, n2, V, stride, k0, nv, w, partials);
   }
   launch_pdl(k_reduce_rows, count, 256, s, count, B, partials, out);
 }
