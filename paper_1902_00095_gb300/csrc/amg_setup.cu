@@ -1692,11 +1692,19 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
     cur.dpos = pool.alloc<int>(n);
     k_diag_pos<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.dpos, err);
     TP_LAUNCH_CHECK();
-    if (read_int(err, s) != 0) fail(TP_EINVAL, "AMG: a row has no diagonal entry");
-    if (n <= opts.coarse_size || (int)L.size() >= opts.max_levels) break;
-    cur.tpos = pool.alloc<int>(A.nnz);
-    csr_transpose_positions(A, cur.tpos, err, s);
-    if (read_int(err, s) != 0) fail(TP_EINVAL, "AMG: pattern is not structurally symmetric");
+    const bool coarsest = n <= opts.coarse_size || (int)L.size() >= opts.max_levels;
+    if (!coarsest) {
+      // transpose positions do not depend on the diagonal: both checks are
+      // read back with one synchronisation
+      cur.tpos = pool.alloc<int>(A.nnz);
+      csr_transpose_positions(A, cur.tpos, err, s);
+    }
+    {
+      const int e = read_int(err, s);
+      if (e & 1) fail(TP_EINVAL, "AMG: a row has no diagonal entry");
+      if (e & 2) fail(TP_EINVAL, "AMG: pattern is not structurally symmetric");
+    }
+    if (coarsest) break;
     // long rows (coarse Galerkin levels): one warp per row
     const bool wrow = A.nnz >= (long long)kWarpRowMean * n;
     const int gw = grid_for((long long)n * 32);
