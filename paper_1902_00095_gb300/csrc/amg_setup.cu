@@ -1727,13 +1727,15 @@ void Hierarchy::setup(const DevCSR& A0, const AmgOpts& o, cudaStream_t s) {
       k_pmis_init<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos, lam,
                                                  cur.cf);
     TP_LAUNCH_CHECK();
-    // rounds are enqueued in pairs before the host reads the count of
-    // undecided points: a round after the last is a no-op (no point is
-    // undecided, so nothing is selected or changed)
+    // rounds are enqueued in batches (four, then pairs) before the host
+    // reads the count of undecided points: a round after the last is a no-op
+    // (no point is undecided, so nothing is selected or changed); levels
+    // here take about five rounds
     int rounds = 0;
     while (true) {
       if (rounds >= opts.max_pmis_rounds) fail(TP_SETUP_FAILED, "PMIS round cap reached");
-      for (int r = 0; r < 2; ++r) {
+      const int batch = rounds == 0 ? 4 : 2;
+      for (int r = 0; r < batch; ++r) {
         ++rounds;
         if (wrow)
           k_pmis_select_warp<<<gw, kBlock, 0, s>>>(n, A.rowptr, A.col, cur.strong, cur.tpos, lam,
