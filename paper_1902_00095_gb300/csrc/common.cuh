@@ -145,21 +145,6 @@ void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
   count_launch();
 }
 
-// the same launch without the dependent-launch attribute
-template <typename... KArgs, typename... Args>
-void launch_plain(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
-                  Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cfg.attrs = nullptr;
-  cfg.numAttrs = 0;
-  TP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
-  count_launch();
-}
-
 // exclusive scan of n ints: out[0] = 0, out[i] = sum in[0..i-1]; out has
 // n + 1 entries and out[n] is the total. `in` and `out` may alias only if
 // equal. Returns the total (synchronises the stream).
