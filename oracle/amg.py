@@ -427,13 +427,87 @@ def l1_diag(A):
     return d
 
 
+def line_factor(A, nxy, nz):
+    """Vertical-line smoother of a grid operator (cells i = c + nxy k, column
+    c, layer k): T is the tridiagonal part of A along each column, T_ii =
+    a_ii and T_{i, i -+ nxy} = a_{i, i -+ nxy}. Factor every column's T by
+    the Thomas algorithm (Gaussian elimination without pivoting on a
+    tridiagonal matrix, Golub and Van Loan, Matrix Computations, Sec. 4.3):
+    m_0 = d_0, m_k = d_k - l_k u_{k-1} / m_{k-1}, with l_k the coefficient
+    of the cell below and u_k of the cell above. Returns (l, 1/m, u/m) per
+    cell, each [n] in cell order. Needs n = nxy nz and both vertical
+    neighbours in every row where they exist."""
+    rp, c, v = A
+    n = rp.size - 1
+    if n != nxy * nz:
+        raise ValueError("line smoother: the level is not the nxy x nz grid")
+    lo, d, up = np.zeros(n), np.zeros(n), np.zeros(n)
+    for i in range(n):
+        found_lo = found_up = False
+        for e in range(rp[i], rp[i + 1]):
+            if c[e] == i:
+                d[i] = v[e]
+            elif c[e] == i - nxy:
+                lo[i], found_lo = v[e], True
+            elif c[e] == i + nxy:
+                up[i], found_up = v[e], True
+        k = i // nxy
+        if (k > 0) != found_lo or (k < nz - 1) != found_up:
+            raise ValueError("line smoother: a vertical neighbour is missing")
+    minv, cp = np.zeros(n), np.zeros(n)
+    for col in range(nxy):
+        cprev = 0.0
+        for k in range(nz):
+            i = col + nxy * k
+            m = d[i] - lo[i] * cprev
+            if m == 0.0 or not np.isfinite(m):
+                raise RuntimeError("line smoother: zero pivot")
+            minv[i] = 1.0 / m
+            cp[i] = up[i] / m
+            cprev = cp[i]
+    return dict(nxy=nxy, nz=nz, lo=lo, minv=minv, cp=cp)
+
+
+def line_solve(lf, r):
+    """e = T^{-1} r for every column: forward elimination g_k = (r_k - l_k
+    g_{k-1}) / m_k, then back substitution e_k = g_k - (u_k / m_k) e_{k+1}."""
+    nxy, nz = lf["nxy"], lf["nz"]
+    lo, minv, cp = (lf[k].reshape(nz, nxy) for k in ("lo", "minv", "cp"))
+    rr = r.reshape(nz, nxy)
+    g = np.zeros((nz, nxy))
+    for k in range(nz):
+        prev = g[k - 1] if k > 0 else np.zeros(nxy)
+        g[k] = (rr[k] - lo[k] * prev) * minv[k]
+    e = np.zeros((nz, nxy))
+    for k in range(nz - 1, -1, -1):
+        nxt = e[k + 1] if k < nz - 1 else np.zeros(nxy)
+        e[k] = g[k] - cp[k] * nxt
+    return e.ravel()
+
+
+def line_sweep(lf, A, b, x):
+    """One vertical-line Jacobi step x <- x + T^{-1} (b - A x); from a zero
+    guess (x None) x = T^{-1} b."""
+    if x is None:
+        return line_solve(lf, b)
+    return x + line_solve(lf, b - spmv(A, x))
+
+
 def setup(A, theta=0.25, seed=0, coarse_size=256, max_levels=25,
           max_coarse_dense=4096, smoother="l1jacobi", cheb_degree=2,
-          interp="ext+i", pmax=4):
+          interp="ext+i", pmax=4, line=None, nu_line=1):
     """Build the hierarchy. Coarsening stops when the level has at most
     coarse_size rows, when max_levels is reached, or when a split keeps
     more than 90% of the points (or none); the coarsest matrix is factored
-    by dense LU with partial pivoting (Gaussian elimination, Sec. 4)."""
+    by dense LU with partial pivoting (Gaussian elimination, Sec. 4).
+
+    line = (nxy, nz) with nz > 1 smooths the finest level by nu_line
+    vertical-line Jacobi steps before and after the coarse correction
+    (line_factor) instead of `smoother`; the coarser levels keep
+    `smoother`. The paper smooths with hybrid symmetric Gauss-Seidel
+    (Sec. 4 solver settings), which carries transport along its sweep
+    direction; the line step carries the vertical (gravity-driven) part of
+    it exactly and in parallel over columns."""
     levels = []
     cur = A
     while True:
@@ -463,7 +537,9 @@ def setup(A, theta=0.25, seed=0, coarse_size=256, max_levels=25,
     if coarse["n"] > max_coarse_dense:
         raise RuntimeError("coarsest level too large for the dense solve")
     coarse["lu"] = scipy.linalg.lu_factor(to_dense(coarse["A"]))
-    return dict(levels=levels, smoother=smoother, cheb_degree=cheb_degree)
+    if line is not None and line[1] > 1 and len(levels) > 1:
+        levels[0]["line"] = line_factor(levels[0]["A"], line[0], line[1])
+    return dict(levels=levels, smoother=smoother, cheb_degree=cheb_degree, nu_line=nu_line)
 
 
 def operator_complexity(h):
@@ -530,12 +606,22 @@ def vcycle(h, b, level=0, nu_pre=1, nu_post=1):
     if level == len(levels) - 1:
         return scipy.linalg.lu_solve(lev["lu"], b)
     kind, deg = h["smoother"], h["cheb_degree"]
-    x = smooth(lev, b, None, nu_pre, kind, deg)
+    lf = lev.get("line")
+    if lf is not None:
+        x = None
+        for _ in range(h["nu_line"]):
+            x = line_sweep(lf, lev["A"], b, x)
+    else:
+        x = smooth(lev, b, None, nu_pre, kind, deg)
     if x is None:
         x = np.zeros_like(b)
     r = b - spmv(lev["A"], x)
     bc = spmv(lev["R"], r)
     ec = vcycle(h, bc, level + 1, nu_pre, nu_post)
     x = x + spmv(lev["P"], ec)
-    x = smooth(lev, b, x, nu_post, kind, deg)
+    if lf is not None:
+        for _ in range(h["nu_line"]):
+            x = line_sweep(lf, lev["A"], b, x)
+    else:
+        x = smooth(lev, b, x, nu_post, kind, deg)
     return x

@@ -164,16 +164,22 @@ def assemble(prob, p=None, T=None):
 def solve(prob, rtol=1e-8, maxit=300, restart=30, theta=0.25, seed=0,
           variant="full", smoother="l1jacobi", nu_pre=3, nu_post=3,
           coarse_size=256, p=None, T=None, schur="plain", interp="ext+i",
-          interp_S="classical", cheb_degree=2, pmax=4, smoother_S="l1jacobi"):
+          interp_S="classical", cheb_degree=2, pmax=4, smoother_S="line", nu_line=1,
+          nu_S=1):
     """Assemble, build the block preconditioner with one V-cycle per
     approximate inverse, and solve with FGMRES(restart) in the scaled
     system. A_pp's hierarchy uses `interp` (extended+i by default: the
     elliptic pressure block), S~_T's uses `interp_S` (classical by default:
     under the gravity-driven upwind advection of S~_T extended+i produces
     weights above one and indefinite coarse operators). `smoother` is A_pp's
-    smoother, `smoother_S` S~_T's (l1-Jacobi by default: Chebyshev on
-    D^{-1} S~_T, whose spectrum is not real for the advective S~_T, can
-    amplify). Returns the FGMRES dict plus the pieces it used."""
+    smoother, `smoother_S` S~_T's: "line" (default) smooths the finest
+    level of S~'s hierarchy by nu_line vertical-line Jacobi steps
+    (amg.line_factor; grids with nz = 1 keep l1-Jacobi there) and the
+    coarser levels by l1-Jacobi; "l1jacobi" everywhere; or "chebyshev"
+    (on D^{-1} S~_T, whose spectrum is not real for the advective S~_T, it
+    can amplify). S~'s hierarchy smooths its coarser levels (all levels
+    without the line steps) with nu_S sweeps before and after (None: nu_pre
+    and nu_post). Returns the FGMRES dict plus the pieces it used."""
     sys, bp, bT, S = assemble(prob, p, T)
     if schur == "att":
         S = sys.ATT
@@ -181,11 +187,15 @@ def solve(prob, rtol=1e-8, maxit=300, restart=30, theta=0.25, seed=0,
         S = physics.schur_diag_sparse(sys.rowptr, sys.col, sys.val)
     h_pp = amg.setup(sys.App, theta, seed, coarse_size, smoother=smoother,
                      interp=interp, cheb_degree=cheb_degree, pmax=pmax)
-    h_S = amg.setup(S, theta, seed, coarse_size, smoother=smoother_S,
-                    interp=interp_S, cheb_degree=cheb_degree, pmax=pmax)
+    line = (prob["nx"] * prob["ny"], prob["nz"]) if smoother_S == "line" else None
+    h_S = amg.setup(S, theta, seed, coarse_size,
+                    smoother="l1jacobi" if smoother_S == "line" else smoother_S,
+                    interp=interp_S, cheb_degree=cheb_degree, pmax=pmax, line=line,
+                    nu_line=nu_line)
     sm, se = sys.s_m, sys.s_e
     V_pp = lambda r: amg.vcycle(h_pp, r, 0, nu_pre, nu_post)
-    V_S = lambda r: amg.vcycle(h_S, r, 0, nu_pre, nu_post)
+    nS_pre, nS_post = (nu_pre, nu_post) if nu_S is None else (nu_S, nu_S)
+    V_S = lambda r: amg.vcycle(h_S, r, 0, nS_pre, nS_post)
     M = block_preconditioner(sys, V_pp, V_S, variant)
 
     def matvec(xp, xT):
