@@ -114,14 +114,29 @@ typedef struct {
   /* overrides for the Schur hierarchy (-1 or 0: same as above) */
   int interp_S;     /* -1 same, 0 classical (default), 1 extended+i           */
   int max_levels_S; /* 0 same                                                 */
-  int nu_S;         /* 0 same; else nu_pre = nu_post = nu_S                   */
+  int nu_S;         /* 0 same; else nu_pre = nu_post = nu_S (default 1: with  */
+                    /* the line smoother of smoother_S = 2 on the finest      */
+                    /* level, one sweep on each coarser level of S~ gives the */
+                    /* same FGMRES iterations as three)                       */
   int pmax;         /* interpolation truncation: at most pmax weights per row  */
                     /* (largest |w|, row sums kept); default 4, 0 = off, <=16 */
-  int smoother_S;   /* -1 same as smoother, 0 l1-Jacobi (default), 1 Chebyshev */
+  int smoother_S;   /* -1 same as smoother, 0 l1-Jacobi, 1 Chebyshev,        */
+                    /* 2 (default): vertical-line Jacobi on the finest level  */
+                    /*   (nu_line steps x += T^-1 (b - S x) before and after  */
+                    /*   the coarse correction, T the tridiagonal part of S~  */
+                    /*   along each grid column, factored by the Thomas       */
+                    /*   algorithm; a GPU-parallel stand-in for the hybrid    */
+                    /*   Gauss-Seidel of Sec. 4 that carries the vertical     */
+                    /*   transport in S~ exactly), l1-Jacobi on coarser       */
+                    /*   levels; grids with nz = 1 use l1-Jacobi throughout.  */
+                    /*   Needs both vertical neighbours in the pattern and    */
+                    /*   non-zero pivots (else TP_SETUP_FAILED)              */
   int tail_rows;    /* coarse levels (below level 0) with at most tail_rows    */
                     /* rows run as one thread-block-cluster kernel per V-cycle */
                     /* (l1-Jacobi only); 0 (default) = one kernel per phase on */
                     /* every level, measured faster on GB300 inside the graph  */
+  int nu_line;      /* smoother_S = 2: line steps before and after, 1..8       */
+                    /* (default 1)                                             */
 } tp_precond_opts;
 
 typedef struct {

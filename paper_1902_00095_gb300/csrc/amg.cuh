@@ -41,6 +41,11 @@ struct AmgOpts {
   int max_pmis_rounds = 64;
   int pmax = 0;          // interpolation truncation (0 = off)
   int tail_rows = 0;      // coarse levels with at most this many rows: one cluster kernel (0 off)
+  // vertical-line smoothing of the finest level: the level is the grid of
+  // line_nxy columns x line_nz layers (cell c + line_nxy k); nu_line line
+  // steps x <- x + T^-1 (b - A x) before and after the coarse correction,
+  // T the tridiagonal part of A along each column (off when line_nz < 2)
+  int line_nxy = 0, line_nz = 0, nu_line = 1;
 };
 
 // Device descriptor of one level for the cluster kernel of the V-cycle's
@@ -125,6 +130,11 @@ struct Level {
   int* ell_col = nullptr;
   double* ell_val = nullptr;
   float* ell_valf = nullptr;
+  // vertical-line smoother (finest level only): per cell the coefficient of
+  // the cell below (l), 1 / m and u / m of the Thomas factorisation of the
+  // column's tridiagonal part (FP64, FP32 copies in the FP32 hierarchy)
+  double *line_lo = nullptr, *line_minv = nullptr, *line_cp = nullptr;
+  float *line_lof = nullptr, *line_minvf = nullptr, *line_cpf = nullptr;
 };
 
 constexpr int kEllMaxW = 8;

@@ -1374,6 +1374,71 @@ __global__ void k_to_bf16(long long n, const double* __restrict__ a,
   if (i < n) b[i] = __float2bfloat16_rn((float)a[i]);
 }
 
+// ------------------------------------------------ vertical-line smoother
+// Thomas factorisation of each column's tridiagonal part (Gaussian
+// elimination without pivoting on a tridiagonal matrix): m_0 = d_0,
+// m_k = d_k - l_k (u_{k-1} / m_{k-1}); stores l_k, 1 / m_k and u_k / m_k.
+// Correctly rounded operations in the oracle's order (no FMA contraction).
+__global__ void k_line_factor(int nxy, int nz, const int* __restrict__ rp,
+                              const int* __restrict__ col, const double* __restrict__ val,
+                              double* __restrict__ lo, double* __restrict__ minv,
+                              double* __restrict__ cp, float* __restrict__ lof,
+                              float* __restrict__ minvf, float* __restrict__ cpf,
+                              int* __restrict__ err) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nxy) return;
+  double cprev = 0.0;
+  for (int k = 0; k < nz; ++k) {
+    const int i = c + k * nxy;
+    double d = 0.0, l = 0.0, u = 0.0;
+    bool has_lo = false, has_up = false;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = col[e];
+      if (j == i) d = val[e];
+      else if (j == i - nxy) { l = val[e]; has_lo = true; }
+      else if (j == i + nxy) { u = val[e]; has_up = true; }
+    }
+    if (has_lo != (k > 0) || has_up != (k < nz - 1)) atomicOr(err, 16);
+    const double m = __dsub_rn(d, __dmul_rn(l, cprev));
+    double mi = 0.0, cpk = 0.0;
+    if (m == 0.0 || !isfinite(m)) {
+      atomicOr(err, 16);
+    } else {
+      mi = __ddiv_rn(1.0, m);
+      cpk = __ddiv_rn(u, m);
+    }
+    lo[i] = l;
+    minv[i] = mi;
+    cp[i] = cpk;
+    if (lof) {
+      lof[i] = (float)l;
+      minvf[i] = (float)mi;
+      cpf[i] = (float)cpk;
+    }
+    cprev = cpk;
+  }
+}
+
+void line_setup(Level& v, int nxy, int nz, Pool& pool, bool f32, int* err, bool allocate,
+                cudaStream_t s) {
+  const int n = v.A.n;
+  if ((long long)nxy * nz != n) fail(TP_EINVAL, "line smoother: level is not the grid");
+  if (allocate) {
+    v.line_lo = pool.alloc<double>(n);
+    v.line_minv = pool.alloc<double>(n);
+    v.line_cp = pool.alloc<double>(n);
+    if (f32) {
+      v.line_lof = pool.alloc<float>(n);
+      v.line_minvf = pool.alloc<float>(n);
+      v.line_cpf = pool.alloc<float>(n);
+    }
+  }
+  k_line_factor<<<grid_for(nxy), kBlock, 0, s>>>(nxy, nz, v.A.rowptr, v.A.col, v.A.val,
+                                                 v.line_lo, v.line_minv, v.line_cp, v.line_lof,
+                                                 v.line_minvf, v.line_cpf, err);
+  TP_LAUNCH_CHECK();
+}
+
 // --------------------------------------------------------------- ELL copy
 __global__ void k_max_row(int n, const int* __restrict__ rp, int* __restrict__ mx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1874,6 +1939,8 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
                                                v.dinvf, err);
       TP_LAUNCH_CHECK();
     }
+    if (l == 0 && opts.line_nz > 1 && L.size() > 1)
+      line_setup(v, opts.line_nxy, opts.line_nz, pool, f32, err, allocate, s);
     if (f32) {
       if (allocate) v.A.valf = pool.alloc<float>(v.A.nnz);
       k_to_float<<<grid_for(v.A.nnz), kBlock, 0, s>>>(v.A.nnz, v.A.val, v.A.valf);
@@ -1937,6 +2004,9 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
     const int e = read_int(err, s);
     if (e & 4) fail(TP_SETUP_FAILED, "AMG: empty, zero-diagonal or non-finite row");
     if (e & 8) fail(TP_SETUP_FAILED, "AMG: Chebyshev power iteration broke down");
+    if (e & 16)
+      fail(TP_SETUP_FAILED,
+           "AMG: vertical-line smoother needs both vertical neighbours and non-zero pivots");
   }
   // coarsest level: explicit inverse by Gauss-Jordan with partial pivoting
   Level& cl = L.back();

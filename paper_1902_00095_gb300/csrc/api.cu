@@ -99,7 +99,10 @@ void check_opts(const tp_precond_opts& o) {
   if (o.precision < 0 || o.precision > 2) fail(TP_EINVAL, "precision must be 0, 1 or 2");
   if (o.interp != 0 && o.interp != 1) fail(TP_EINVAL, "interp must be 0 or 1");
   if (o.smoother != 0 && o.smoother != 1) fail(TP_EINVAL, "smoother must be 0 or 1");
-  if (o.smoother_S < -1 || o.smoother_S > 1) fail(TP_EINVAL, "smoother_S must be -1, 0 or 1");
+  if (o.smoother_S < -1 || o.smoother_S > 2)
+    fail(TP_EINVAL, "smoother_S must be -1, 0, 1 or 2");
+  if (o.smoother_S == 2 && (o.nu_line < 1 || o.nu_line > 8))
+    fail(TP_EINVAL, "nu_line must be in 1..8");
   if (o.cheb_degree < 1 || o.cheb_degree > 4) fail(TP_EINVAL, "cheb_degree must be in 1..4");
   if (o.nu_pre < 1 || o.nu_post < 1 || o.nu_pre > 8 || o.nu_post > 8)
     fail(TP_EINVAL, "nu_pre and nu_post must be in 1..8");
@@ -200,10 +203,11 @@ void tp_default_opts(tp_precond_opts* o) {
   o->use_graphs = 1;
   o->interp_S = 0;
   o->max_levels_S = 0;
-  o->nu_S = 0;
+  o->nu_S = 1;
   o->pmax = 4;
-  o->smoother_S = 0;
+  o->smoother_S = 2;
   o->tail_rows = 0;
+  o->nu_line = 1;
 }
 
 const char* tp_status_string(int st) {
@@ -1104,7 +1108,18 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
   if (o.interp_S >= 0) aS.interp = o.interp_S;
   if (o.max_levels_S > 0) aS.max_levels = o.max_levels_S;
   if (o.nu_S > 0) aS.nu_pre = aS.nu_post = o.nu_S;
-  if (o.smoother_S >= 0) aS.smoother = o.smoother_S;
+  if (o.smoother_S == 2) {
+    // vertical-line steps on the finest level (grids with one layer keep
+    // l1-Jacobi there), l1-Jacobi on the coarser levels
+    aS.smoother = 0;
+    if (c->grid.nz > 1) {
+      aS.line_nxy = c->grid.nx * c->grid.ny;
+      aS.line_nz = c->grid.nz;
+      aS.nu_line = o.nu_line;
+    }
+  } else if (o.smoother_S >= 0) {
+    aS.smoother = o.smoother_S;
+  }
   // The two hierarchies are independent: S~'s is set up by a second host
   // thread on a second stream while this thread sets up A_pp's (both setups
   // are chains of small kernels with host round trips, so they overlap).

@@ -352,6 +352,56 @@ __global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __rest
   if (lane == 0) x[row] = (TO)acc;
 }
 
+// Vertical-line step x_out = x_in + T^-1 (b - A x_in) (x_in null: x_out =
+// T^-1 b), one thread per column c of the nxy x nz grid (cell c + nxy k):
+// forward elimination g_k = (r_k - l_k g_{k-1}) / m_k with the residual row
+// r_k formed on the way up (ELL slots when the level has them, else the CSR
+// row), g_k parked in x_out, then back substitution e_k = g_k - (u_k / m_k)
+// e_{k+1} from the top down. Consecutive threads own consecutive columns,
+// so every plane is read and written coalesced.
+template <class TV, class TB, class TO>
+__global__ void __launch_bounds__(128) k_line_sweep(
+    int nxy, int nz, int n, int ell_w, const int* __restrict__ ecol, const TV* __restrict__ eval,
+    const int* __restrict__ rp, const int* __restrict__ col, const TV* __restrict__ val,
+    const TV* __restrict__ lo, const TV* __restrict__ minv, const TV* __restrict__ cp,
+    const TB* __restrict__ b, const TV* __restrict__ xin, TO* __restrict__ xout) {
+  pdl_wait();
+  pdl_trigger();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nxy) return;
+  TV gprev = TV(0);
+#pragma unroll 2
+  for (int k = 0; k < nz; ++k) {
+    const int i = c + k * nxy;
+    TV r = (TV)b[i];
+    if (xin) {
+      TV ax = TV(0);
+      if (ell_w > 0) {
+#pragma unroll
+        for (int q = 0; q < kEllMaxW; ++q)
+          if (q < ell_w) {
+            const long long e = (long long)q * n + i;
+            ax += eval[e] * xin[ecol[e]];
+          }
+      } else {
+        for (int e = rp[i]; e < rp[i + 1]; ++e) ax += val[e] * xin[col[e]];
+      }
+      r -= ax;
+    }
+    const TV g = (r - lo[i] * gprev) * minv[i];
+    xout[i] = (TO)g;
+    gprev = g;
+  }
+  TV enext = TV(0);
+#pragma unroll 2
+  for (int k = nz - 1; k >= 0; --k) {
+    const int i = c + k * nxy;
+    const TV e = (TV)xout[i] - cp[i] * enext;
+    xout[i] = (TO)(xin ? xin[i] + e : e);
+    enext = e;
+  }
+}
+
 template <class TV, class TB, class TO>
 void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b, const TV* xin,
             TO* xout, cudaStream_t s) {
@@ -437,6 +487,9 @@ struct Vals {
 };
 template <>
 struct Vals<double> {
+  static const double* lo(const Level& l) { return l.line_lo; }
+  static const double* minv(const Level& l) { return l.line_minv; }
+  static const double* cp(const Level& l) { return l.line_cp; }
   static const double* E(const Level& l) { return l.ell_val; }
   static const double* A(const Level& l) { return l.A.val; }
   static const double* P(const Level& l) { return l.P.val; }
@@ -445,6 +498,9 @@ struct Vals<double> {
 };
 template <>
 struct Vals<float> {
+  static const float* lo(const Level& l) { return l.line_lof; }
+  static const float* minv(const Level& l) { return l.line_minvf; }
+  static const float* cp(const Level& l) { return l.line_cpf; }
   static const float* E(const Level& l) { return l.ell_valf; }
   static const float* A(const Level& l) { return l.A.valf; }
   static const float* P(const Level& l) { return l.P.valf; }
@@ -505,12 +561,40 @@ void sweep_probed(Probe* pr, const Level& v, const TV* dinv, const TB* b, const 
 }
 
 // smoother selection of one V-cycle: 0 l1-Jacobi, 1 Chebyshev of `degree`;
-// tail_first >= 0: levels from tail_first down run as one cluster kernel
+// tail_first >= 0: levels from tail_first down run as one cluster kernel;
+// line_nz > 1: the finest level takes nu_line vertical-line steps instead
 struct Smooth {
   int kind = 0, degree = 2;
   int tail_first = -1, tail_cluster = 0, nc = 0;
   const TailLevel* tail_desc = nullptr;
+  int line_nxy = 0, line_nz = 0, nu_line = 1;
 };
+
+// algorithmic bytes of one line step: the level operator (ELL slots or CSR
+// row pattern), the three factor arrays, b, x_in (when present) and x_out
+template <class TV, class TB, class TO>
+double line_bytes(const Level& v, bool from_zero) {
+  const double n = v.A.n;
+  double bytes = n * (3 * sizeof(TV) + sizeof(TB) + sizeof(TO));
+  if (!from_zero) {
+    bytes += n * sizeof(TV);
+    if (v.ell_w > 0) bytes += n * v.ell_w * (sizeof(int) + sizeof(TV));
+    else bytes += (double)v.A.nnz * (sizeof(int) + sizeof(TV)) + 4.0 * (n + 1);
+  }
+  return bytes;
+}
+
+template <class TV, class TB, class TO>
+void line_step(const Smooth& sm, const Level& v, const TB* b, const TV* xin, TO* xout,
+               cudaStream_t s) {
+  // one thread per column; small blocks spread a few thousand columns over
+  // every SM
+  const int threads = sm.line_nxy >= 152 * 128 * 2 ? 128 : 32;
+  const int grid = (sm.line_nxy + threads - 1) / threads;
+  launch_pdl(k_line_sweep<TV, TB, TO>, grid, threads, s, sm.line_nxy, sm.line_nz, v.A.n,
+             v.ell_w, v.ell_col, Vals<TV>::E(v), v.A.rowptr, v.A.col, Vals<TV>::A(v),
+             Vals<TV>::lo(v), Vals<TV>::minv(v), Vals<TV>::cp(v), b, xin, xout);
+}
 
 // one smoothing step xin -> xout (xin null: zero initial guess, Chebyshev only)
 template <class TV, class TB, class TO>
@@ -554,6 +638,38 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   Probe* pr = (l == 0) ? probe : nullptr;
   TV* cur = x;
   TV* oth = t;
+  if (l == 0 && sm.line_nz > 1 && v.line_minv) {
+    // vertical-line smoothing of the finest level
+    line_step<TV, TB, TV>(sm, v, b, (const TV*)nullptr, cur, s);
+    for (int k = 1; k < sm.nu_line; ++k) {
+      line_step<TV, TB, TV>(sm, v, b, cur, oth, s);
+      std::swap(cur, oth);
+    }
+    TV* r = static_cast<TV*>(v.r);
+    level_residual<TV, TB>(v, b, cur, r, s);
+    Level& c = L[l + 1];
+    TV* bc = static_cast<TV*>(c.b);
+    if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s);
+    else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
+    TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s);
+    if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
+    else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
+    double span_bytes = 0.0;
+    if (pr) pr->before(s);
+    for (int k = 1; k <= sm.nu_line; ++k) {
+      if (k == sm.nu_line && final_out) {
+        line_step<TV, TB, TO>(sm, v, b, cur, final_out, s);
+        span_bytes += line_bytes<TV, TB, TO>(v, false);
+        if (pr) pr->after(s, span_bytes, sm.nu_line);
+        return nullptr;
+      }
+      line_step<TV, TB, TV>(sm, v, b, cur, oth, s);
+      span_bytes += line_bytes<TV, TB, TV>(v, false);
+      std::swap(cur, oth);
+    }
+    if (pr) pr->after(s, span_bytes, sm.nu_line);
+    return cur;
+  }
   int done = 1;
   if (sm.kind == 1) {
     // pre-smoothing from a zero guess
@@ -607,13 +723,15 @@ void Hierarchy::vcycle(cudaStream_t s) {
 }
 
 void Hierarchy::vcycle_fp64(cudaStream_t s) {
-  Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc};
+  Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc,
+            opts.line_nxy, opts.line_nz, opts.nu_line};
   run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                     probe);
 }
 
 void Hierarchy::vcycle_fp32(cudaStream_t s) {
-  Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc};
+  Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc,
+            opts.line_nxy, opts.line_nz, opts.nu_line};
   run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                    probe);
 }

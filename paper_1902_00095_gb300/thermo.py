@@ -44,7 +44,7 @@ class PrecondOpts(C.Structure):
                 ("max_levels", C.c_int), ("coarse_size", C.c_int), ("seed", C.c_ulonglong),
                 ("use_graphs", C.c_int), ("interp_S", C.c_int), ("max_levels_S", C.c_int),
                 ("nu_S", C.c_int), ("pmax", C.c_int), ("smoother_S", C.c_int),
-                ("tail_rows", C.c_int)]
+                ("tail_rows", C.c_int), ("nu_line", C.c_int)]
 
 
 class SolveInfo(C.Structure):
