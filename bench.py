@@ -6,11 +6,19 @@ Eq. AXR), build the block preconditioner (S~_T of Eq. Se plus one AMG
 hierarchy each for A_pp and S~_T) and solve with FGMRES(30) to relative
 residual 1e-8 (Sec. 3.2, Sec. 4 settings), all through the C-ABI library.
 
-Workload: the 64x64x32 five-spot recipe (131,072 cells, 262,144 unknowns,
-Gaussian-random-field log-permeability, 10-day step). Metric: unknowns per
-second of the whole step (higher is better); time-to-1e-8 is ms_per_step.
+Workload (default): the first Newton system of the 256x256x64 layered
+time-step recipe (4,194,304 cells, 8,388,608 unknowns, eight layers of
+log-permeability, five-spot, 30-day step). Metric: unknowns per second of
+the whole step with the plain S~_T and FP64 hierarchies (higher is better;
+ms_per_step is the time to relative residual 1e-8 in both the
+equation-scaled and the unscaled 2-norm). The variant line carries the same
+for FP32 hierarchies with the learned S~ correction; both carry an
+end-to-end figure through host buffers. V-cycle bandwidth (algorithmic
+bytes of one V-cycle over its event time) and the CUDA-event roofline of
+the largest kernel class are measured after the timed regions.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--config RECIPE] [--shape NX,NY,NZ]
 
 Multi-GPU: the path does not shard here (replicas only): each rank solves its
 own copy of the workload, value = total unknowns of all ranks / max time.
@@ -34,8 +42,10 @@ sys.path.insert(0, ROOT)
 
 from synthetic import RECIPE_SHAPES, make_problem  # noqa: E402
 
-METRIC = "unknowns/s (assemble + preconditioner setup + FGMRES to rel-res 1e-8)"
-CPU_SAMPLE = "grf32"  # the 64x64x32 recipe at 32x32x16 (1/8 of the cells)
+METRIC = ("unknowns/s (assemble + preconditioner setup + FGMRES to relative residual 1e-8 "
+          "in the scaled and the unscaled 2-norm)")
+# the oracle's bounded sample of the workload: the same recipe at 32x32x16
+CPU_SAMPLE_SHAPE = (32, 32, 16)
 
 
 def parse():
@@ -44,19 +54,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="grf64", choices=sorted(RECIPE_SHAPES),
-                    help="workload recipe (default: the 64x64x32 five-spot)")
+    ap.add_argument("--config", default="layered256", choices=sorted(RECIPE_SHAPES),
+                    help="workload recipe (default: the 256x256x64 layered recipe)")
+    ap.add_argument("--shape", default=None,
+                    help="run the recipe at another grid shape nx,ny,nz (profiling cuts)")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-sample", default=CPU_SAMPLE,
-                    help="recipe the reference arm times per step (default: the 64x64x32 "
-                         "recipe at 32x32x16)")
+    ap.add_argument("--ref-shape", default="32,32,16",
+                    help="grid shape of the bounded sample of the workload recipe that the "
+                         "reference arm times per step")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip the FP32-hierarchy + learned-Schur variant")
     ap.add_argument("--train-problems", type=int, default=16)
+    ap.add_argument("--train-shape", default="32,32,16",
+                    help="grid of the training problems (the workload recipe, seeds 1000..)")
     ap.add_argument("--nu", type=int, default=3, help="l1-Jacobi sweeps before and after")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--sequence", type=int, default=0,
@@ -72,9 +86,11 @@ def parse():
     ap.add_argument("--scaling-sizes", default="20,40,80,160,320")
     ap.add_argument("--sequence-variant", action="store_true",
                     help="--sequence with FP32 hierarchies + learned S~ (trained untimed)")
-    ap.add_argument("--probe", type=int, default=0,
-                    help="kernel timed for the roofline: 0 finest A_pp sweep, "
-                         "1 finest S~ sweep, 2 block SpMV")
+    ap.add_argument("--probe", type=int, default=3,
+                    help="kernel class timed for the roofline: 0 finest A_pp sweep, "
+                         "1 finest S~ line step, 2 block SpMV, 3 A_pp level-1 CSR sweep "
+                         "(default: the largest class of the layered step)")
+    ap.add_argument("--vcycle-reps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -133,8 +149,13 @@ class ClockSampler:
 
 
 PROBE_NAMES = {0: "k_jacobi_ell (finest A_pp level, l1-Jacobi sweep, ELL)",
-               1: "k_jacobi_ell (finest S~ level, l1-Jacobi sweep, ELL)",
-               2: "k_block_spmv (2x2 block-CSR SpMV, FP64)"}
+               1: "k_line_sweep (finest S~ level, vertical-line step)",
+               2: "k_block_spmv (2x2 block-CSR SpMV, FP64)",
+               3: "k_jacobi (A_pp level 1, l1-Jacobi sweep, CSR)"}
+
+
+def shape_of(text):
+    return tuple(int(v) for v in text.split(",")) if text else None
 
 
 def measured_peak():
@@ -146,45 +167,57 @@ def measured_peak():
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the probed
-# kernel, keyed by (recipe, probe, precision); None until a capture of the
-# current kernel
-TRAFFIC = {("grf64", 0, 0): 14.16e6,  # profiles/k_jacobi_ell_grf64_64x64x32_fp64.md
-           ("channel128", 0, 0): 118.4e6}  # profiles/k_jacobi_ell_channel128_128x128x64_fp64.md
+# kernel class of the current kernels, keyed by (recipe, shape, probe,
+# precision); absent until captured
+TRAFFIC = {}
 
 
-def cpu_baseline(seconds_target=20.0):
-    """The oracle (as it stands) on a bounded sample of the same recipe."""
+def cpu_baseline(recipe, seconds_target=10.0):
+    """The oracle (as it stands) on a bounded sample of the same recipe: one
+    or more assemble + setup + solve passes at 32x32x16, single thread."""
     from oracle import krylov as okry
-    prob = make_problem(CPU_SAMPLE)
+    prob = make_problem(recipe, shape=CPU_SAMPLE_SHAPE)
     N = prob["nx"] * prob["ny"] * prob["nz"]
     t0 = time.perf_counter()
-    out = okry.solve(prob, rtol=1e-8)
-    t = time.perf_counter() - t0
+    runs = 0
+    while True:
+        out = okry.solve(prob, rtol=1e-8)
+        runs += 1
+        if time.perf_counter() - t0 >= seconds_target:
+            break
+    t = (time.perf_counter() - t0) / runs
+    nx, ny, nz = CPU_SAMPLE_SHAPE
     return {"value": 2 * N / t, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-            "sample": f"one assemble+setup+solve of the 64x64x32 recipe at 32x32x16 "
-                      f"({2 * N} unknowns, {out['iters']} FGMRES its, {t:.1f} s, single thread)",
+            "sample": f"{runs} assemble+setup+solve passes of the {recipe} recipe at "
+                      f"{nx}x{ny}x{nz} ({2 * N} unknowns, {out['iters']} FGMRES its, "
+                      f"{t:.1f} s each, single thread)",
             "host_cores": os.cpu_count()}
 
 
-def arm_config(args, world):
-    """The workload description both arms print (the reference arm times a
-    bounded sample of it, described in its cpu_baseline)."""
-    nx, ny, nz = RECIPE_SHAPES[args.config]
+def arm_config(recipe, shape, args, world, precision="fp64 plain S~_T"):
+    """The workload description of a line: the recipe and the grid timed."""
+    nx, ny, nz = shape
     n2 = 2 * nx * ny * nz
-    return {"workload": f"{args.config}: {WORKLOAD[args.config]}, {n2} unknowns, "
-                        f"one Newton system",
+    full = tuple(RECIPE_SHAPES[recipe]) == tuple(shape)
+    where = "" if full else f" at {nx}x{ny}x{nz}"
+    return {"workload": f"{recipe}: {WORKLOAD[recipe]}{where}, {n2} unknowns, "
+                        f"first Newton system",
             "grid": [nx, ny, nz], "unknowns": n2,
-            "rtol": args.rtol, "precision": "fp64" if args.precision == 0 else "fp32 hierarchy",
-            "l2": "flushed (512 MB write) before every timed step",
+            "rtol": args.rtol, "solver": precision,
+            "nu": args.nu, "restart": args.restart,
+            "l2": "flushed (512 MB write) before every timed step; inputs > L2",
             "parallelism": f"replicas{world}"}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    """Reference arm: the FP64 CPU oracle timed on the host cores, each step
+    one assemble + setup + solve of a bounded sample (--ref-shape) of the
+    workload recipe."""
     if rank != 0:
         return
     from oracle import krylov as okry
-    prob = make_problem(args.ref_sample)
+    shape = shape_of(args.ref_shape)
+    prob = make_problem(args.config, shape=shape)
     N = prob["nx"] * prob["ny"] * prob["nz"]
     for _ in range(args.warmup):
         okry.solve(prob, rtol=args.rtol)
@@ -200,12 +233,12 @@ def run_reference(args, rank, world):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": arm_config(args, world),
+        "config": arm_config(args.config, shape, args, world),
         "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one assemble+setup+solve per step of the same recipe on a "
-                                   f"{prob['nx']}x{prob['ny']}x{prob['nz']} grid ({2 * N} "
-                                   f"unknowns), single thread; value in unknowns of the "
-                                   f"sample per second"},
+                         "sample": f"one assemble+setup+solve per step of the {args.config} "
+                                   f"recipe on a {prob['nx']}x{prob['ny']}x{prob['nz']} grid "
+                                   f"({2 * N} unknowns), single thread; value in unknowns of "
+                                   f"the sample per second"},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "fgmres_iters": int(np.median(its)),
@@ -213,21 +246,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def train_schur_model(args, after_step=False):
+def train_schur_model(args, after_step=False, recipe="grf32"):
     """Train the learned Schur correction on the GPU (untimed): exact Schur
-    columns probed on --train-problems seeded 32x32x16 problems of the
-    64x64x32 recipe, 128 columns each, 40 epochs of Adam; with after_step the
-    systems are those at the start of a second time step (behind a
-    temperature front), as in a time-step sequence."""
+    columns probed on --train-problems seeded problems of `recipe` at
+    --train-shape (seeds 1000..), 128 columns each, 40 epochs of Adam; with
+    after_step the systems are those at the start of a second time step
+    (behind a temperature front), as in a time-step sequence."""
     from paper_1902_00095_gb300 import learned as L
     from paper_1902_00095_gb300 import thermo
     from synthetic.mlp import flatten, initial_params
     t0 = time.perf_counter()
     rng = np.random.Generator(np.random.PCG64(12345))
+    shape = shape_of(args.train_shape)
     parts = []
     ts = None
     for q in range(args.train_problems):
-        tp = make_problem("grf32", seed=1000 + q)
+        tp = make_problem(recipe, seed=1000 + q, shape=shape)
         if ts is None:
             ts = thermo.Solver.from_problem(tp)
         else:
@@ -258,7 +292,8 @@ def run_ours(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prob = make_problem(args.config)
+    shape = shape_of(args.shape) or tuple(RECIPE_SHAPES[args.config])
+    prob = make_problem(args.config, shape=shape)
     N = prob["nx"] * prob["ny"] * prob["nz"]
     stream = torch.cuda.Stream(device=dev)
     s = thermo.Solver(prob["nx"], prob["ny"], prob["nz"], prob["fluid"], prob["dx"], prob["dy"],
@@ -271,145 +306,165 @@ def run_ours(args, rank, world, local):
     Re = torch.empty(N, dtype=torch.float64, device=dev)
     xp = torch.empty(N, dtype=torch.float64, device=dev)
     xT = torch.empty(N, dtype=torch.float64, device=dev)
-    opts = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
-    s.probe_enable(args.probe)
+    pin = lambda a: torch.as_tensor(a, dtype=torch.float64).contiguous().pin_memory()
+    hf = [pin(prob[k]) for k in ("Kx", "Ky", "Kz", "phi", "kTr")]
+    hs = [pin(prob[k]) for k in ("p_k", "T_k", "p_n", "T_n")]
+    hx = (torch.empty(N, dtype=torch.float64).pin_memory(),
+          torch.empty(N, dtype=torch.float64).pin_memory())
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    plain = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
 
-    def step():
+    def step(opts, rtol):
         s.set_fields(*fields)
         s.assemble(*state, prob["dt"], R_m=Rm, R_e=Re)
         s.build(opts)
-        return s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart, out=(xp, xT))[2]
+        return s.solve(rtol=rtol, maxit=args.maxit, restart=args.restart, out=(xp, xT))[2]
 
-    # the clock sampler starts during the warm-up (nvidia-smi's own start-up
-    # then falls outside the timed region) and samples until it ends
-    clk = ClockSampler(local)
-    torch.cuda.synchronize()
-    for w in range(args.warmup):
-        if w == args.warmup - 1:
-            clk.start()
-        info = step()
-    if args.warmup == 0:
-        clk.start()
-    # timed region: K steps, L2 flushed before each (flush not timed)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    s.probe_read(reset=True)
-    l0 = thermo.kernel_launches()
-    t0 = time.perf_counter()
-    infos = []
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        evs[k][0].record(stream)
-        infos.append(step())
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    launches = thermo.kernel_launches() - l0
-    pr = s.probe_read(reset=True)
-    if world > 1:
-        dist.barrier()
-    clocks = clk.stop()
-    peak, peak_kind = measured_peak()
-    achieved = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else None
-    roofline = {"bound": "hbm", "kernel": PROBE_NAMES[args.probe],
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "traffic": TRAFFIC.get((args.config, args.probe, args.precision)),
-                "launches_timed": pr["launches"],
-                "avg_launch_us": pr["ms"] * 1e3 / max(1, pr["launches"]),
-                "algorithmic_bytes_per_launch": pr["bytes"] / max(1, pr["launches"])}
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 2 * N / (ms * 1e-3)
+    def step_host(opts, rtol):
+        # end to end: inputs from pinned host memory, solution back to it
+        s.set_fields(*hf)
+        s.assemble(*hs, prob["dt"])
+        s.build(opts)
+        return s.solve(rtol=rtol, maxit=args.maxit, restart=args.restart, out=hx)[2]
 
-    # end to end through the C-ABI with pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        pin = lambda a: torch.as_tensor(a, dtype=torch.float64).contiguous().pin_memory()
-        hf = [pin(prob[k]) for k in ("Kx", "Ky", "Kz", "phi", "kTr")]
-        hs = [pin(prob[k]) for k in ("p_k", "T_k", "p_n", "T_n")]
-        hx = (torch.empty(N, dtype=torch.float64).pin_memory(),
-              torch.empty(N, dtype=torch.float64).pin_memory())
+    def warm(opts):
+        """W untimed warm-up steps; the FGMRES tolerance (a bound on the
+        equation-scaled residual) is halved until the solution also meets
+        the target in the unscaled 2-norm."""
+        rtol = args.rtol
+        w = 0
+        while True:
+            info = step(opts, rtol)
+            w += 1
+            if info["rel_res_unscaled"] > args.rtol and rtol > args.rtol / 1024:
+                rtol *= 0.5
+                continue
+            if w >= max(1, args.warmup):
+                return rtol
 
-        def step_host():
-            s.set_fields(*hf)
-            s.assemble(*hs, prob["dt"])
-            s.build(opts)
-            return s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart, out=hx)[2]
+    def timed(opts, rtol):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = thermo.kernel_launches()
+        t0 = time.perf_counter()
+        infos = []
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            evs[k][0].record(stream)
+            infos.append(step(opts, rtol))
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        launches = thermo.kernel_launches() - l0
+        if world > 1:
+            dist.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, launches, wall
 
-        step_host()
+    def e2e_run(opts, rtol):
+        if args.no_e2e:
+            return None
+        step_host(opts, rtol)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            step_host()
+            step_host(opts, rtol)
         torch.cuda.synchronize()
         te = (time.perf_counter() - t0) / args.steps
         if world > 1:
             t = torch.tensor([te], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
-        e2e = {"value": world * 2 * N / te, "unit": "unknowns/s",
-               "h2d_bytes_per_step": 9 * N * 8, "d2h_bytes_per_step": 2 * N * 8 + 2 * N * 8,
-               "ms_per_step": te * 1e3}
+        # per step: five fields and four states in, x_p and x_T out
+        return {"value": world * 2 * N / te, "unit": "unknowns/s",
+                "h2d_bytes_per_step": 9 * N * 8, "d2h_bytes_per_step": 2 * N * 8,
+                "ms_per_step": te * 1e3}
 
-    # variant: FP32 hierarchy + learned Schur correction (network trained on
-    # probed exact Schur columns of the 32x32x16 recipe before timing)
+    def solver_summary(infos, rtol):
+        last = infos[-1]
+        out = {k: last[k] for k in ("iters", "restarts", "levels_pp", "levels_S", "opc_pp",
+                                    "opc_S", "t_solve_ms")}
+        out.update(rtol_scaled_stop=rtol,
+                   max_rel_res=max(i["rel_res"] for i in infos),
+                   max_rel_res_unscaled=max(i["rel_res_unscaled"] for i in infos),
+                   max_rel_res_p=max(i["rel_res_p"] for i in infos),
+                   max_rel_res_T=max(i["rel_res_T"] for i in infos))
+        return out
+
+    peak, peak_kind = measured_peak()
+
+    def vcycles(opts):
+        """Untimed: each hierarchy's V-cycle replayed as a graph (the timed
+        build's hierarchies), algorithmic bytes / event time."""
+        out = {}
+        for which, name in ((0, "A_pp"), (1, "S")):
+            m = s.vcycle_measure(which, args.vcycle_reps)
+            m["frac"] = m["gbs"] / peak if m["gbs"] else None
+            out[name] = m
+        return out
+
+    clk = ClockSampler(local)
+    clk.start()
+    # ---- FP64 plain
+    rtol64 = warm(plain)
+    ms, infos, launches, wall = timed(plain, rtol64)
+    value = world * 2 * N / (ms * 1e-3)
+    e2e = e2e_run(plain, rtol64)
+    step(plain, rtol64)
+    vc64 = vcycles(plain)
+    setup64 = {"A_pp": s.setup_timings(0), "S": s.setup_timings(1)}
+    # ---- variant: FP32 hierarchies + learned Schur correction (network
+    # trained untimed on probed exact Schur columns of the same recipe)
     variant = None
     if not args.no_variant:
-        mlp, hist, t_train = train_schur_model(args)
+        mlp, hist, t_train = train_schur_model(args, recipe=args.config)
         s.set_schur_model(mlp)
-        # the same smoothing and restart as the FP64 run
         vopts = thermo.default_opts(precision=1, schur=1, nu_pre=args.nu, nu_post=args.nu)
-        s.probe_enable(args.probe)
-
-        def step_variant():
-            s.set_fields(*fields)
-            s.assemble(*state, prob["dt"], R_m=Rm, R_e=Re)
-            s.build(vopts)
-            return s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart,
-                           out=(xp, xT))[2]
-
-        for _ in range(args.warmup):
-            step_variant()
-        torch.cuda.synchronize()
-        s.probe_read(reset=True)
-        vev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        vinfo = None
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            vev[k][0].record(stream)
-            vinfo = step_variant()
-            vev[k][1].record(stream)
-        torch.cuda.synchronize()
-        vms = sum(a.elapsed_time(b) for a, b in vev) / args.steps
-        vpr = s.probe_read(reset=True)
+        rtol32 = warm(vopts)
+        vms, vinfos, vlaunches, _ = timed(vopts, rtol32)
+        ve2e = e2e_run(vopts, rtol32)
+        step(vopts, rtol32)
         fb_rows, fb_all = s.learned_status()
         variant = {"name": "fp32 hierarchy + learned S~ (FP64 FGMRES)", "ms_per_step": vms,
                    "value": world * 2 * N / (vms * 1e-3), "unit": "unknowns/s",
-                   "speedup_vs_fp64_plain": ms / vms, "iters": vinfo["iters"],
-                   "rel_res": vinfo["rel_res"], "rel_res_unscaled": vinfo["rel_res_unscaled"],
-                   "t_solve_ms": vinfo["t_solve_ms"],
-                   "finest_sweep_gbs": (vpr["bytes"] / (vpr["ms"] * 1e-3) / 1e9) if vpr["ms"] > 0 else None,
+                   "speedup_vs_fp64_plain": ms / vms, "e2e": ve2e,
+                   "solver": solver_summary(vinfos, rtol32),
+                   "vcycle": vcycles(vopts),
+                   "gpu_launches": int(vlaunches),
                    "learned_fallback_rows": fb_rows, "learned_global_fallback": fb_all,
-                   "training": {"problems": args.train_problems, "columns_per_problem": 128,
+                   "training": {"recipe": args.config, "shape": args.train_shape,
+                                "problems": args.train_problems, "columns_per_problem": 128,
                                 "loss_first": hist[0], "loss_last": hist[-1],
                                 "val_loss_identity": mlp.val_losses[0],
                                 "val_loss_selected": mlp.val_losses[mlp.selected_epoch],
                                 "selected_epoch": mlp.selected_epoch,
                                 "seconds_untimed": t_train}}
+    clocks = clk.stop()
+    # ---- roofline of the probed kernel class (untimed FP64 pass: the probe's
+    # events sit between the kernels of the captured preconditioner graph)
+    s.probe_enable(args.probe)
+    step(plain, rtol64)
+    pr = s.probe_read(reset=True)
+    s.probe_enable(-1)
+    achieved = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else None
+    roofline = {"bound": "hbm", "kernel": PROBE_NAMES[args.probe],
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "traffic": TRAFFIC.get((args.config, shape, args.probe, args.precision)),
+                "launches_timed": pr["launches"],
+                "avg_launch_us": pr["ms"] * 1e3 / max(1, pr["launches"]),
+                "algorithmic_bytes_per_launch": pr["bytes"] / max(1, pr["launches"])}
 
     if rank != 0:
         return
@@ -419,20 +474,19 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == 0 else "f64+f32",
         "data": "synthetic",
-        "config": arm_config(args, world),
+        "config": arm_config(args.config, shape, args, world),
         "e2e": e2e,
         "variant": variant,
+        "vcycle": vc64,
         "roofline": roofline,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed": wall,
-        "solver": {k: infos[-1][k] for k in ("iters", "restarts", "rel_res", "rel_res_unscaled",
-                                              "levels_pp", "levels_S", "opc_pp", "opc_S",
-                                              "t_solve_ms")},
-        "setup_ms": {"A_pp": s.setup_timings(0), "S": s.setup_timings(1)},
+        "solver": solver_summary(infos, rtol64),
+        "setup_ms": setup64,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(args.config)
     print(json.dumps(line), flush=True)
 
 

@@ -203,7 +203,9 @@ int tp_solve(tp_ctx* ctx, const double* b_p, const double* b_T,
  * around every launch of one kernel class during tp_solve, read back after
  * the per-iteration host synchronisation FGMRES already performs.
  * which = 0: finest-level l1-Jacobi sweeps of the A_pp hierarchy;
- *         1: finest-level sweeps of the S~ hierarchy; 2: block SpMV;
+ *         1: finest-level sweeps (or vertical-line steps) of the S~
+ *            hierarchy; 2: block SpMV; 3: l1-Jacobi sweeps on level 1 of
+ *            the A_pp hierarchy (the first Galerkin level, CSR);
  *        -1: off. Enabling resets the totals and requires a new
  * tp_build_preconditioner (the events are captured into the graph). */
 int tp_probe_enable(tp_ctx* ctx, int which);
@@ -260,6 +262,19 @@ int tp_apply_preconditioner(tp_ctx* ctx, const double* v_p, const double* v_T,
  * NULL. Also the equation scales (s_m, s_e) used by tp_solve. */
 int tp_export_system(tp_ctx* ctx, int* rowptr, int* col, double* val,
                      double* schur_val, double* scales);
+
+/* V-cycle bandwidth measurement (Sec. 3.2: each approximate inverse is one
+ * AMG V-cycle): captures one V-cycle of hierarchy which (0 A_pp, 1 Schur)
+ * of the last build as a CUDA graph, replays it once untimed and then reps
+ * times between two events on the context stream, with every entry of the
+ * right-hand side 1. Writes the mean time per V-cycle (ms), its algorithmic
+ * bytes (every level's operator, smoother scaling or line factors, R, P
+ * and vectors, each counted once per kernel that reads or writes them) and
+ * the hierarchy's operator complexity (sum of level nnz / finest nnz). Any
+ * output pointer may be NULL. Overwrites the hierarchy's work vectors (no
+ * effect on later solves). TP_ESTATE before tp_build_preconditioner. */
+int tp_vcycle_measure(tp_ctx* ctx, int which, int reps, double* ms, double* bytes,
+                      double* opc);
 
 /* Host wall time (ms) of the last AMG setup of hierarchy which (0 A_pp,
  * 1 Schur) by phase: ms[0] strength + PMIS, ms[1] interpolation,

@@ -158,9 +158,13 @@ class Hierarchy {
   // One V-cycle: out = V(in). in/out are the hierarchy's own FP64 buffers.
   void vcycle(cudaStream_t s);
   double operator_complexity() const;
+  // algorithmic bytes of one V-cycle (each kernel's operator, scaling and
+  // vectors counted once)
+  double vcycle_bytes() const;
 
   AmgOpts opts;
-  Probe* probe = nullptr;  // times the finest-level smoothing sweeps when set
+  Probe* probe = nullptr;  // times the smoothing sweeps of level probe_level when set
+  int probe_level = 0;
   std::vector<Level> L;
   int n0 = 0;
   double* in = nullptr;    // [n0] FP64 right-hand side

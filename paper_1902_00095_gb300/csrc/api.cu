@@ -63,6 +63,11 @@ __global__ void k_negate(double* a, long long n) {
   if (i < n) a[i] = -a[i];
 }
 
+__global__ void k_fill(double* a, long long n, double v) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
 void negate(double* a, long long n, cudaStream_t s) {
   k_negate<<<tp::grid_for(n), tp::kBlock, 0, s>>>(a, n);
   TP_LAUNCH_CHECK();
@@ -510,7 +515,7 @@ int tp_solve(tp_ctx* c, const double* b_p, const double* b_T, double* x_p, doubl
 }
 
 int tp_probe_enable(tp_ctx* c, int which) {
-  if (!c || which < -1 || which > 2) return TP_EINVAL;
+  if (!c || which < -1 || which > 3) return TP_EINVAL;
   TP_API_BEGIN
   if (which >= 0) c->probe.create();
   c->probe_which = which;
@@ -650,6 +655,75 @@ int tp_hierarchy_info(tp_ctx* c, int which, int* nlevels, int* n, int* nnz, int 
   if (!c || (which != 0 && which != 1)) return TP_EINVAL;
   if (!c->built) return TP_ESTATE;
   return hierarchy_info(which == 0 ? c->hpp.get() : c->hS.get(), nlevels, n, nnz, max_levels);
+}
+
+int tp_vcycle_measure(tp_ctx* c, int which, int reps, double* ms, double* bytes,
+                      double* opc) {
+  if (!c || (which != 0 && which != 1) || reps < 1) return TP_EINVAL;
+  if (!c->built) return TP_ESTATE;
+  TP_API_BEGIN
+  tp::Hierarchy* h = which == 0 ? c->hpp.get() : c->hS.get();
+  cudaStream_t s = c->s;
+  tp::Probe* saved = h->probe;
+  h->probe = nullptr;
+  k_fill<<<tp::grid_for(h->n0), tp::kBlock, 0, s>>>(h->in, h->n0, 1.0);
+  TP_LAUNCH_CHECK();
+  // one V-cycle captured as a graph (as inside the preconditioner) and
+  // replayed reps times between two events
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  tp::g_capturing = true;
+  cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    try {
+      h->vcycle(s);
+    } catch (...) {
+      tp::g_capturing = false;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      h->probe = saved;
+      throw;
+    }
+    ce = cudaStreamEndCapture(s, &g);
+  }
+  tp::g_capturing = false;
+  h->probe = saved;
+  TP_CUDA_TRY(ce);
+  size_t nodes = 0;
+  long long kernels = 0;
+  TP_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nodes));
+  std::vector<cudaGraphNode_t> list(nodes);
+  if (nodes) TP_CUDA_TRY(cudaGraphGetNodes(g, list.data(), &nodes));
+  for (cudaGraphNode_t nd : list) {
+    cudaGraphNodeType ty;
+    TP_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  TP_CUDA_TRY(cudaGraphInstantiate(&ge, g, 0));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float t = 0.f;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) err = cudaGraphLaunch(ge, s);  // warm-up
+  if (err == cudaSuccess) tp::count_launch(kernels);
+  if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    err = cudaGraphLaunch(ge, s);
+    if (err == cudaSuccess) tp::count_launch(kernels);
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  TP_CUDA_TRY(err);
+  if (ms) *ms = (double)t / reps;
+  if (bytes) *bytes = h->vcycle_bytes();
+  if (opc) *opc = h->operator_complexity();
+  return TP_OK;
+  TP_API_END
 }
 
 int tp_export_level(tp_ctx* c, int which, int level, int* rowptr, int* col, double* val,
@@ -1154,8 +1228,10 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
   if (tfail) throw terr;
   TP_CUDA_TRY(cudaEventRecord(c->ev_join, c->s2));
   TP_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
-  c->hpp->probe = c->probe_which == 0 ? &c->probe : nullptr;
+  c->hpp->probe = (c->probe_which == 0 || c->probe_which == 3) ? &c->probe : nullptr;
+  c->hpp->probe_level = c->probe_which == 3 ? 1 : 0;
   c->hS->probe = c->probe_which == 1 ? &c->probe : nullptr;
+  c->hS->probe_level = 0;
   if (o.use_graphs) {
     cudaGraph_t graph = nullptr;
     TP_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

@@ -568,6 +568,7 @@ struct Smooth {
   int tail_first = -1, tail_cluster = 0, nc = 0;
   const TailLevel* tail_desc = nullptr;
   int line_nxy = 0, line_nz = 0, nu_line = 1;
+  int probe_level = 0;  // level whose smoothing sweeps the probe times
 };
 
 // algorithmic bytes of one line step: the level operator (ELL slots or CSR
@@ -635,7 +636,7 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     return cur;
   }
   const TV* dinv = Vals<TV>::dinv(v);
-  Probe* pr = (l == 0) ? probe : nullptr;
+  Probe* pr = ((int)l == sm.probe_level) ? probe : nullptr;
   TV* cur = x;
   TV* oth = t;
   if (l == 0 && sm.line_nz > 1 && v.line_minv) {
@@ -651,7 +652,8 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     TV* bc = static_cast<TV*>(c.b);
     if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s);
     else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
-    TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s);
+    TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s,
+                                   probe);
     if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
     else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
     double span_bytes = 0.0;
@@ -692,7 +694,8 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   TV* bc = static_cast<TV*>(c.b);
   if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s);
   else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
-  TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s);
+  TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s,
+                                 probe);
   if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
   else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
   // post-smoothing; on the probed level one event pair spans all sweeps
@@ -724,16 +727,62 @@ void Hierarchy::vcycle(cudaStream_t s) {
 
 void Hierarchy::vcycle_fp64(cudaStream_t s) {
   Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc,
-            opts.line_nxy, opts.line_nz, opts.nu_line};
+            opts.line_nxy, opts.line_nz, opts.nu_line, probe_level};
   run_level<double, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                     probe);
 }
 
 void Hierarchy::vcycle_fp32(cudaStream_t s) {
   Smooth sm{opts.smoother, opts.cheb_degree, tail_first, tail_cluster, nc, tail_desc,
-            opts.line_nxy, opts.line_nz, opts.nu_line};
+            opts.line_nxy, opts.line_nz, opts.nu_line, probe_level};
   run_level<float, double, double>(L, coarse_inv, 0, in, out, opts.nu_pre, opts.nu_post, sm, s,
                                    probe);
+}
+
+// ------------------------------------------------- V-cycle byte count
+// Algorithmic bytes of one V-cycle as run_level executes it: every matrix
+// entry, index and vector element each kernel touches counted once per
+// kernel (level operator, smoother scaling or line factors, right-hand side,
+// input and output vectors; R and P with their row pointers; the coarsest
+// inverse and its two vectors). Values and vectors in the hierarchy's
+// precision; level 0 reads its right-hand side and writes its result in FP64.
+double Hierarchy::vcycle_bytes() const {
+  const bool f32 = opts.precision >= 1;
+  const double sv = f32 ? 4.0 : 8.0;
+  const double spr = opts.precision == 2 ? 2.0 : sv;  // P and R values
+  double total = 0.0;
+  const size_t nl = L.size();
+  for (size_t l = 0; l < nl; ++l) {
+    const Level& v = L[l];
+    const double n = v.A.n;
+    const double sb = (l == 0) ? 8.0 : sv;  // right-hand side
+    if (l + 1 == nl) {
+      total += n * n * 8.0 + n * sb + n * (l == 0 ? 8.0 : sv);
+      break;
+    }
+    const double amat = v.ell_w > 0 ? n * v.ell_w * (4.0 + sv)
+                                    : (double)v.A.nnz * (4.0 + sv) + 4.0 * (n + 1);
+    const double sweep = amat + n * (sv /*dinv*/ + sb + sv /*x in*/ + sv /*x out*/);
+    const double resid = amat + n * (sb + sv + sv);
+    const double nc = L[l + 1].A.n;
+    const double restr = (double)v.R.nnz * (4.0 + spr) + 4.0 * (nc + 1) + n * sv + nc * sv;
+    const double prol = (double)v.P.nnz * (4.0 + spr) + 4.0 * (n + 1) + nc * sv + 2.0 * n * sv;
+    double smooth = 0.0;
+    if (l == 0 && opts.line_nz > 1 && v.line_minv) {
+      const double fac = 3.0 * sv;
+      const double zero = n * (fac + sb + sv);
+      const double step = amat + n * (fac + sb + sv + sv);
+      smooth = zero + (opts.nu_line - 1) * step + opts.nu_line * step;
+    } else {
+      const int pre = opts.nu_pre, post = opts.nu_post;
+      const double deg = opts.smoother == 1 ? (double)opts.cheb_degree : 1.0;
+      if (opts.smoother == 0 && pre >= 2) smooth += sweep + (pre - 2) * sweep;
+      else smooth += deg * pre * sweep;
+      smooth += deg * post * sweep;
+    }
+    total += smooth + resid + restr + prol;
+  }
+  return total;
 }
 
 // ------------------------------------------------------------------ probe

@@ -97,6 +97,7 @@ SIGNATURES = {
     "tp_apply_preconditioner": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
     "tp_export_system": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp, _dp]),
     "tp_hierarchy_info": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, _ip, C.c_int]),
+    "tp_vcycle_measure": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp]),
     "tp_setup_timings": (C.c_int, [C.c_void_p, C.c_int, _dp]),
     "tp_export_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip, _ip, _dp, _sp, _sp, _ip,
                                   _ip, _ip, _dp]),
@@ -348,8 +349,8 @@ class Solver:
 
     def probe_enable(self, which):
         """Time every launch of one kernel class (0 finest A_pp sweeps,
-        1 finest S~ sweeps, 2 block SpMV, -1 off) during solves; call
-        before build()."""
+        1 finest S~ sweeps or line steps, 2 block SpMV, 3 A_pp level-1
+        sweeps, -1 off) during solves; call before build()."""
         _check(self._lib.tp_probe_enable(self._h, int(which)), "tp_probe_enable")
 
     def probe_read(self, reset=False):
@@ -397,6 +398,16 @@ class Solver:
         _check(self._lib.tp_hierarchy_info(self._h, which, C.byref(nl), n.ctypes.data_as(_ip),
                                            nnz.ctypes.data_as(_ip), 64), "tp_hierarchy_info")
         return n[:nl.value].copy(), nnz[:nl.value].copy()
+
+    def vcycle_measure(self, which, reps=20):
+        """Mean time (ms) of one V-cycle of hierarchy `which` (0 A_pp, 1
+        Schur) replayed as a graph, its algorithmic bytes and the operator
+        complexity."""
+        ms, by, opc = C.c_double(), C.c_double(), C.c_double()
+        _check(self._lib.tp_vcycle_measure(self._h, which, reps, C.byref(ms), C.byref(by),
+                                           C.byref(opc)), "tp_vcycle_measure")
+        return {"ms": ms.value, "bytes": by.value, "opc": opc.value,
+                "gbs": by.value / (ms.value * 1e-3) / 1e9 if ms.value > 0 else None}
 
     def export_level(self, which, level):
         n, nnz = self.hierarchy_info(which)

@@ -25,7 +25,7 @@ def test_reference_arm_two_gloo_ranks():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", str(free_port()),
            os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
-           "--steps", "1", "--warmup", "0", "--ref-sample", "iid16"]
+           "--steps", "1", "--warmup", "0", "--ref-shape", "12,12,8"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -34,3 +34,5 @@ def test_reference_arm_two_gloo_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the line describes the grid the oracle actually timed
+    assert d["config"]["grid"] == [12, 12, 8] and d["config"]["unknowns"] == 2 * 12 * 12 * 8
