@@ -28,15 +28,20 @@ DIRS = ("z-", "y-", "x-", "x+", "y+", "z+")
 
 def direction_slots(prob):
     """For every pattern entry e = (i, j): 0 for the diagonal, 1..6 for the
-    face direction of j seen from i (z-, y-, x-, x+, y+, z+)."""
+    face direction of j seen from i (z-, y-, x-, x+, y+, z+), read from the
+    cells' grid coordinates (the one coordinate in which i and j differ), so
+    that grids with nx = 1 or ny = 1, where index offsets coincide, still
+    name the face's true direction."""
     nx, ny = prob["nx"], prob["ny"]
     rowptr, col = physics.block_pattern(prob)
     N = rowptr.size - 1
     rows = np.repeat(np.arange(N), np.diff(rowptr))
-    d = col - rows
+    coord = lambda c: (c % nx, (c // nx) % ny, c // (nx * ny))
+    xi, yi, zi = coord(rows)
+    xj, yj, zj = coord(col)
     slot = np.zeros(col.size, np.int64)
-    for k, off in enumerate((-nx * ny, -nx, -1, 1, nx, nx * ny)):
-        slot[d == off] = k + 1
+    for k, m in enumerate((zj < zi, yj < yi, xj < xi, xj > xi, yj > yi, zj > zi)):
+        slot[m] = k + 1
     return rowptr, col, slot
 
 
@@ -193,16 +198,20 @@ def apply_correction(prob, S, O):
     """Learned S~ values on the pattern from per-cell outputs O [N, 8], with
     the per-row guard: a row falls back to plain S~ if its corrected diagonal
     is not positive or an off-diagonal changes sign or the row loses the
-    diagonal dominance the plain row had. Returns (values, fallback rows)."""
+    diagonal dominance the plain row had, or any corrected value of the row
+    is not finite (exp of a large output overflows to inf, which passes the
+    sign and dominance tests). Returns (values, fallback rows)."""
     rowptr, col, slot = direction_slots(prob)
     N = rowptr.size - 1
     rows = np.repeat(np.arange(N), np.diff(rowptr))
     dpos = physics.block_positions(rowptr, col, np.arange(N), np.arange(N))
     Sd = S[dpos]
     pick = np.where(slot == 0, 0, slot)
-    new = S * np.exp(O[rows, pick]) + np.where(slot == 0, O[rows, 7] * Sd[rows], 0.0)
+    with np.errstate(over="ignore", invalid="ignore"):
+        new = S * np.exp(O[rows, pick]) + np.where(slot == 0, O[rows, 7] * Sd[rows], 0.0)
     off = slot != 0
     bad = np.zeros(N, bool)
+    np.logical_or.at(bad, rows[~np.isfinite(new)], True)
     newd = new[dpos]
     bad |= ~(newd > 0)
     flip = off & (np.sign(new) != np.sign(S))

@@ -122,3 +122,69 @@ def test_training_reduces_the_loss():
         loss, g = learned.loss_and_grads(params, Xs, sl, St, Sd, tgt)
         params = learned.adam_step(params, g, state, lr=3e-3)
     assert loss < 0.5 * l0
+
+
+def test_features_by_hand_on_two_cells():
+    """All 24 features of a 2 x 1 x 1 grid evaluated by hand (see
+    tests/test_oracle_physics.py::two_cells: flow from cell 0 to cell 1,
+    dPhi = 1e5 Pa, T_f = 1.5e-12 m^3, Tc_f = 9.6979592 W/K, lambda =
+    9.99e5 and 999 / (1e-3 exp(-0.2)), advective coefficient 626.9724 W/K,
+    accumulation 32249.574 W/K, S~ diagonals 32886.244 and 32259.272, A_pp
+    diagonals 1.4985e-6, A_pT,00 = 2.997e-3, A_Tp,00 = 2.00631168, A_TT
+    diagonals 36898.868 and 32259.272): cell 0 sees its neighbour through
+    x+ (slot 3), cell 1 through x- (slot 2); 19 is A_pT A_Tp / (A_pp A_TT),
+    20/21 the log10 of the diagonals times s_m = 2 / sum|A_pp,ii| and s_e,
+    22 (A_TT - S~)/S~, 23 the accumulation over S~_ii; the outward advective
+    coefficient is +626.97 out of cell 0 and -626.97 out of cell 1."""
+    from test_oracle_physics import two_cells
+    prob = two_cells()
+    p, T = prob["p_k"], prob["T_k"]
+    rowptr, col, val = physics.jacobian(prob, p, T)
+    _, _, S = physics.schur_approx(prob, p, T)
+    F = learned.features(prob, p, T, val, S)
+    f0 = np.zeros(24)
+    f1 = np.zeros(24)
+    f0[3] = f1[2] = 0.17609125905568124           # log10(1.5)
+    f0[9] = f1[8] = 0.9866803519446234            # log10(9.6979592)
+    f0[12], f1[12] = -0.0004345117740176917, 0.08642438460663264
+    f0[16], f1[15] = 0.019064882926125334, -0.019435416873437864
+    f0[19] = 0.10874651716910394
+    f0[21], f1[21] = 0.0281997327426756, -0.030158744886521743
+    f0[22] = 0.1220152507272021
+    f0[23], f1[23] = 0.9806402229821107, 0.999699374518629
+    np.testing.assert_allclose(F[0], f0, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(F[1], f1, rtol=1e-12, atol=1e-15)
+
+
+def test_guard_falls_back_on_non_finite_values():
+    """An output of 1e3 overflows exp to +inf; inf passes the sign test and a
+    diagonal of +inf passes the positivity test, so the guard must reject
+    the row for not being finite; the other rows keep their corrections."""
+    prob, p, T, rowptr, col, val, S = small()
+    N = p.size
+    O = np.full((N, 8), 0.01)
+    O[5, 0] = 1e3      # diagonal of row 5 -> +inf
+    O[7, 4] = 1e3      # the x+ off-diagonal of row 7 -> -inf
+    out, bad = learned.apply_correction(prob, S, O)
+    assert bad[5] and bad[7]
+    assert bad.sum() == 2
+    assert np.all(np.isfinite(out))
+
+
+def test_direction_slots_on_degenerate_grids():
+    """With nx = 1 the neighbour at index offset -1 is the cell below in y
+    (slot 2, y-) and +1 the one above in y (slot 5, y+); with ny = 1 the
+    offset -nx is the cell below in z (slot 1, z-): the slot names the grid
+    coordinate in which the two cells differ."""
+    prob = make_problem("tiny", shape=(1, 4, 3), seed=1)
+    rowptr, col, slot = learned.direction_slots(prob)
+    i = 5    # (x, y, z) = (0, 1, 1)
+    got = {int(c) - i: int(s) for c, s in zip(col[rowptr[i]:rowptr[i + 1]],
+                                              slot[rowptr[i]:rowptr[i + 1]])}
+    assert got == {-4: 1, -1: 2, 0: 0, 1: 5, 4: 6}
+    prob = make_problem("tiny", shape=(3, 1, 4), seed=1)
+    rowptr, col, slot = learned.direction_slots(prob)
+    i = 4    # (1, 0, 1)
+    got = {int(c) - i: int(s) for c, s in zip(col[rowptr[i]:rowptr[i + 1]],
+                                              slot[rowptr[i]:rowptr[i + 1]])}
+    assert got == {-3: 1, -1: 3, 0: 0, 1: 4, 3: 6}
