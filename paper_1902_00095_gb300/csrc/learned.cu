@@ -392,10 +392,12 @@ __global__ void k_mlp_pack(MlpDev m) {
   }
 }
 
-// Row i: S_ii <- S~_ii exp(o_0) + o_7 S~_ii, S_ij <- S~_ij exp(o_d). The row
-// keeps plain S~ when the corrected diagonal is not positive, an
-// off-diagonal changes sign, or the row loses the diagonal dominance the
-// plain row had.
+// Row i: S_ii <- S~_ii exp(o_0) + o_7 S~_ii, S_ij <- S~_ij exp(o_d), d the
+// face direction of j read from the grid coordinates (z-, y-, x-, x+, y+,
+// z+: the one coordinate in which i and j differ). The row keeps plain S~
+// when a corrected value is not finite, the corrected diagonal is not
+// positive, an off-diagonal changes sign, or the row loses the diagonal
+// dominance the plain row had.
 __global__ void k_learned_schur(int N, int nx, int ny, const int* __restrict__ rowptr,
                                 const int* __restrict__ col, const int* __restrict__ dpos,
                                 const double* __restrict__ S, const float* __restrict__ O,
@@ -406,6 +408,7 @@ __global__ void k_learned_schur(int N, int nx, int ny, const int* __restrict__ r
   const float* o = O + (size_t)i * kMlpOut;
   const double sd = S[d];
   const int nxy = nx * ny;
+  const int xi = i % nx, yi = (i / nx) % ny, zi = i / nxy;
   bool bad = false;
   double offo = 0.0, offn = 0.0, nd = 0.0;
   for (int e = r0; e < r1; ++e) {
@@ -415,14 +418,14 @@ __global__ void k_learned_schur(int N, int nx, int ny, const int* __restrict__ r
       v = sd * exp((double)o[0]) + (double)o[7] * sd;
       nd = v;
     } else {
-      const int delta = j - i;
-      const int k = delta == -nxy ? 1 : delta == -nx ? 2 : delta == -1 ? 3
-                  : delta == 1 ? 4 : delta == nx ? 5 : 6;
+      const int xj = j % nx, yj = (j / nx) % ny, zj = j / nxy;
+      const int k = zj < zi ? 1 : yj < yi ? 2 : xj < xi ? 3 : xj > xi ? 4 : yj > yi ? 5 : 6;
       v = S[e] * exp((double)o[k]);
       if ((v > 0.0) != (S[e] > 0.0) || (v < 0.0) != (S[e] < 0.0)) bad = true;
       offo += fabs(S[e]);
       offn += fabs(v);
     }
+    if (!isfinite(v)) bad = true;
     out[e] = v;
   }
   if (!(nd > 0.0)) bad = true;

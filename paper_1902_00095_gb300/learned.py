@@ -27,13 +27,16 @@ if ROOT not in sys.path:
 
 def direction_slots(rowptr, col, nx, ny):
     """0 for the diagonal entry of a row, 1..6 for the face direction
-    (z-, y-, x-, x+, y+, z+) of the column."""
+    (z-, y-, x-, x+, y+, z+) of the column, from the cells' grid
+    coordinates (the one coordinate in which row and column cell differ)."""
     N = rowptr.size - 1
     rows = np.repeat(np.arange(N), np.diff(rowptr))
-    d = col - rows
+    coord = lambda c: (c % nx, (c // nx) % ny, c // (nx * ny))
+    xi, yi, zi = coord(rows)
+    xj, yj, zj = coord(col)
     slot = np.zeros(col.size, np.int32)
-    for k, off in enumerate((-nx * ny, -nx, -1, 1, nx, nx * ny)):
-        slot[d == off] = k + 1
+    for k, m in enumerate((zj < zi, yj < yi, xj < xi, xj > xi, yj > yi, zj > zi)):
+        slot[m] = k + 1
     return rows, slot
 
 
@@ -119,7 +122,9 @@ def evaluate(mlp, prob, rtol=1e-8, maxit=600, **opts):
     fb_rows, fb_all = s.learned_status()
     s.close()
     return dict(plain_iters=plain["iters"], plain_rel_res=plain["rel_res"],
+                plain_rel_res_unscaled=plain["rel_res_unscaled"],
                 learned_iters=learned["iters"], learned_rel_res=learned["rel_res"],
+                learned_rel_res_unscaled=learned["rel_res_unscaled"],
                 fallback_rows=fb_rows, global_fallback=fb_all)
 
 
@@ -133,6 +138,9 @@ def main():
     ap.add_argument("--eval", type=int, default=5)
     ap.add_argument("--eval-shape", default="96,96,48")
     ap.add_argument("--out", default=None, help="write trained parameters (.npy)")
+    ap.add_argument("--after-step", action="store_true",
+                    help="train and evaluate at the start of a second time step (behind "
+                         "the temperature front of the first), where S~_T is not exact")
     a = ap.parse_args()
     t0 = time.time()
     rng = np.random.Generator(np.random.PCG64(12345))
@@ -145,17 +153,30 @@ def main():
         else:
             s.set_fields(prob["Kx"], prob["Ky"], prob["Kz"], prob["phi"], prob["kTr"])
             s.set_wells(prob["wells"])
+        if a.after_step:
+            prob = advance_one_step(s, prob)
         parts.append(collect_samples(s, prob, a.cols, rng))
     data = concat(parts)
     t1 = time.time()
     mlp, hist = train(data, flatten(initial_params(0)), epochs=a.epochs)
     t2 = time.time()
     shape = tuple(int(v) for v in a.eval_shape.split(","))
-    evals = [evaluate(mlp, make_problem("grf96", seed=5000 + q, shape=shape)) for q in range(a.eval)]
+    evals = []
+    for q in range(a.eval):
+        prob = make_problem("grf96", seed=5000 + q, shape=shape)
+        if a.after_step:
+            es = thermo.Solver.from_problem(prob)
+            prob = advance_one_step(es, prob)
+            es.close()
+        evals.append(evaluate(mlp, prob))
     if a.out:
         np.save(a.out, mlp.params())
     print(json.dumps(dict(samples=int(data["target"].size), probe_s=t1 - t0, train_s=t2 - t1,
-                          loss_first=hist[0], loss_last=hist[-1], eval=evals)))
+                          loss_first=hist[0], loss_last=hist[-1],
+                          val_loss_identity=mlp.val_losses[0],
+                          val_loss_selected=mlp.val_losses[mlp.selected_epoch],
+                          selected_epoch=mlp.selected_epoch, after_step=a.after_step,
+                          eval=evals)))
 
 
 if __name__ == "__main__":

@@ -36,8 +36,12 @@ def random_params(seed):
     return P
 
 
-def test_features_match_oracle():
-    prob, p, T = problem()
+@pytest.mark.parametrize("shape,seed", [((12, 10, 6), 4), ((1, 9, 6), 4), ((8, 1, 5), 5)])
+def test_features_match_oracle(shape, seed):
+    """Also on grids with nx = 1 or ny = 1, where index offsets of different
+    face directions coincide: both sides name a face by the grid coordinate
+    in which its two cells differ."""
+    prob, p, T = problem(shape, seed)
     s = thermo.Solver.from_problem(prob)
     s.assemble(p, T, prob["p_n"], prob["T_n"], prob["dt"])
     X = s.learned_features().astype(np.float64)
@@ -258,3 +262,68 @@ def test_learned_correction_gains_at_time_stepping_states():
     assert err_learned < 0.9 * err_plain, report
     assert learned["iters"] <= plain["iters"] + 1, report
     assert learned["rel_res"] <= 1e-8
+
+
+def partial_fallback_params(seed=42):
+    """A network that changes every entry (outputs of order one) and whose
+    diagonal term o_7 is negative enough on some rows to make the corrected
+    diagonal non-positive there: the guard rejects about 7-14 % of the rows,
+    below the 25 % global fallback."""
+    P = initial_params(0)
+    rng = np.random.default_rng(seed)
+    P["W3"] = rng.normal(0, 0.5, P["W3"].shape)
+    P["b3"] = rng.normal(0, 0.2, 8)
+    P["W3"][7] = rng.normal(0, 1.0, 64)
+    P["b3"][7] = -0.5
+    return P
+
+
+@pytest.mark.parametrize("shape,seed", [((7, 6, 5), 3), ((1, 9, 6), 4), ((8, 1, 5), 5)])
+def test_learned_schur_matches_oracle_correction(shape, seed):
+    """The corrected S~ of a learned build equals the oracle's correction
+    (oracle.learned.apply_correction) of the same plain S~ with the same
+    network outputs, entry by entry, and the rows that fall back are the
+    same; some rows fall back, fewer than a quarter (no global fallback).
+    The outputs are the GPU network's (BF16 tensor cores) evaluated on the
+    GPU features through tp_mlp_forward, the kernel the build runs."""
+    prob, p, T = problem(shape, seed)
+    s = thermo.Solver.from_problem(prob)
+    s.assemble(p, T, prob["p_n"], prob["T_n"], prob["dt"])
+    mlp = thermo.MLP(flatten(partial_fallback_params()))
+    s.set_schur_model(mlp)
+    s.build(schur=1)
+    rows, glob = s.learned_status()
+    _, _, _, S_plain, _ = s.export_system()
+    S_learned = s.export_level(1, 0)["A"][2]
+    O = mlp.forward(s.learned_features()).astype(np.float64)
+    want, bad = olearn.apply_correction(prob, S_plain, O)
+    assert 0 < rows == int(bad.sum()) < s.N / 4 and not glob, (rows, int(bad.sum()), s.N)
+    rp, _ = ophys.block_pattern(prob)
+    r = np.repeat(np.arange(s.N), np.diff(rp))
+    scale = np.zeros(s.N)
+    np.maximum.at(scale, r, np.abs(want))
+    assert np.all(np.abs(S_learned - want) <= 1e-12 * scale[r]), np.max(np.abs(S_learned - want))
+    # changed entries outside the fallback rows
+    assert np.any(np.abs(S_learned - S_plain) > 1e-3 * scale[r])
+
+
+def test_overflowing_network_output_falls_back():
+    """An output of 800 for the z- direction overflows exp to +inf: every
+    row with a cell below falls back (not finite), as in the oracle, and with
+    more than a quarter of the rows rejected the build uses plain S~."""
+    prob, p, T = problem((7, 6, 5), 3)
+    P = initial_params(0)
+    P["b3"][1] = 800.0
+    s = thermo.Solver.from_problem(prob)
+    s.assemble(p, T, prob["p_n"], prob["T_n"], prob["dt"])
+    mlp = thermo.MLP(flatten(P))
+    s.set_schur_model(mlp)
+    s.build(schur=1)
+    rows, glob = s.learned_status()
+    _, _, _, S_plain, _ = s.export_system()
+    O = mlp.forward(s.learned_features()).astype(np.float64)
+    _, bad = olearn.apply_correction(prob, S_plain, O)
+    assert rows == int(bad.sum()) == 7 * 6 * 4 and glob
+    assert np.array_equal(s.export_level(1, 0)["A"][2], S_plain)
+    _, _, info = s.solve(rtol=1e-8)
+    assert info["status"] == 0
