@@ -15,7 +15,7 @@ import pytest
 from oracle import amg as oamg
 from oracle import krylov as okry
 from oracle import physics as ophys
-from synthetic import bennison_oil, make_problem
+from synthetic import bennison_oil, make_problem, scaling_case
 from synthetic.recipes import perturbed_state
 
 pytestmark = pytest.mark.gpu
@@ -36,8 +36,26 @@ def assemble_both(prob, p=None, T=None):
     return s, (Rm, Re), (osys, obp, obT, oS)
 
 
+def with_sources(prob, extra):
+    prob["wells"] = list(prob["wells"]) + extra
+    return prob
+
+
 PROBLEMS = {
     "iid16": lambda: (make_problem("iid16"), None),
+    # heaters of Sec. 2.1.5 (U (T_h - T) in the energy equation and U on the
+    # S~ diagonal, Eq. Se) in two columns next to the wells
+    "heater": lambda: (with_sources(make_problem("tiny", shape=(9, 8, 5), seed=31), [
+        dict(i=4, j=3, k0=0, k1=4, kind=2, value=0.0, T_inj=450.0, U=5.0e3),
+        dict(i=6, j=1, k0=1, k1=2, kind=2, value=0.0, T_inj=300.0, U=2.0e3)]), 10),
+    # rate producers (kind 3: q rho and q rho c_v T leave the cell)
+    "rateprod": lambda: (with_sources(make_problem("tiny", shape=(10, 7, 4), seed=32), [
+        dict(i=7, j=5, k0=0, k1=3, kind=3, value=4.0e-4, T_inj=0.0, U=0.0),
+        dict(i=2, j=6, k0=2, k1=2, kind=3, value=1.0e-4, T_inj=0.0, U=0.0)]), 11),
+    # the two-dimensional cases of Sec. 4.3 (heavy oil, one layer): heaters
+    # (Case IV, anisotropic) and rate injectors/producers (Case V, 12 h)
+    "case4": lambda: (scaling_case(4, 24), None),
+    "case5": lambda: (scaling_case(5, 24), None),
     "ragged": lambda: (make_problem("tiny", shape=(13, 11, 7), seed=21), 7),
     "thin": lambda: (make_problem("tiny", shape=(37, 1, 3), seed=4), 8),
     # more than 4096 cells: the finest level also gets the ELL copy
@@ -304,7 +322,8 @@ def _oracle_scaled_residual(osys, obp, obT, xp, xT):
 ERROR_RTOL = {"thin": 1e-10}
 
 
-@pytest.mark.parametrize("name", ["iid16", "ragged", "thin", "oil"])
+@pytest.mark.parametrize("name", ["iid16", "ragged", "thin", "oil", "heater", "rateprod",
+                                  "case4", "case5"])
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_matches_direct_solution(name, precision):
     prob, p, T = problem(name)
