@@ -376,9 +376,11 @@ int  tp_probe_schur_columns(tp_ctx* ctx, const int* cols, int ncols, double rtol
  * [4*nnzb] row-major 2x2 blocks), all DEVICE pointers, writing scales [2]
  * (device). It calls no cudaMalloc/cudaFree: its only scratch is a fixed
  * 64 KiB __device__ array that every GPU loading this library keeps until
- * exit. Limit: N <= 8,388,608 cells; larger N returns TP_EINVAL. The first
- * call on each device looks up the array's device address (call it once
- * before any stream capture). All calls share the array, so calls whose
+ * exit. Limit: N <= 8,388,608 cells; larger N returns TP_EINVAL. A call on
+ * a stream that is not capturing looks up the array's device address
+ * afresh (following a device reset or a new context); a call inside a stream
+ * capture reuses the address of the last uncaptured call on that device, so
+ * make one uncaptured call on each device before capturing. All calls share the array, so calls whose
  * kernels overlap on the GPU (different streams, or concurrent host
  * threads) race; serialise them. Work is enqueued on cuda_stream (a
  * cudaStream_t, NULL = legacy default stream) and the call returns without

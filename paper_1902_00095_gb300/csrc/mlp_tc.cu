@@ -18,6 +18,8 @@
 // the MMAs and commits them to an mbarrier that all threads wait on, with a
 // bounded spin that records a timeout in an error word.
 #include <cstdint>
+#include <atomic>
+
 #include "learned.cuh"
 
 namespace tp {
@@ -270,12 +272,16 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(MlpDev m, int n,
 
 void mlp_forward_tc(const MlpDev& m, int n, const float* X, float* O, int* err, cudaStream_t s) {
   if (n <= 0) return;
-  static const bool attr = []() {
+  // the large dynamic shared memory is an opt-in of the current device:
+  // set once per device ordinal
+  static std::atomic<bool> opted[64];
+  int dev = 0;
+  TP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || !opted[dev].load(std::memory_order_acquire)) {
     TP_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kTcSmem));
-    return true;
-  }();
-  (void)attr;
+    if (dev >= 0 && dev < 64) opted[dev].store(true, std::memory_order_release);
+  }
   const int blocks = (n + kTcRows - 1) / kTcRows;
   // the features' tile is bulk-copied when X is 16-byte aligned (every
   // tile then starts on a 96-byte row boundary and spans whole rows)

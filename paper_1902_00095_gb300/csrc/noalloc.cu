@@ -69,20 +69,29 @@ __global__ void k_scale_finish(int N, int nblocks, const double* __restrict__ pa
   scales[1] = (double)N / se;
 }
 
-// Device address of the scratch array, looked up once per device (host code
-// may not pass the symbol itself: on the host it is only a stand-in).
+// Device address of the scratch array (host code may not pass the symbol
+// itself: on the host it is only a stand-in). Outside stream capture it is
+// looked up on every call, so a device reset or another context on the same
+// device (where the module, and with it the array, may be loaded at a new
+// address) is followed; inside a capture the address of the last uncaptured
+// call on this device is used.
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-int scratch_for_current_device(double** out) {
+int scratch_for_current_device(cudaStream_t s, double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return TP_ECUDA;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return TP_ECUDA;
+  }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_scale_partials);
     if (e != cudaSuccess || !p) {
@@ -103,10 +112,10 @@ extern "C" int tp_equation_scales_noalloc(int N, const int* rowptr, const int* c
   if (N < 1 || !rowptr || !col || !bval || !scales) return TP_EINVAL;
   const long long nblocks = ((long long)N + kRowsPerBlock - 1) / kRowsPerBlock;
   if (nblocks > kMaxBlocks) return TP_EINVAL;  // N above 8,388,608 cells
-  double* partials = nullptr;
-  int st = scratch_for_current_device(&partials);
-  if (st != TP_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  double* partials = nullptr;
+  int st = scratch_for_current_device(s, &partials);
+  if (st != TP_OK) return st;
   k_scale_partials<<<(int)nblocks, kThreads, 0, s>>>(N, rowptr, col, bval, partials);
   k_scale_finish<<<1, 32, 0, s>>>(N, (int)nblocks, partials, scales);
   if (cudaGetLastError() != cudaSuccess) return TP_ECUDA;
