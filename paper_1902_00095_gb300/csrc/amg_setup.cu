@@ -929,8 +929,8 @@ __global__ void k_rank_rows_warp(int n, const int* __restrict__ rp, const int* _
 
 // ------------------------------------------------------------- SpGEMM C = A B
 // Upper bound (product count) of every row of C = A B; rows too long for
-// the thread-per-row kernel are listed for the warp kernel (kSpShort < ub <=
-// kSpCap) or the block kernel (ub > kSpCap), so those visit only their rows.
+// the thread-per-row kernel are listed for the warp kernel (kSpShort < ub <
+// kSpCap) or the block kernel (ub >= kSpCap), so those visit only their rows.
 // The list order is not deterministic; each row's result is.
 __global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
                             const int* __restrict__ Brp, int* __restrict__ ub,
@@ -1037,13 +1037,23 @@ __global__ void __launch_bounds__(32 * kDenseWarps) k_spgemm_dense(
   }
 }
 
-// Warp-per-row variant of k_spgemm_rows with the same summation order.
-// The products of row i are staged in shared memory with key (column << 32 |
-// sequence number), sorted by a warp bitonic sort, and every column's run is
-// summed from 0.0 in sequence order by one lane. Rows with more than kSpCap
-// products fall back to the serial insertion of k_spgemm_rows (lane 0).
+// Warp-per-row variant of k_spgemm_rows with the same summation order. The
+// warp walks row i of A in ascending k; for each k its lanes take distinct
+// entries of row k of B (whose columns are distinct), so no two lanes update
+// the same column at once, and a __syncwarp between k's keeps every
+// column's additions in ascending k, each sum starting at 0.0: the canonical
+// order. Columns find their accumulator through an open-addressing hash
+// table in shared memory (linear probing, at least twice as many slots as
+// products, so an empty slot always exists); the distinct columns are then
+// sorted by a warp bitonic sort of (column << 32 | slot) keys and written
+// in ascending order. Each batch of 32 entries of row i of A (column k,
+// value, row k's extent in B) is loaded by the warp at once, so a step over
+// k waits for one round trip (row k of B), not three. Rows with fewer than
+// kSpMid products use tables of kSpMid slots (four warps per block), rows
+// up to kSpCap tables of kSpCap slots (two warps); longer rows go to the
+// block kernel.
+constexpr int kSpMid = 512;
 constexpr int kSpCap = 1024;
-constexpr int kSpWarps = 2;  // 2 x 16 KiB static shared memory per block
 
 __global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
                             const int* __restrict__ Brp, int* __restrict__ ub,
@@ -1057,7 +1067,8 @@ __global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __res
     u += Brp[k + 1] - Brp[k];
   }
   ub[i] = u;
-  if (u > kSpCap) blist[atomicAdd(&counts[1], 1)] = i;
+  if (u >= kSpCap) blist[atomicAdd(&counts[1], 1)] = i;
+  else if (u >= kSpMid) wlist[n - 1 - atomicAdd(&counts[2], 1)] = i;
   else if (u > kSpShort) wlist[atomicAdd(&counts[0], 1)] = i;
 }
 
@@ -1094,110 +1105,123 @@ __device__ void spgemm_row_serial(int i, const int* __restrict__ Arp, const int*
   cnt[i] = u;
 }
 
-// one warp: products of row i staged in key/val (capacity >= ex), sorted,
-// runs summed in sequence order
-__device__ void spgemm_row_warp(int i, int ex, int lane, const int* __restrict__ Arp,
+// one warp: row i of C = A B through a shared-memory hash table of
+// 2^k >= 2 ex slots (hkey/hval, at most `tcap`), then the distinct columns
+// sorted in skey (capacity tcap)
+__device__ void spgemm_row_hash(int i, int ex, int lane, int tcap, const int* __restrict__ Arp,
                                 const int* __restrict__ Acol, const double* __restrict__ Aval,
                                 const int* __restrict__ Brp, const int* __restrict__ Bcol,
-                                const double* __restrict__ Bval, unsigned long long* key,
-                                double* val, int* __restrict__ cc, double* __restrict__ cv,
-                                int* __restrict__ cnt) {
-  // 1. products in canonical order (A row ascending, then B row ascending)
+                                const double* __restrict__ Bval, int* hkey, double* hval,
+                                unsigned long long* skey, int* __restrict__ cc,
+                                double* __restrict__ cv, int* __restrict__ cnt) {
+  int bits = 5;
+  while ((1 << bits) < 2 * ex && (1 << bits) < tcap) ++bits;
+  const int cap = 1 << bits;
+  for (int q = lane; q < cap; q += 32) hkey[q] = -1;
+  __syncwarp();
+  // 1. accumulate in canonical order
   const int a0 = Arp[i], a1 = Arp[i + 1];
-  int base = 0;
   for (int e0 = a0; e0 < a1; e0 += 32) {
     const int e = e0 + lane;
-    int k = 0, len = 0;
+    double a = 0.0;
+    int fb = 0, fe = 0;
     if (e < a1) {
-      k = Acol[e];
-      len = Brp[k + 1] - Brp[k];
+      const int k = Acol[e];
+      a = Aval[e];
+      fb = Brp[k];
+      fe = Brp[k + 1];
     }
-    int incl = len;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (e < a1) {
-      const double a = Aval[e];
-      const int fb = Brp[k];
-      int pidx = base + incl - len;
-      for (int t = 0; t < len; ++t, ++pidx) {
-        key[pidx] = ((unsigned long long)(unsigned)Bcol[fb + t] << 32) | (unsigned)pidx;
-        val[pidx] = __dmul_rn(a, Bval[fb + t]);
+    const int ne = min(32, a1 - e0);
+    for (int t = 0; t < ne; ++t) {
+      const double at = __shfl_sync(0xffffffffu, a, t);
+      const int f0 = __shfl_sync(0xffffffffu, fb, t);
+      const int f1 = __shfl_sync(0xffffffffu, fe, t);
+      for (int f = f0 + lane; f < f1; f += 32) {
+        const int j = Bcol[f];
+        const double prod = __dmul_rn(at, Bval[f]);
+        unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - bits);
+        for (int probe = 0; probe < cap; ++probe) {
+          const int prev = atomicCAS(&hkey[h], -1, j);
+          if (prev == -1) {
+            hval[h] = __dadd_rn(0.0, prod);
+            break;
+          }
+          if (prev == j) {
+            hval[h] = __dadd_rn(hval[h], prod);
+            break;
+          }
+          h = (h + 1) & (unsigned)(cap - 1);
+        }
       }
+      __syncwarp();
     }
-    base += total;
+  }
+  // 2. compact the occupied slots as (column << 32 | slot) keys
+  const unsigned below = (1u << lane) - 1u;
+  int d = 0;
+  for (int q0 = 0; q0 < cap; q0 += 32) {
+    const int q = q0 + lane;
+    const int c = hkey[q];
+    const unsigned m = __ballot_sync(0xffffffffu, c >= 0);
+    if (c >= 0)
+      skey[d + __popc(m & below)] = ((unsigned long long)(unsigned)c << 32) | (unsigned)q;
+    d += __popc(m);
   }
   int P = 1;
-  while (P < ex) P <<= 1;
-  for (int q = ex + lane; q < P; q += 32) key[q] = ~0ull;
+  while (P < d) P <<= 1;
+  for (int q = d + lane; q < P; q += 32) skey[q] = ~0ull;
   __syncwarp();
-  // 2. bitonic sort of the keys (ascending)
+  // 3. bitonic sort of the keys (ascending)
   for (int size = 2; size <= P; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int t = lane; t < (P >> 1); t += 32) {
         const int lo = 2 * stride * (t / stride) + (t % stride);
         const int hi = lo + stride;
         const bool up = (lo & size) == 0;
-        const unsigned long long x = key[lo], y = key[hi];
+        const unsigned long long x = skey[lo], y = skey[hi];
         if ((x > y) == up) {
-          key[lo] = y;
-          key[hi] = x;
+          skey[lo] = y;
+          skey[hi] = x;
         }
       }
       __syncwarp();
     }
   }
-  // 3. one lane per column run: sum from 0.0 in sequence order
-  int nrun = 0;
-  for (int q0 = 0; q0 < ex; q0 += 32) {
-    const int q = q0 + lane;
-    int start = 0;
-    if (q < ex) start = (q == 0) || ((key[q] >> 32) != (key[q - 1] >> 32));
-    int incl = start;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (start) {
-      const unsigned col = (unsigned)(key[q] >> 32);
-      double sum = 0.0;
-      for (int r = q; r < ex && (unsigned)(key[r] >> 32) == col; ++r)
-        sum = __dadd_rn(sum, val[(unsigned)(key[r] & 0xffffffffu)]);
-      const int rid = nrun + incl - 1;
-      cc[rid] = (int)col;
-      cv[rid] = sum;
-    }
-    nrun += total;
+  // 4. columns in ascending order with their sums
+  for (int r = lane; r < d; r += 32) {
+    const unsigned long long kk = skey[r];
+    cc[r] = (int)(kk >> 32);
+    cv[r] = hval[(unsigned)(kk & 0xffffffffu)];
   }
-  if (lane == 0) cnt[i] = nrun;
+  if (lane == 0) cnt[i] = d;
 }
 
-// rows with kSpShort < ex <= kSpCap: two warps per block, static shared memory
-__global__ void __launch_bounds__(32 * kSpWarps) k_spgemm_rows_warp(
+// rows listed for the warp kernel: tables of CAP slots, WARPS warps per block
+// (static shared memory: 20 CAP bytes per warp); rows [first, first + count)
+// of the list, count read from the device, in list order
+template <int CAP, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_spgemm_rows_warp(
     int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
     const double* __restrict__ Aval, const int* __restrict__ Brp, const int* __restrict__ Bcol,
     const double* __restrict__ Bval, const int* __restrict__ off, const int* __restrict__ ub,
-    const int* __restrict__ wlist, const int* __restrict__ counts,
+    const int* __restrict__ wlist, const int* __restrict__ counts, int which,
     int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
-  __shared__ unsigned long long s_key[kSpWarps][kSpCap];
-  __shared__ double s_val[kSpWarps][kSpCap];
+  __shared__ int s_hkey[WARPS][CAP];
+  __shared__ double s_hval[WARPS][CAP];
+  __shared__ unsigned long long s_skey[WARPS][CAP];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int count = counts[0];
-  for (int t = blockIdx.x * kSpWarps + w; t < count; t += gridDim.x * kSpWarps) {
-    const int i = wlist[t];
+  // list 0 fills wlist from the front, list 2 from the back
+  const int count = counts[which];
+  for (int t = blockIdx.x * WARPS + w; t < count; t += gridDim.x * WARPS) {
+    const int i = which == 0 ? wlist[t] : wlist[n - 1 - t];
     const int ex = ub[i];
-    spgemm_row_warp(i, ex, lane, Arp, Acol, Aval, Brp, Bcol, Bval, s_key[w], s_val[w],
-                    ccol + off[i], cval + off[i], cnt);
+    spgemm_row_hash(i, ex, lane, CAP, Arp, Acol, Aval, Brp, Bcol, Bval, s_hkey[w], s_hval[w],
+                    s_skey[w], ccol + off[i], cval + off[i], cnt);
     __syncwarp();
   }
 }
 
-// rows with ex > kSpCap: one 256-thread block per row with kSpBig entries of
+// rows with ex >= kSpCap: one 256-thread block per row with kSpBig entries of
 // dynamic shared memory (products staged by warp 0, the bitonic sort shared
 // by all threads); rows beyond that are summed serially
 constexpr int kSpBig = 8192;
@@ -1553,9 +1577,13 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ A, double* __restrict
 // threads per CSR row in the V-cycle kernels: a power of two giving each
 // lane about 4 entries (fewer lanes mean fewer shuffle steps per row, more
 // mean more parallelism on short coarse levels), halved while the launch
-// would exceed four waves of resident threads (FGMRES time per iteration on
-// the 64x64x32 / 128x128x64 hierarchies, against 4 entries per lane without
-// the cap: 2 entries +1 % / +18 %, 8 entries +8 % / -7 %)
+// would exceed four waves of resident threads, but not below the width that
+// leaves each lane at most 12 entries. FGMRES solve time on GB300 (FP64,
+// ms; layered 256x256x64 / grf 64x64x32 / channelised 128x128x64): this
+// rule 183.4 / 11.5 / 41.5; halving down to one lane (the rule of the
+// smaller grids, where level 1 of the layered A_pp, 1.25 M rows of 29.5
+// entries, ran with one lane) 200.2 / 11.4 / 42.5; floors of 8 or 16
+// entries 186.5-188.8 / 11.4-11.5 / 41.5-42.4.
 int pick_lanes(const DevCSR& A) {
   static const long long resident = []() {
     int dev = 0, sms = 0, thr = 0;
@@ -1567,7 +1595,9 @@ int pick_lanes(const DevCSR& A) {
   const double avg = A.n > 0 ? (double)A.nnz / A.n : 1.0;
   int l = 1;
   while (l * 4.0 <= avg && l < 32) l *= 2;
-  while (l > 1 && (long long)A.n * l > 4 * resident) l /= 2;
+  int lmin = 1;
+  while (lmin < 32 && avg / lmin > 12.0) lmin *= 2;
+  while (l > lmin && (long long)A.n * l > 4 * resident) l /= 2;
   return l;
 }
 
@@ -1596,8 +1626,8 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   int* off = scratch.alloc<int>(n + 1);
   int* wlist = scratch.alloc<int>(n + 1);
   int* blist = scratch.alloc<int>(n + 1);
-  int* counts = scratch.alloc<int>(2);
-  TP_CUDA_TRY(cudaMemsetAsync(counts, 0, 2 * sizeof(int), s));
+  int* counts = scratch.alloc<int>(3);
+  TP_CUDA_TRY(cudaMemsetAsync(counts, 0, 3 * sizeof(int), s));
   k_spgemm_ub<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, B.rowptr, ub, wlist, blist,
                                              counts);
   TP_LAUNCH_CHECK();
@@ -1632,11 +1662,19 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
     return v;
   }();
   {
-    long long blocks = (n + kSpWarps - 1) / kSpWarps;
+    // rows with kSpShort < ub < kSpMid (4 warps x 10 KiB per block), then
+    // kSpMid <= ub < kSpCap (2 warps x 20 KiB)
+    long long blocks = (n + 3) / 4;
+    if (blocks > 12LL * num_sms) blocks = 12LL * num_sms;
+    k_spgemm_rows_warp<kSpMid, 4><<<(int)blocks, 128, 0, s>>>(
+        n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, wlist, counts, 0, ccol, cval,
+        cnt);
+    TP_LAUNCH_CHECK();
+    blocks = (n + 1) / 2;
     if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
-    k_spgemm_rows_warp<<<(int)blocks, 32 * kSpWarps, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr,
-                                                             B.col, B.val, off, ub, wlist, counts,
-                                                             ccol, cval, cnt);
+    k_spgemm_rows_warp<kSpCap, 2><<<(int)blocks, 64, 0, s>>>(
+        n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ub, wlist, counts, 2, ccol, cval,
+        cnt);
   }
   TP_LAUNCH_CHECK();
   static const bool big_attr = []() {
