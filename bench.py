@@ -91,6 +91,10 @@ def parse():
                          "1 finest S~ line step, 2 block SpMV, 3 A_pp level-1 CSR sweep "
                          "(default: the largest class of the layered step)")
     ap.add_argument("--vcycle-reps", type=int, default=20)
+    ap.add_argument("--single", action="store_true",
+                    help="one untimed assemble + build + solve of the workload with the default "
+                         "options (no clock sampler, no measurement passes): the command the "
+                         "launch lists and kernel profiles are captured on")
     return ap.parse_args()
 
 
@@ -158,6 +162,18 @@ def shape_of(text):
     return tuple(int(v) for v in text.split(",")) if text else None
 
 
+# FP64 FMA peak of the GB300 (the bound of the FP64 sparse kernels: ncu
+# shows the FP64 pipe 85 % busy where DRAM is 39 %): 2 DFMA per clock per SM
+# (ncu sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained) x 152
+# SMs x 2 flops x 2.07 GHz maximum SM clock
+FP64_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+
+# probe classes that run in FP64 and are bound by the FP64 pipe (ncu), and
+# the algorithmic FP64 flops of one launch from the probed level's size:
+# 2 per matrix entry (multiply-add) + 3 per row (b - Ax, scaling, update)
+ALU_PROBES = {3: (0, 1)}  # probe -> (hierarchy, level)
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -168,8 +184,12 @@ def measured_peak():
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the probed
 # kernel class of the current kernels, keyed by (recipe, shape, probe,
-# precision); absent until captured
-TRAFFIC = {}
+# precision); absent until captured. The 256x256x64 figures are scaled from
+# a capture of the same kernel on the recipe at 160x160x64 by the rows of the
+# probed level (1,252,507 / 488,860; one pass over the level's rows, so the
+# traffic grows in proportion): FP64 191.35 MB, FP32 126.55 MB per launch.
+TRAFFIC = {("layered256", (256, 256, 64), 3, 0): 191.35e6 * 1252507 / 488860,
+           ("layered256", (256, 256, 64), 3, 1): 126.55e6 * 1252507 / 488860}
 
 
 def cpu_baseline(recipe, seconds_target=10.0):
@@ -452,19 +472,40 @@ def run_ours(args, rank, world, local):
     clocks = clk.stop()
     # ---- roofline of the probed kernel class (untimed FP64 pass: the probe's
     # events sit between the kernels of the captured preconditioner graph)
-    s.probe_enable(args.probe)
-    step(plain, rtol64)
-    pr = s.probe_read(reset=True)
-    s.probe_enable(-1)
-    achieved = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else None
-    roofline = {"bound": "hbm", "kernel": PROBE_NAMES[args.probe],
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "traffic": TRAFFIC.get((args.config, shape, args.probe, args.precision)),
-                "launches_timed": pr["launches"],
-                "avg_launch_us": pr["ms"] * 1e3 / max(1, pr["launches"]),
-                "algorithmic_bytes_per_launch": pr["bytes"] / max(1, pr["launches"])}
+    def probe_pass(opts, rtol, precision):
+        s.probe_enable(args.probe)
+        step(opts, rtol)
+        pr = s.probe_read(reset=True)
+        s.probe_enable(-1)
+        nl = max(1, pr["launches"])
+        gbs = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else None
+        hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s",
+               "frac": gbs / peak if gbs else None,
+               "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
+        out = {"kernel": PROBE_NAMES[args.probe] + (" FP32" if precision else " FP64"),
+               "traffic": TRAFFIC.get((args.config, shape, args.probe, precision)),
+               "launches_timed": pr["launches"], "avg_launch_us": pr["ms"] * 1e3 / nl,
+               "algorithmic_bytes_per_launch": pr["bytes"] / nl}
+        if precision == 0 and args.probe in ALU_PROBES and pr["ms"] > 0:
+            which, level = ALU_PROBES[args.probe]
+            n_l, nnz_l = s.hierarchy_info(which)
+            flops = 2.0 * float(nnz_l[level]) + 3.0 * float(n_l[level])
+            tf = flops / (pr["ms"] * 1e-3 / nl) / 1e12
+            out.update({"bound": "alu", "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                        "frac": tf / FP64_TFLOPS,
+                        "peak_kind": "FP64 FMA pipe: 2 DFMA/clock/SM x 152 SMs x 2 flops x "
+                                     "2.07 GHz (unit counts and clock; ncu: this kernel keeps "
+                                     "the FP64 pipe 85 % busy)",
+                        "algorithmic_flops_per_launch": flops, "hbm": hbm})
+        else:
+            out.update({"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit",
+                                                               "frac", "peak_kind")}})
+        return out
+
+    roofline = probe_pass(plain, rtol64, args.precision)
+    if variant is not None:
+        s.set_schur_model(mlp)
+        variant["roofline"] = probe_pass(vopts, rtol32, 1)
 
     if rank != 0:
         return
@@ -488,6 +529,36 @@ def run_ours(args, rank, world, local):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config)
     print(json.dumps(line), flush=True)
+
+
+def run_single(args, rank, world, local):
+    """One assemble + preconditioner build + FGMRES solve, nothing else."""
+    import torch
+    from paper_1902_00095_gb300 import thermo
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shape = shape_of(args.shape) or tuple(RECIPE_SHAPES[args.config])
+    prob = make_problem(args.config, shape=shape)
+    N = prob["nx"] * prob["ny"] * prob["nz"]
+    s = thermo.Solver.from_problem(prob)
+    d = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
+    st = [d(prob[k]) for k in ("p_k", "T_k", "p_n", "T_n")]
+    xp = torch.empty(N, dtype=torch.float64, device=dev)
+    xT = torch.empty(N, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.assemble(*st, prob["dt"])
+    s.build(thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu))
+    info = s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart, out=(xp, xT))[2]
+    torch.cuda.synchronize()
+    if rank == 0:
+        levels = {name: [[int(a), int(b)] for a, b in zip(*s.hierarchy_info(w))]
+                  for w, name in ((0, "A_pp"), (1, "S"))}
+        print(json.dumps({"single_step": f"{args.config} {shape}", "precision": args.precision,
+                          "iters": info["iters"], "status": info["status"],
+                          "ms": (time.perf_counter() - t0) * 1e3,
+                          "launches": thermo.kernel_launches(),
+                          "levels_rows_nnz": levels}), flush=True)
 
 
 def run_sequence(args, rank, world, local):
@@ -617,6 +688,8 @@ def main():
         dist.init_process_group(backend=backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.single:
+        run_single(args, rank, world, local)
     elif args.sequence > 0:
         run_sequence(args, rank, world, local)
     elif args.scaling2d:
