@@ -186,10 +186,10 @@ def measured_peak():
 # kernel class of the current kernels, keyed by (recipe, shape, probe,
 # precision); absent until captured. The 256x256x64 figures are scaled from
 # a capture of the same kernel on the recipe at 160x160x64 by the rows of the
-# probed level (1,252,507 / 488,860; one pass over the level's rows, so the
+# probed level (1,252,507 / 488,874; one pass over the level's rows, so the
 # traffic grows in proportion): FP64 191.35 MB, FP32 126.55 MB per launch.
-TRAFFIC = {("layered256", (256, 256, 64), 3, 0): 191.35e6 * 1252507 / 488860,
-           ("layered256", (256, 256, 64), 3, 1): 126.55e6 * 1252507 / 488860}
+TRAFFIC = {("layered256", (256, 256, 64), 3, 0): 191.35e6 * 1252507 / 488874,
+           ("layered256", (256, 256, 64), 3, 1): 126.55e6 * 1252507 / 488874}
 
 
 def cpu_baseline(recipe, seconds_target=10.0):
