@@ -476,6 +476,7 @@ def run_ours(args, rank, world, local):
         s.probe_enable(args.probe)
         step(opts, rtol)
         pr = s.probe_read(reset=True)
+        levels = s.hierarchy_info(0)  # before the probe is switched off (that unbuilds)
         s.probe_enable(-1)
         nl = max(1, pr["launches"])
         gbs = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else None
@@ -488,7 +489,7 @@ def run_ours(args, rank, world, local):
                "algorithmic_bytes_per_launch": pr["bytes"] / nl}
         if precision == 0 and args.probe in ALU_PROBES and pr["ms"] > 0:
             which, level = ALU_PROBES[args.probe]
-            n_l, nnz_l = s.hierarchy_info(which)
+            n_l, nnz_l = levels if which == 0 else s.hierarchy_info(which)
             flops = 2.0 * float(nnz_l[level]) + 3.0 * float(n_l[level])
             tf = flops / (pr["ms"] * 1e-3 / nl) / 1e12
             out.update({"bound": "alu", "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
