@@ -71,7 +71,9 @@ def parse():
     ap.add_argument("--train-problems", type=int, default=16)
     ap.add_argument("--train-shape", default="32,32,16",
                     help="grid of the training problems (the workload recipe, seeds 1000..)")
-    ap.add_argument("--nu", type=int, default=3, help="l1-Jacobi sweeps before and after")
+    ap.add_argument("--nu", type=int, default=None,
+                    help="l1-Jacobi sweeps of A_pp's hierarchy before and after (default: the "
+                         "library's 3 and 4)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--sequence", type=int, default=0,
                     help="run this many backward-Euler steps with Newton (e.g. on "
@@ -158,6 +160,11 @@ PROBE_NAMES = {0: "k_jacobi_ell (finest A_pp level, l1-Jacobi sweep, ELL)",
                3: "k_jacobi (A_pp level 1, l1-Jacobi sweep, CSR)"}
 
 
+def nu_kw(args):
+    """A_pp's sweep counts: the library defaults unless --nu overrides both."""
+    return {} if args.nu is None else {"nu_pre": args.nu, "nu_post": args.nu}
+
+
 def shape_of(text):
     return tuple(int(v) for v in text.split(",")) if text else None
 
@@ -224,7 +231,7 @@ def arm_config(recipe, shape, args, world, precision="fp64 plain S~_T"):
                         f"first Newton system",
             "grid": [nx, ny, nz], "unknowns": n2,
             "rtol": args.rtol, "solver": precision,
-            "nu": args.nu, "restart": args.restart,
+            "nu": args.nu if args.nu is not None else [3, 4], "restart": args.restart,
             "l2": "flushed (512 MB write) before every timed step; inputs > L2",
             "parallelism": f"replicas{world}"}
 
@@ -332,7 +339,7 @@ def run_ours(args, rank, world, local):
     hx = (torch.empty(N, dtype=torch.float64).pin_memory(),
           torch.empty(N, dtype=torch.float64).pin_memory())
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
-    plain = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
+    plain = thermo.default_opts(precision=args.precision, **nu_kw(args))
 
     def step(opts, rtol):
         s.set_fields(*fields)
@@ -449,7 +456,7 @@ def run_ours(args, rank, world, local):
     if not args.no_variant:
         mlp, hist, t_train = train_schur_model(args, recipe=args.config)
         s.set_schur_model(mlp)
-        vopts = thermo.default_opts(precision=1, schur=1, nu_pre=args.nu, nu_post=args.nu)
+        vopts = thermo.default_opts(precision=1, schur=1, **nu_kw(args))
         rtol32 = warm(vopts)
         vms, vinfos, vlaunches, _ = timed(vopts, rtol32)
         ve2e = e2e_run(vopts, rtol32)
@@ -549,7 +556,7 @@ def run_single(args, rank, world, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.assemble(*st, prob["dt"])
-    s.build(thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu))
+    s.build(thermo.default_opts(precision=args.precision, **nu_kw(args)))
     info = s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart, out=(xp, xT))[2]
     torch.cuda.synchronize()
     if rank == 0:
@@ -579,11 +586,11 @@ def run_sequence(args, rank, world, local):
     if args.sequence_variant:
         mlp, hist, t_train = train_schur_model(args, after_step=True)
         s.set_schur_model(mlp)
-        opts = thermo.default_opts(precision=1, schur=1, nu_pre=args.nu, nu_post=args.nu)
+        opts = thermo.default_opts(precision=1, schur=1, **nu_kw(args))
         train = {"problems": args.train_problems, "loss_first": hist[0], "loss_last": hist[-1],
                  "selected_epoch": mlp.selected_epoch, "seconds_untimed": t_train}
     else:
-        opts = thermo.default_opts(precision=args.precision, nu_pre=args.nu, nu_post=args.nu)
+        opts = thermo.default_opts(precision=args.precision, **nu_kw(args))
     d = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
     p, T = d(prob["p_n"]), d(prob["T_n"])
     from paper_1902_00095_gb300.timestep import advance
@@ -613,7 +620,8 @@ def run_sequence(args, rank, world, local):
         "dtype": "f64+f32" if (args.sequence_variant or args.precision) else "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.config}: {WORKLOAD[args.config]}, {args.sequence} steps",
-                   "unknowns": 2 * N, "nu": args.nu, "restart": args.restart,
+                   "unknowns": 2 * N, "nu": args.nu if args.nu is not None else [3, 4],
+                   "restart": args.restart,
                    "max_newton": args.max_newton, "max_cuts": args.max_cuts,
                    "solver": "fp32 hierarchy + learned S~" if args.sequence_variant else
                              ("fp32 hierarchy" if args.precision else "fp64 plain")},

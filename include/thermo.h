@@ -103,7 +103,8 @@ typedef struct {
   int smoother;     /* 0: l1-Jacobi; 1: Chebyshev on D^-1 A, D = diag(A),     */
                     /*    over [lambda/30, 1.1 lambda], lambda from 10 power  */
                     /*    iterations (A_pp; S~ uses smoother_S)               */
-  int nu_pre, nu_post, cheb_degree;  /* cheb_degree in 1..4                   */
+  int nu_pre, nu_post, cheb_degree;  /* sweeps before/after the coarse       */
+                    /* correction (defaults 3 and 4); cheb_degree in 1..4    */
   double theta;     /* strength threshold                                     */
   int max_levels;   /* at most this many levels (default 25)                  */
   int coarse_size;  /* coarsening stops at <= coarse_size rows (default 256); */

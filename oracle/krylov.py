@@ -162,7 +162,7 @@ def assemble(prob, p=None, T=None):
 
 
 def solve(prob, rtol=1e-8, maxit=300, restart=30, theta=0.25, seed=0,
-          variant="full", smoother="l1jacobi", nu_pre=3, nu_post=3,
+          variant="full", smoother="l1jacobi", nu_pre=3, nu_post=4,
           coarse_size=256, p=None, T=None, schur="plain", interp="ext+i",
           interp_S="classical", cheb_degree=2, pmax=4, smoother_S="line", nu_line=1,
           nu_S=1):

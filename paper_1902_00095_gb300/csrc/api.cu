@@ -199,7 +199,7 @@ void tp_default_opts(tp_precond_opts* o) {
   o->interp = 1;
   o->smoother = 0;
   o->nu_pre = 3;
-  o->nu_post = 3;
+  o->nu_post = 4;
   o->cheb_degree = 2;
   o->theta = 0.25;
   o->max_levels = 25;

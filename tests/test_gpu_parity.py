@@ -151,7 +151,7 @@ def test_amg_hierarchy_is_bit_exact_on_oracle_matrices(name, which, interp, pmax
     rng = np.random.default_rng(3)
     b = rng.standard_normal(A[0].size - 1)
     xg = g.vcycle(b)
-    xo = oamg.vcycle(oh, b, 0, 3, 3)
+    xo = oamg.vcycle(oh, b, 0, 3, 4)
     assert np.max(np.abs(xg - xo)) <= 1e-11 * np.max(np.abs(xo))
     g.close()
 
@@ -175,7 +175,7 @@ def test_amg_hierarchy_is_bit_exact_at_46080_cells(which, interp):
     _compare_hierarchies(g, oh, iname)
     b = np.random.default_rng(4).standard_normal(A[0].size - 1)
     xg = g.vcycle(b)
-    xo = oamg.vcycle(oh, b, 0, 3, 3)
+    xo = oamg.vcycle(oh, b, 0, 3, 4)
     assert np.max(np.abs(xg - xo)) <= 1e-11 * np.max(np.abs(xo))
     g.close()
 
@@ -287,7 +287,7 @@ def test_block_preconditioner_matches_oracle(variant, smoother_S, nu_line, preci
     oh_pp = oamg.setup(osys.App, seed=7)
     line = (prob["nx"] * prob["ny"], prob["nz"]) if smoother_S == 2 else None
     oh_S = oamg.setup(oS, seed=7, interp="classical", line=line, nu_line=nu_line)
-    M = okry.block_preconditioner(osys, lambda r: oamg.vcycle(oh_pp, r, 0, 3, 3),
+    M = okry.block_preconditioner(osys, lambda r: oamg.vcycle(oh_pp, r, 0, 3, 4),
                                   lambda r: oamg.vcycle(oh_S, r, 0, nu_S, nu_S),
                                   "full" if variant == 0 else "lower")
     rng = np.random.default_rng(2)
@@ -518,7 +518,11 @@ def test_schur_diag_matches_oracle(name):
 
 def test_schur_diag_newton_refresh_matches_rebuild():
     """Newton with structure reuse refreshes S~_diag's values in place: two
-    Newton iterations with and without reuse end at the same state."""
+    Newton iterations with and without reuse end at the same state. The
+    linear solves stop at a scaled residual of 1e-12: the temperature update
+    is small in the scaled norm (its own relative accuracy is about 1e3 times
+    the scaled tolerance), and the two runs' hierarchies differ in the second
+    iteration, so at 1e-11 their temperatures agree only to ~2e-8."""
     prob = make_problem("tiny", shape=(12, 10, 6), seed=5, dt_days=0.5)
     prob["wells"][0]["value"] = 2e-4
     prob["wells"][1]["value"] = 14.8e6
@@ -526,7 +530,7 @@ def test_schur_diag_newton_refresh_matches_rebuild():
     for reuse in (False, True):
         s = gpu_solver(prob)
         p, T, info = s.newton_step(prob["p_n"], prob["T_n"], prob["dt"], max_newton=2,
-                                   tol_f=0.0, tol_dx=0.0, rtol=1e-11, reuse=reuse, schur=3)
+                                   tol_f=0.0, tol_dx=0.0, rtol=1e-12, reuse=reuse, schur=3)
         assert info["last_linear_status"] == 0
         out.append((p, T))
     assert np.linalg.norm(out[0][0] - out[1][0]) <= 1e-8 * np.linalg.norm(out[0][0] - prob["p_n"])
