@@ -31,8 +31,16 @@ __device__ __forceinline__ int find_in(const int* __restrict__ a, int lo, int hi
   return (lo < h && a[lo] == key) ? lo : -1;
 }
 
+// (d > 0 && a < 0) || (d < 0 && a > 0), decided on the bit patterns: both
+// non-zero, neither NaN, signs differ. Integer operations instead of FP64
+// comparisons, which on this part share the FP64 pipe (2 per clock per SM)
+// with the setup's multiply-adds and divisions.
 __device__ __forceinline__ bool opposite(double a, double d) {
-  return (d > 0.0 && a < 0.0) || (d < 0.0 && a > 0.0);
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ud = (unsigned long long)__double_as_longlong(d);
+  const unsigned long long ma = ua & 0x7fffffffffffffffull, md = ud & 0x7fffffffffffffffull;
+  const unsigned long long inf = 0x7ff0000000000000ull;
+  return ma != 0 && md != 0 && ma <= inf && md <= inf && ((ua ^ ud) >> 63) != 0;
 }
 
 __global__ void k_diag_pos(int n, const int* __restrict__ rp, const int* __restrict__ col,

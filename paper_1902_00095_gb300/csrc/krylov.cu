@@ -5,9 +5,12 @@
 // equation-scaled system D A x = D b, D = diag(s_m I, s_e I) (the mass and
 // energy rows differ by ~10 orders of magnitude in SI units); the block
 // preconditioner of D A is M^{-1} D^{-1} because each V-cycle is linear and
-// scale-homogeneous. Orthogonalisation is classical Gram-Schmidt with one
-// re-orthogonalisation (CGS2); all reductions use a fixed block partition and
-// tree order, so results are deterministic.
+// scale-homogeneous. Orthogonalisation is classical Gram-Schmidt with a
+// re-orthogonalisation pass when the first pass cancelled most of w (the
+// criterion of Daniel, Gragg, Kaufman and Stewart 1976: ||w'|| < ||w|| /
+// sqrt(2), ||w||^2 = ||w'||^2 + sum h^2), decided on the device so the host
+// never waits; all reductions use a fixed block partition and tree order, so
+// results are deterministic.
 #include <cmath>
 #include <chrono>
 #include "solver.cuh"
@@ -143,10 +146,12 @@ template <int NV>
 __global__ void __launch_bounds__(256) k_mdot(long long n2, const double* __restrict__ V,
                                               long long stride, int k0, int nv,
                                               const double* __restrict__ w,
-                                              double* __restrict__ partials) {
+                                              double* __restrict__ partials,
+                                              const int* __restrict__ gate) {
   __shared__ double sh[8][NV];
   pdl_wait();
   pdl_trigger();
+  if (gate && *gate == 0) return;  // re-orthogonalisation not needed
   long long lo, hi;
   chunk_of(n2, lo, hi);
   double acc[NV];
@@ -174,13 +179,17 @@ __global__ void __launch_bounds__(256) k_mdot(long long n2, const double* __rest
   }
 }
 
-// out[k] = sum_b partials[k * B + b], k < count (fixed order)
+// out[k] = sum_b partials[k * B + b], k < count (fixed order); 0 when gated off
 __global__ void k_reduce_rows(int count, int B, const double* __restrict__ partials,
-                              double* __restrict__ out) {
+                              double* __restrict__ out, const int* __restrict__ gate) {
   pdl_wait();
   pdl_trigger();
   const int k = blockIdx.x;
   if (k >= count) return;
+  if (gate && *gate == 0) {
+    if (threadIdx.x == 0) out[k] = 0.0;
+    return;
+  }
   double v = 0.0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) v += partials[(long long)k * B + b];
   block_sum_store(v, &out[k]);
@@ -194,9 +203,11 @@ __global__ void __launch_bounds__(256) k_orth_update(long long n2, const double*
                                                      long long stride, int count,
                                                      const double* __restrict__ h,
                                                      double* __restrict__ w,
-                                                     double* __restrict__ norm_partials) {
+                                                     double* __restrict__ norm_partials,
+                                                     const int* __restrict__ gate) {
   pdl_wait();
   pdl_trigger();
+  if (gate && *gate == 0) return;  // w and the first pass's norm partials stand
   const long long step = (long long)gridDim.x * blockDim.x;
   double nrm = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += step) {
@@ -259,6 +270,23 @@ __global__ void __launch_bounds__(256) k_arnoldi(int j, int ldh, double* __restr
   est[0] = fabs(g[j + 1]);
   est[1] = hn;
   est[2] = den;
+}
+
+// re-orthogonalise iff ||w'||^2 < (||w'||^2 + sum_k h_k^2) / 2 after the
+// first pass (fixed-order sums)
+__global__ void __launch_bounds__(256) k_reorth_gate(int count, const double* __restrict__ h,
+                                                     const double* __restrict__ npart, int B,
+                                                     int* __restrict__ gate) {
+  __shared__ double tot;
+  pdl_wait();
+  pdl_trigger();
+  double part = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) part += npart[b];
+  block_sum_store(part, &tot);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double hh = 0.0;
+  for (int k = 0; k < count; ++k) hh += h[k] * h[k];
+  *gate = (2.0 * tot < tot + hh || !(tot == tot)) ? 1 : 0;
 }
 
 __global__ void k_normalize(long long n2, const double* __restrict__ w,
@@ -384,16 +412,17 @@ __global__ void k_sqrt_inplace(double* v) {
 }
 
 void mdot_all(long long n2, const double* V, long long stride, int count, const double* w,
-              double* partials, int B, double* out, cudaStream_t s) {
+              double* partials, int B, double* out, cudaStream_t s,
+              const int* gate = nullptr) {
   const int nvmax = n2 <= kDotWideMaxN ? kDotWide : kDotNarrow;
   for (int k0 = 0; k0 < count; k0 += nvmax) {
     const int nv = count - k0 < nvmax ? count - k0 : nvmax;
     if (nvmax == kDotWide)
-      launch_pdl(k_mdot<kDotWide>, B, 256, s, n2, V, stride, k0, nv, w, partials);
+      launch_pdl(k_mdot<kDotWide>, B, 256, s, n2, V, stride, k0, nv, w, partials, gate);
     else
-      launch_pdl(k_mdot<kDotNarrow>, B, 256, s, n2, V, stride, k0, nv, w, partials);
+      launch_pdl(k_mdot<kDotNarrow>, B, 256, s, n2, V, stride, k0, nv, w, partials, gate);
   }
-  launch_pdl(k_reduce_rows, count, 256, s, count, B, partials, out);
+  launch_pdl(k_reduce_rows, count, 256, s, count, B, partials, out, gate);
 }
 
 // grid of k_orth_update: enough blocks for 8 resident per SM, at most one
@@ -430,6 +459,7 @@ void ensure_workspace(tp_ctx* c, int restart) {
   c->h2 = c->kpool.alloc<double>(2 * (restart + 2));
   c->kparts = c->kpool.alloc<double>((size_t)(restart + 2) * 4 * c->nparts + 16);
   c->oparts = c->kpool.alloc<double>((size_t)orth_grid(c, 2ll * c->N) + 16);
+  c->reorth = c->kpool.alloc<int>(4);
   c->restart_alloc = restart;
 }
 
@@ -553,10 +583,10 @@ int scalar_fgmres(tp_ctx* c, Hierarchy& h, const DevCSR& A, const double* b, dou
       double* h2 = c->h2 + (restart + 2);
       const int G = orth_grid(c, n);
       mdot_all(n, c->Vb, n, j + 1, c->w, c->kparts, B, h1, s);
-      k_orth_update<<<G, 256, 0, s>>>(n, c->Vb, n, j + 1, h1, c->w, nullptr);
+      k_orth_update<<<G, 256, 0, s>>>(n, c->Vb, n, j + 1, h1, c->w, nullptr, nullptr);
       TP_LAUNCH_CHECK();
       mdot_all(n, c->Vb, n, j + 1, c->w, c->kparts, B, h2, s);
-      k_orth_update<<<G, 256, 0, s>>>(n, c->Vb, n, j + 1, h2, c->w, c->oparts);
+      k_orth_update<<<G, 256, 0, s>>>(n, c->Vb, n, j + 1, h2, c->w, c->oparts, nullptr);
       TP_LAUNCH_CHECK();
       k_arnoldi<<<1, 256, 0, s>>>(j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, c->oparts, G, c->hn,
                                   c->est);
@@ -735,14 +765,18 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
           c->probe.after(s, 36.0 * c->nnzb + 4.0 * (N + 1) + 48.0 * N);
           c->probe.active = 0;
         }
-        // CGS2 against V_0..V_j
+        // classical Gram-Schmidt against V_0..V_j, a second pass when the
+        // first cancelled most of w
         double* h1 = c->h2;
         double* h2 = c->h2 + (restart + 2);
         const int G = orth_grid(c, n2);
         mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h1, s);
-        launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h1, c->w, (double*)nullptr);
-        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h2, s);
-        launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h2, c->w, c->oparts);
+        launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h1, c->w, c->oparts,
+                   (const int*)nullptr);
+        launch_pdl(k_reorth_gate, 1, 256, s, j + 1, h1, c->oparts, G, c->reorth);
+        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h2, s, c->reorth);
+        launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h2, c->w, c->oparts,
+                   (const int*)c->reorth);
         launch_pdl(k_arnoldi, 1, 256, s, j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, c->oparts, G,
                    c->hn, c->est);
         TP_CUDA_TRY(cudaMemcpyAsync(hp_host + kEstSlot + 4 * (j & 1), c->est, 3 * sizeof(double),

@@ -68,6 +68,7 @@ struct tp_ctx {
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
          *hn = nullptr, *est = nullptr, *kparts = nullptr, *h2 = nullptr;
   double* oparts = nullptr;    // norm partials of the orthogonalisation update
+  int* reorth = nullptr;       // 1: this column's Gram-Schmidt takes its second pass
   double* host_est = nullptr;  // pinned [32]
   cudaEvent_t ev_est[2] = {nullptr, nullptr};  // convergence estimates of iterations j, j+1
   // learned Schur correction
