@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--nu", type=int, default=None,
                     help="l1-Jacobi sweeps of A_pp's hierarchy before and after (default: the "
                          "library's 3 and 4)")
+    ap.add_argument("--sell-rows", type=int, default=None,
+                    help="minimum rows of a level's sliced-ELL copy (default: the library's "
+                         "one wave of resident threads; -1 never, 1 every level between the "
+                         "finest and the coarsest)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--sequence", type=int, default=0,
                     help="run this many backward-Euler steps with Newton (e.g. on "
@@ -158,25 +162,33 @@ PROBE_NAMES = {0: "k_jacobi_ell (finest A_pp level, l1-Jacobi sweep, ELL)",
                1: "k_line_sweep (finest S~ level, vertical-line step)",
                2: "k_block_spmv (2x2 block-CSR SpMV, FP64)",
                3: "k_jacobi (A_pp level 1, l1-Jacobi sweep, CSR)"}
+# class 3 when level 1 keeps a sliced-ELL copy (levels of a full wave of
+# resident threads or more)
+PROBE_NAME_SLICED = "k_sell_jacobi (A_pp level 1, l1-Jacobi sweep, sliced ELL)"
 
 
 def nu_kw(args):
-    """A_pp's sweep counts: the library defaults unless --nu overrides both."""
-    return {} if args.nu is None else {"nu_pre": args.nu, "nu_post": args.nu}
+    """A_pp's sweep counts (--nu overrides both) and the sliced-ELL threshold
+    (--sell-rows): the library defaults unless given."""
+    kw = {} if args.nu is None else {"nu_pre": args.nu, "nu_post": args.nu}
+    if args.sell_rows is not None:
+        kw["sell_rows"] = args.sell_rows
+    return kw
 
 
 def shape_of(text):
     return tuple(int(v) for v in text.split(",")) if text else None
 
 
-# FP64 FMA peak of the GB300 (the bound of the FP64 sparse kernels: ncu
-# shows the FP64 pipe 85 % busy where DRAM is 39 %): 2 DFMA per clock per SM
+# FP64 FMA peak of the GB300 (a bound of the FP64 sparse kernels next to
+# HBM: ncu shows the FP64 pipe 85 % busy where DRAM is 39 % in the CSR sweep
+# with lanes per row, 69 % and 54 % in the sliced-ELL sweep): 2 DFMA per clock per SM
 # (ncu sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained) x 152
 # SMs x 2 flops x 2.07 GHz maximum SM clock
 FP64_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
-# probe classes that run in FP64 and are bound by the FP64 pipe (ncu), and
-# the algorithmic FP64 flops of one launch from the probed level's size:
+# probe classes that run in FP64 with the FP64 pipe as a bound next to HBM,
+# and the algorithmic FP64 flops of one launch from the probed level's size:
 # 2 per matrix entry (multiply-add) + 3 per row (b - Ax, scaling, update)
 ALU_PROBES = {3: (0, 1)}  # probe -> (hierarchy, level)
 
@@ -191,12 +203,17 @@ def measured_peak():
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the probed
 # kernel class of the current kernels, keyed by (recipe, shape, probe,
-# precision); absent until captured. The 256x256x64 figures are scaled from
-# a capture of the same kernel on the recipe at 160x160x64 by the rows of the
-# probed level (1,252,507 / 488,874; one pass over the level's rows, so the
-# traffic grows in proportion): FP64 191.35 MB, FP32 126.55 MB per launch.
-TRAFFIC = {("layered256", (256, 256, 64), 3, 0): 191.35e6 * 1252507 / 488874,
-           ("layered256", (256, 256, 64), 3, 1): 126.55e6 * 1252507 / 488874}
+# level 1 sliced, precision); absent until captured. The 256x256x64 figures
+# are scaled from a capture of the same kernel on the recipe at 160x160x64
+# (one pass over the level's stored slots and rows, so the traffic grows in
+# proportion).
+TRAFFIC = {
+    # sliced-ELL sweep at 160x160x64 (15,413,760 stored slots): FP64 198.73 +
+    # 4.77 MB, FP32 131.21 + 3.66 MB per launch; scaled by the stored slots of
+    # the 256x256x64 level (39,624,512; rows scale by 2.562, slots by 2.571)
+    ("layered256", (256, 256, 64), 3, True, 0): 203.50e6 * 39624512 / 15413760,
+    ("layered256", (256, 256, 64), 3, True, 1): 134.87e6 * 39624512 / 15413760,
+}
 
 
 def cpu_baseline(recipe, seconds_target=10.0):
@@ -232,6 +249,7 @@ def arm_config(recipe, shape, args, world, precision="fp64 plain S~_T"):
             "grid": [nx, ny, nz], "unknowns": n2,
             "rtol": args.rtol, "solver": precision,
             "nu": args.nu if args.nu is not None else [3, 4], "restart": args.restart,
+            "sell_rows": args.sell_rows if args.sell_rows is not None else "one wave",
             "l2": "flushed (512 MB write) before every timed step; inputs > L2",
             "parallelism": f"replicas{world}"}
 
@@ -484,27 +502,38 @@ def run_ours(args, rank, world, local):
         step(opts, rtol)
         pr = s.probe_read(reset=True)
         levels = s.hierarchy_info(0)  # before the probe is switched off (that unbuilds)
+        sliced = args.probe == 3 and s.level_storage(0, 1)[0] == 2
         s.probe_enable(-1)
         nl = max(1, pr["launches"])
         gbs = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else None
         hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s",
                "frac": gbs / peak if gbs else None,
                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
-        out = {"kernel": PROBE_NAMES[args.probe] + (" FP32" if precision else " FP64"),
-               "traffic": TRAFFIC.get((args.config, shape, args.probe, precision)),
+        name = PROBE_NAME_SLICED if sliced else PROBE_NAMES[args.probe]
+        out = {"kernel": name + (" FP32" if precision else " FP64"),
+               "traffic": TRAFFIC.get((args.config, shape, args.probe, sliced, precision)),
                "launches_timed": pr["launches"], "avg_launch_us": pr["ms"] * 1e3 / nl,
                "algorithmic_bytes_per_launch": pr["bytes"] / nl}
         if precision == 0 and args.probe in ALU_PROBES and pr["ms"] > 0:
+            # the FP64 sweep has two bounds: the FP64 FMA pipe and HBM; the
+            # one it reaches the larger fraction of is reported as the bound
+            # (CSR with lanes per row: the pipe, 85 % busy in ncu; sliced
+            # ELL: HBM, the pipe 66 % busy), the other nested beside it
             which, level = ALU_PROBES[args.probe]
             n_l, nnz_l = levels if which == 0 else s.hierarchy_info(which)
             flops = 2.0 * float(nnz_l[level]) + 3.0 * float(n_l[level])
             tf = flops / (pr["ms"] * 1e-3 / nl) / 1e12
-            out.update({"bound": "alu", "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                        "frac": tf / FP64_TFLOPS,
-                        "peak_kind": "FP64 FMA pipe: 2 DFMA/clock/SM x 152 SMs x 2 flops x "
-                                     "2.07 GHz (unit counts and clock; ncu: this kernel keeps "
-                                     "the FP64 pipe 85 % busy)",
-                        "algorithmic_flops_per_launch": flops, "hbm": hbm})
+            alu = {"achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                   "frac": tf / FP64_TFLOPS,
+                   "peak_kind": "FP64 FMA pipe: 2 DFMA/clock/SM x 152 SMs x 2 flops x 2.07 GHz "
+                                "(unit counts and clock)",
+                   "algorithmic_flops_per_launch": flops}
+            if hbm["frac"] is not None and hbm["frac"] >= alu["frac"]:
+                out.update({"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit",
+                                                                   "frac", "peak_kind")},
+                            "alu": alu})
+            else:
+                out.update({"bound": "alu", **alu, "hbm": hbm})
         else:
             out.update({"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit",
                                                                "frac", "peak_kind")}})
@@ -560,7 +589,10 @@ def run_single(args, rank, world, local):
     info = s.solve(rtol=args.rtol, maxit=args.maxit, restart=args.restart, out=(xp, xT))[2]
     torch.cuda.synchronize()
     if rank == 0:
-        levels = {name: [[int(a), int(b)] for a, b in zip(*s.hierarchy_info(w))]
+        # per level: rows, entries, storage format (0 CSR, 1 ELL, 2 sliced
+        # ELL) and stored entries (padding included)
+        levels = {name: [[int(a), int(b), *s.level_storage(w, l)]
+                         for l, (a, b) in enumerate(zip(*s.hierarchy_info(w)))]
                   for w, name in ((0, "A_pp"), (1, "S"))}
         print(json.dumps({"single_step": f"{args.config} {shape}", "precision": args.precision,
                           "iters": info["iters"], "status": info["status"],

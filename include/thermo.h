@@ -138,6 +138,14 @@ typedef struct {
                     /* every level, measured faster on GB300 inside the graph  */
   int nu_line;      /* smoother_S = 2: line steps before and after, 1..8       */
                     /* (default 1)                                             */
+  int sell_rows;    /* CSR levels between the finest and the coarsest with at */
+                    /* least sell_rows rows keep a sliced-ELL copy of their   */
+                    /* operator (32-row slices, rows sorted by length within  */
+                    /* windows of 256, each slice padded to its longest row)  */
+                    /* for their l1-Jacobi sweeps and residuals, one thread   */
+                    /* per row; 0 (default): one wave of resident threads     */
+                    /* (SMs x maximum threads per SM); -1: never. The results */
+                    /* differ only in the order of the row sums               */
 } tp_precond_opts;
 
 typedef struct {
@@ -307,6 +315,14 @@ int  tp_amg_info(tp_amg* amg, int* nlevels, int* n, int* nnz, int max_levels);
 int  tp_amg_export_level(tp_amg* amg, int level, int* rowptr, int* col,
                          double* val, signed char* cf, signed char* strong,
                          int* P_nnz, int* P_rowptr, int* P_col, double* P_val);
+/* Storage of level `level`'s operator in its smoothing sweeps: format 0 CSR,
+ * 1 ELL (column-major, padded to the longest row), 2 sliced ELL (see
+ * tp_precond_opts.sell_rows); stored = entries held, padding included (CSR:
+ * nnz). Host-only (no device work); TP_ESTATE before a build, TP_EINVAL for
+ * a level out of range. tp_level_storage: a context hierarchy (which = 0
+ * A_pp, 1 Schur). */
+int  tp_amg_level_storage(tp_amg* amg, int level, int* format, long long* stored);
+int  tp_level_storage(tp_ctx* ctx, int which, int level, int* format, long long* stored);
 /* Same introspection for a context hierarchy (which = 0 A_pp, 1 Schur). */
 int  tp_export_level(tp_ctx* ctx, int which, int level, int* rowptr, int* col,
                      double* val, signed char* cf, signed char* strong,

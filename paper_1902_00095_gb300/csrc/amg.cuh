@@ -41,6 +41,7 @@ struct AmgOpts {
   int max_pmis_rounds = 64;
   int pmax = 0;          // interpolation truncation (0 = off)
   int tail_rows = 0;      // coarse levels with at most this many rows: one cluster kernel (0 off)
+  int sell_rows = 0;      // sliced-ELL copy from this many rows (0: one wave of threads, -1 off)
   // vertical-line smoothing of the finest level: the level is the grid of
   // line_nxy columns x line_nz layers (cell c + line_nxy k); nu_line line
   // steps x <- x + T^-1 (b - A x) before and after the coarse correction,
@@ -130,6 +131,19 @@ struct Level {
   int* ell_col = nullptr;
   double* ell_val = nullptr;
   float* ell_valf = nullptr;
+  // sliced-ELL copy of A for long-row levels below the finest: rows sorted by
+  // length (descending) within windows of kSellWindow rows, slices of 32
+  // consecutive sorted rows padded to the slice's longest row, entry k of
+  // slot t of slice s at sell_ptr[s] + 32 k + t (padding: column = the row
+  // itself, value 0; slots past n: column 0). sell_perm[slot] = the row of a
+  // slot (-1 past n).
+  int sell_slices = 0;
+  long long sell_entries = 0;  // stored slots, padding included
+  int* sell_ptr = nullptr;
+  int* sell_perm = nullptr;
+  int* sell_col = nullptr;
+  double* sell_val = nullptr;
+  float* sell_valf = nullptr;
   // vertical-line smoother (finest level only): per cell the coefficient of
   // the cell below (l), 1 / m and u / m of the Thomas factorisation of the
   // column's tridiagonal part (FP64, FP32 copies in the FP32 hierarchy)
@@ -138,6 +152,7 @@ struct Level {
 };
 
 constexpr int kEllMaxW = 8;
+constexpr int kSellWindow = 256;
 
 class Hierarchy {
  public:

@@ -19,6 +19,7 @@ namespace {
 constexpr signed char kC = 1, kF = -1, kU = 0;
 
 int setup_sms();
+long long resident_threads();
 
 // index of key in a[lo, hi) (ascending), or -1
 __device__ __forceinline__ int find_in(const int* __restrict__ a, int lo, int hi, int key) {
@@ -1471,6 +1472,64 @@ void line_setup(Level& v, int nxy, int nz, Pool& pool, bool f32, int* err, bool 
   TP_LAUNCH_CHECK();
 }
 
+// -------------------------------------------------------- sliced-ELL copy
+// One block per window of kSellWindow rows: the rows sorted by descending
+// length (ties by ascending row) with a block bitonic sort; slice widths
+// are the lengths of each slice's first (longest) row.
+__global__ void __launch_bounds__(kSellWindow) k_sell_perm(int n, const int* __restrict__ rp,
+                                                           int* __restrict__ perm,
+                                                           int* __restrict__ width32) {
+  __shared__ unsigned long long key[kSellWindow];
+  const int t = threadIdx.x;
+  const int r = blockIdx.x * kSellWindow + t;
+  unsigned long long k = ~0ull;  // slots past n sort last
+  if (r < n) {
+    const int len = rp[r + 1] - rp[r];
+    k = ((unsigned long long)(unsigned)(0x7fffffff - len) << 32) | (unsigned)r;
+  }
+  key[t] = k;
+  __syncthreads();
+  for (int size = 2; size <= kSellWindow; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int partner = t ^ stride;
+      if (partner > t) {
+        const bool up = (t & size) == 0;
+        const unsigned long long a = key[t], c = key[partner];
+        if ((a > c) == up) {
+          key[t] = c;
+          key[partner] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const unsigned long long kk = key[t];
+  const int row = kk == ~0ull ? -1 : (int)(kk & 0xffffffffu);
+  perm[r] = row;
+  if ((t & 31) == 0) width32[r >> 5] = row >= 0 ? 32 * (rp[row + 1] - rp[row]) : 0;
+}
+
+// slot t of slice s: the entries of its row, padded to the slice width
+__global__ void k_sell_fill(int nslots, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, const int* __restrict__ perm,
+                            const int* __restrict__ ptr, int* __restrict__ scol,
+                            double* __restrict__ sval, float* __restrict__ svalf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nslots) return;
+  const int sl = t >> 5, lane = t & 31;
+  const int row = perm[t];
+  const int w = (ptr[sl + 1] - ptr[sl]) >> 5;
+  const int e0 = row >= 0 ? rp[row] : 0, len = row >= 0 ? rp[row + 1] - e0 : 0;
+  for (int k = 0; k < w; ++k) {
+    const long long q = (long long)ptr[sl] + 32 * k + lane;
+    const bool has = k < len;
+    if (scol) scol[q] = has ? col[e0 + k] : (row >= 0 ? row : 0);
+    const double v = has ? val[e0 + k] : 0.0;
+    sval[q] = v;
+    if (svalf) svalf[q] = (float)v;
+  }
+}
+
 // --------------------------------------------------------------- ELL copy
 __global__ void k_max_row(int n, const int* __restrict__ rp, int* __restrict__ mx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1593,13 +1652,7 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ A, double* __restrict
 // entries, ran with one lane) 200.2 / 11.4 / 42.5; floors of 8 or 16
 // entries 186.5-188.8 / 11.4-11.5 / 41.5-42.4.
 int pick_lanes(const DevCSR& A) {
-  static const long long resident = []() {
-    int dev = 0, sms = 0, thr = 0;
-    TP_CUDA_TRY(cudaGetDevice(&dev));
-    TP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    TP_CUDA_TRY(cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
-    return (long long)sms * thr;
-  }();
+  const long long resident = resident_threads();
   const double avg = A.n > 0 ? (double)A.nnz / A.n : 1.0;
   int l = 1;
   while (l * 4.0 <= avg && l < 32) l *= 2;
@@ -1607,6 +1660,18 @@ int pick_lanes(const DevCSR& A) {
   while (lmin < 32 && avg / lmin > 12.0) lmin *= 2;
   while (l > lmin && (long long)A.n * l > 4 * resident) l /= 2;
   return l;
+}
+
+// threads resident on the whole device at full occupancy, once per process
+long long resident_threads() {
+  static const long long r = []() {
+    int dev = 0, sms = 0, thr = 0;
+    TP_CUDA_TRY(cudaGetDevice(&dev));
+    TP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TP_CUDA_TRY(cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    return (long long)sms * thr;
+  }();
+  return r;
 }
 
 // SM count of the current device, once per process (thread-safe)
@@ -2027,6 +2092,40 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
       k_to_ell<<<grid_for(n), kBlock, 0, s>>>(n, v.ell_w, v.A.rowptr, v.A.col, v.A.val,
                                               allocate ? v.ell_col : nullptr, v.ell_val,
                                               v.ell_valf);
+      TP_LAUNCH_CHECK();
+    }
+    // sliced-ELL copy of the large levels below the finest: one thread per
+    // row gives coalesced loads and no cross-lane reduction (the FP64 adds of
+    // a split row's reduction compete with its multiply-adds for the FP64
+    // pipe). It needs a full wave of resident threads: on smaller levels the
+    // lane-split CSR sweep fills the machine better. Measured FP64 / FP32
+    // solve times (ms) without it, with it from one wave and with it on every
+    // level of 4096 rows or more: 256x256x64 layered 169.9 / 116.6,
+    // 154.6 / 107.4, 166.0 / 111.7; 128^2x64 channel 41.9 / 26.3,
+    // 40.7 / 25.1, 49.7 / 28.5.
+    const long long sell_min = opts.sell_rows == 0 ? resident_threads() : opts.sell_rows;
+    if (allocate && opts.sell_rows >= 0 && l > 0 && v.ell_w == 0 && n >= sell_min &&
+        l + 1 < L.size()) {
+      const int windows = (n + kSellWindow - 1) / kSellWindow;
+      const int slices = windows * (kSellWindow / 32);
+      v.sell_perm = pool.alloc<int>((size_t)windows * kSellWindow);
+      int* w32 = scratch.alloc<int>(slices + 1);
+      k_sell_perm<<<windows, kSellWindow, 0, s>>>(n, v.A.rowptr, v.sell_perm, w32);
+      TP_LAUNCH_CHECK();
+      v.sell_ptr = pool.alloc<int>(slices + 1);
+      const long long tot = scan_exclusive(w32, v.sell_ptr, slices, scratch, s);
+      v.sell_col = pool.alloc<int>(tot + 1);
+      v.sell_val = pool.alloc<double>(tot + 1);
+      v.sell_valf = f32 ? pool.alloc<float>(tot + 1) : nullptr;
+      v.sell_slices = slices;
+      v.sell_entries = tot;
+    }
+    if (v.sell_slices > 0) {
+      const int nslots = v.sell_slices * 32;
+      k_sell_fill<<<grid_for(nslots), kBlock, 0, s>>>(nslots, v.A.rowptr, v.A.col, v.A.val,
+                                                     v.sell_perm, v.sell_ptr,
+                                                     allocate ? v.sell_col : nullptr, v.sell_val,
+                                                     v.sell_valf);
       TP_LAUNCH_CHECK();
     }
     if (allocate) {

@@ -94,6 +94,7 @@ tp::AmgOpts amg_opts(const tp_precond_opts& o) {
   a.precision = o.precision;
   a.pmax = o.pmax;
   a.tail_rows = o.tail_rows;
+  a.sell_rows = o.sell_rows;
   return a;
 }
 
@@ -117,6 +118,7 @@ void check_opts(const tp_precond_opts& o) {
     fail(TP_EINVAL, "bad Schur-hierarchy override");
   if (o.pmax < 0 || o.pmax > 16) fail(TP_EINVAL, "pmax must be in 0..16");
   if (o.tail_rows < 0) fail(TP_EINVAL, "tail_rows must be >= 0");
+  if (o.sell_rows < -1) fail(TP_EINVAL, "sell_rows must be >= -1");
 }
 
 }  // namespace
@@ -213,6 +215,7 @@ void tp_default_opts(tp_precond_opts* o) {
   o->smoother_S = 2;
   o->tail_rows = 0;
   o->nu_line = 1;
+  o->sell_rows = 0;
 }
 
 const char* tp_status_string(int st) {
@@ -613,6 +616,24 @@ static int hierarchy_info(tp::Hierarchy* h, int* nlevels, int* n, int* nnz, int 
   return TP_OK;
 }
 
+static int level_storage(tp::Hierarchy* h, int level, int* format, long long* stored) {
+  if (!h) return TP_ESTATE;
+  if (level < 0 || level >= (int)h->L.size()) return TP_EINVAL;
+  const tp::Level& v = h->L[level];
+  int f = 0;
+  long long e = v.A.nnz;
+  if (v.sell_slices > 0) {
+    f = 2;
+    e = v.sell_entries;
+  } else if (v.ell_w > 0) {
+    f = 1;
+    e = (long long)v.ell_w * v.A.n;
+  }
+  if (format) *format = f;
+  if (stored) *stored = e;
+  return TP_OK;
+}
+
 static int export_level(tp::Hierarchy* h, cudaStream_t s, int level, int* rowptr, int* col,
                         double* val, signed char* cf, signed char* strong, int* P_nnz,
                         int* P_rowptr, int* P_col, double* P_val) {
@@ -649,6 +670,11 @@ int tp_setup_timings(tp_ctx* c, int which, double* ms) {
   tp::Hierarchy* h = which == 0 ? c->hpp.get() : c->hS.get();
   for (int k = 0; k < 5; ++k) ms[k] = h->phase_ms[k];
   return TP_OK;
+}
+
+int tp_level_storage(tp_ctx* c, int which, int level, int* format, long long* stored) {
+  if (!c || (which != 0 && which != 1)) return TP_EINVAL;
+  return level_storage(which == 0 ? c->hpp.get() : c->hS.get(), level, format, stored);
 }
 
 int tp_hierarchy_info(tp_ctx* c, int which, int* nlevels, int* n, int* nnz, int max_levels) {
@@ -1018,6 +1044,11 @@ int tp_amg_vcycle(tp_amg* a, const double* b, double* x, int ptr_is_device) {
 int tp_amg_info(tp_amg* a, int* nlevels, int* n, int* nnz, int max_levels) {
   if (!a) return TP_EINVAL;
   return hierarchy_info(a->h.get(), nlevels, n, nnz, max_levels);
+}
+
+int tp_amg_level_storage(tp_amg* a, int level, int* format, long long* stored) {
+  if (!a) return TP_EINVAL;
+  return level_storage(a->h.get(), level, format, stored);
 }
 
 int tp_amg_export_level(tp_amg* a, int level, int* rowptr, int* col, double* val,

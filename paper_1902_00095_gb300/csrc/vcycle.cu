@@ -402,6 +402,159 @@ __global__ void __launch_bounds__(128) k_line_sweep(
   }
 }
 
+// Sliced-ELL forms (levels below the finest with long rows): one thread per
+// row in length-sorted order, one warp per 32-row slice, so a warp loads 32
+// consecutive entries at each step and its lanes idle only on the slice's
+// padding; a row's sum runs over its entries in CSR order. The row of each
+// slot, the slice extent and the first K entries are loaded before the
+// dependency wait.
+template <class TV>
+struct SellRow {
+  static constexpr int K = sizeof(TV) >= 8 ? 4 : 8;
+  int row = -1, q0 = 0, w = 0;
+  int c[K];
+  TV v[K];
+
+  __device__ __forceinline__ void load(int nslots, const int* __restrict__ ptr,
+                                       const int* __restrict__ perm, const int* __restrict__ col,
+                                       const TV* __restrict__ val, int t) {
+    if (t < nslots) {
+      const int sl = t >> 5;
+      row = perm[t];
+      q0 = ptr[sl] + (t & 31);
+      w = (ptr[sl + 1] - ptr[sl]) >> 5;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      c[k] = 0;
+      v[k] = TV(0);
+      if (k < w) {
+        c[k] = col[q0 + 32 * k];
+        v[k] = val[q0 + 32 * k];
+      }
+    }
+  }
+
+  // FP64: the next group's K entries are loaded while the current group's
+  // gathers are in flight (one DRAM round trip per group instead of two);
+  // FP32 rows hold 2K entries in the first group and keep the plain loop
+  // (measured faster there)
+  template <class TX>
+  __device__ __forceinline__ TV dot(const int* __restrict__ col, const TV* __restrict__ val,
+                                    const TX* __restrict__ x) const {
+    TV acc = TV(0);
+    if constexpr (sizeof(TV) >= 8) {
+      int cc[K];
+      TV vv[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        cc[k] = c[k];
+        vv[k] = v[k];
+      }
+      for (int k0 = 0; k0 < w; k0 += K) {
+        TV xv[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) xv[j] = (k0 + j < w) ? (TV)x[cc[j]] : TV(0);
+        int cn[K];
+        TV vn[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const int k = k0 + K + j;
+          cn[j] = 0;
+          vn[j] = TV(0);
+          if (k < w) {
+            cn[j] = col[q0 + 32 * k];
+            vn[j] = val[q0 + 32 * k];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+          if (k0 + j < w) acc += vv[j] * xv[j];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          cc[j] = cn[j];
+          vv[j] = vn[j];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (k < w) acc += v[k] * (TV)x[c[k]];
+      for (int k = K; k < w; ++k) acc += val[q0 + 32 * k] * (TV)x[col[q0 + 32 * k]];
+    }
+    return acc;
+  }
+};
+
+template <class TV, class TB, class TO>
+__global__ void __launch_bounds__(256) k_sell_jacobi(int nslots, const int* __restrict__ ptr,
+                                                     const int* __restrict__ perm,
+                                                     const int* __restrict__ col,
+                                                     const TV* __restrict__ val,
+                                                     const TV* __restrict__ dinv,
+                                                     const TB* __restrict__ b,
+                                                     const TV* __restrict__ xin,
+                                                     TO* __restrict__ xout) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  SellRow<TV> a;
+  a.load(nslots, ptr, perm, col, val, t);
+  const TV di = a.row >= 0 ? dinv[a.row] : TV(0);
+  pdl_wait();
+  pdl_trigger();
+  if (a.row < 0) return;
+  const TV xi = xin[a.row], bi = (TV)b[a.row];
+  const TV ax = a.dot(col, val, xin);
+  xout[a.row] = (TO)(xi + di * (bi - ax));
+}
+
+template <class TV, class TB>
+__global__ void __launch_bounds__(256) k_sell_residual(int nslots, const int* __restrict__ ptr,
+                                                       const int* __restrict__ perm,
+                                                       const int* __restrict__ col,
+                                                       const TV* __restrict__ val,
+                                                       const TB* __restrict__ b,
+                                                       const TV* __restrict__ x,
+                                                       TV* __restrict__ r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  SellRow<TV> a;
+  a.load(nslots, ptr, perm, col, val, t);
+  pdl_wait();
+  pdl_trigger();
+  if (a.row < 0) return;
+  const TV bi = (TV)b[a.row];
+  r[a.row] = bi - a.dot(col, val, x);
+}
+
+// two sweeps from a zero guess: x = d b + d (b - A d b)
+template <class TV, class TB>
+__global__ void __launch_bounds__(256) k_sell_jacobi2z(int nslots, const int* __restrict__ ptr,
+                                                       const int* __restrict__ perm,
+                                                       const int* __restrict__ col,
+                                                       const TV* __restrict__ val,
+                                                       const TV* __restrict__ dinv,
+                                                       const TB* __restrict__ b,
+                                                       TV* __restrict__ x, int first) {
+  if (first) pdl_wait();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  SellRow<TV> a;
+  a.load(nslots, ptr, perm, col, val, t);
+  const TV d = a.row >= 0 ? dinv[a.row] : TV(0);
+  pdl_wait();
+  pdl_trigger();
+  if (a.row < 0) return;
+  const TV bi = (TV)b[a.row];
+  TV acc = TV(0);
+  constexpr int K = SellRow<TV>::K;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (k < a.w) acc += a.v[k] * (dinv[a.c[k]] * (TV)b[a.c[k]]);
+  for (int k = K; k < a.w; ++k) {
+    const int j = col[a.q0 + 32 * k];
+    acc += val[a.q0 + 32 * k] * (dinv[j] * (TV)b[j]);
+  }
+  x[a.row] = d * bi + d * (bi - acc);
+}
+
 template <class TV, class TB, class TO>
 void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b, const TV* xin,
             TO* xout, cudaStream_t s) {
@@ -487,6 +640,7 @@ struct Vals {
 };
 template <>
 struct Vals<double> {
+  static const double* S(const Level& l) { return l.sell_val; }
   static const double* lo(const Level& l) { return l.line_lo; }
   static const double* minv(const Level& l) { return l.line_minv; }
   static const double* cp(const Level& l) { return l.line_cp; }
@@ -498,6 +652,7 @@ struct Vals<double> {
 };
 template <>
 struct Vals<float> {
+  static const float* S(const Level& l) { return l.sell_valf; }
   static const float* lo(const Level& l) { return l.line_lof; }
   static const float* minv(const Level& l) { return l.line_minvf; }
   static const float* cp(const Level& l) { return l.line_cpf; }
@@ -515,7 +670,11 @@ struct Vals<float> {
 template <class TV, class TB, class TO>
 void level_sweep(const Level& v, const TV* dinv, const TB* b, const TV* xin, TO* xout,
                  cudaStream_t s) {
-  if (v.ell_w > 0) {
+  if (v.sell_slices > 0) {
+    const int nslots = v.sell_slices * 32;
+    launch_pdl(k_sell_jacobi<TV, TB, TO>, grid_for(nslots), kBlock, s, nslots, v.sell_ptr,
+               v.sell_perm, v.sell_col, Vals<TV>::S(v), dinv, b, xin, xout);
+  } else if (v.ell_w > 0) {
     launch_pdl(k_jacobi_ell<TV, TB, TO>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
                Vals<TV>::E(v), dinv, b, xin, xout);
   } else {
@@ -525,7 +684,11 @@ void level_sweep(const Level& v, const TV* dinv, const TB* b, const TV* xin, TO*
 
 template <class TV, class TB>
 void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_t s) {
-  if (v.ell_w > 0) {
+  if (v.sell_slices > 0) {
+    const int nslots = v.sell_slices * 32;
+    launch_pdl(k_sell_residual<TV, TB>, grid_for(nslots), kBlock, s, nslots, v.sell_ptr,
+               v.sell_perm, v.sell_col, Vals<TV>::S(v), b, x, r);
+  } else if (v.ell_w > 0) {
     launch_pdl(k_residual_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
                Vals<TV>::E(v), b, x, r);
   } else {
@@ -537,7 +700,11 @@ void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_
 template <class TV, class TB>
 void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* x, int first,
                                 cudaStream_t s) {
-  if (v.ell_w > 0) {
+  if (v.sell_slices > 0) {
+    const int nslots = v.sell_slices * 32;
+    launch_pdl(k_sell_jacobi2z<TV, TB>, grid_for(nslots), kBlock, s, nslots, v.sell_ptr,
+               v.sell_perm, v.sell_col, Vals<TV>::S(v), dinv, b, x, first);
+  } else if (v.ell_w > 0) {
     launch_pdl(k_jacobi2z_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
                Vals<TV>::E(v), dinv, b, x, first);
   } else {

@@ -44,7 +44,8 @@ class PrecondOpts(C.Structure):
                 ("max_levels", C.c_int), ("coarse_size", C.c_int), ("seed", C.c_ulonglong),
                 ("use_graphs", C.c_int), ("interp_S", C.c_int), ("max_levels_S", C.c_int),
                 ("nu_S", C.c_int), ("pmax", C.c_int), ("smoother_S", C.c_int),
-                ("tail_rows", C.c_int), ("nu_line", C.c_int)]
+                ("tail_rows", C.c_int), ("nu_line", C.c_int),
+                ("sell_rows", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -121,6 +122,9 @@ SIGNATURES = {
                                              C.c_void_p, C.c_void_p]),
     "tp_amg_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "tp_amg_info": (C.c_int, [C.c_void_p, _ip, _ip, _ip, C.c_int]),
+    "tp_amg_level_storage": (C.c_int, [C.c_void_p, C.c_int, _ip, C.POINTER(C.c_longlong)]),
+    "tp_level_storage": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip,
+                                   C.POINTER(C.c_longlong)]),
     "tp_amg_export_level": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, _dp, _sp, _sp, _ip, _ip,
                                       _ip, _dp]),
 }
@@ -409,6 +413,14 @@ class Solver:
         return {"ms": ms.value, "bytes": by.value, "opc": opc.value,
                 "gbs": by.value / (ms.value * 1e-3) / 1e9 if ms.value > 0 else None}
 
+    def level_storage(self, which, level):
+        """(format, stored entries) of a level's operator: format 0 CSR,
+        1 ELL, 2 sliced ELL."""
+        f, e = C.c_int(), C.c_longlong()
+        _check(self._lib.tp_level_storage(self._h, which, level, C.byref(f), C.byref(e)),
+               "tp_level_storage")
+        return f.value, e.value
+
     def export_level(self, which, level):
         n, nnz = self.hierarchy_info(which)
         return _export_level(lambda *a: self._lib.tp_export_level(self._h, which, level, *a),
@@ -543,6 +555,14 @@ class AMG:
         _check(self._lib.tp_amg_info(self._h, C.byref(nl), n.ctypes.data_as(_ip),
                                      nnz.ctypes.data_as(_ip), 64), "tp_amg_info")
         return n[:nl.value].copy(), nnz[:nl.value].copy()
+
+    def level_storage(self, level):
+        """(format, stored entries) of a level's operator: format 0 CSR,
+        1 ELL, 2 sliced ELL."""
+        f, e = C.c_int(), C.c_longlong()
+        _check(self._lib.tp_amg_level_storage(self._h, level, C.byref(f), C.byref(e)),
+               "tp_amg_level_storage")
+        return f.value, e.value
 
     def export_level(self, level):
         n, nnz = self.info()

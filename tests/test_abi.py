@@ -40,6 +40,7 @@ def test_host_only_calls_need_no_gpu(lib):
     o = thermo.default_opts()
     assert o.interp == 1 and o.nu_pre == 3 and abs(o.theta - 0.25) < 1e-15
     assert o.nu_post == 4 and o.smoother_S == 2 and o.nu_line == 1 and o.nu_S == 1
+    assert o.sell_rows == 0
     assert lib.tp_status_string(-5) == b"AMG setup failed"
     assert lib.tp_status_string(1) == b"not converged"
 

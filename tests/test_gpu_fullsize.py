@@ -74,18 +74,22 @@ def errors(xp, xT, rp, rT):
         np.linalg.norm(xT - rT) / np.linalg.norm(rT)
 
 
-@pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("precision", [0, 1])
-def test_solution_matches_stored_oracle_reference(name, precision):
+@pytest.mark.parametrize("name,precision,sell_rows",
+                         [(n, p, 0) for n in CASES for p in (0, 1)]
+                         + [("layered64", 0, 1), ("layered64", 1, 1)])
+def test_solution_matches_stored_oracle_reference(name, precision, sell_rows):
+    """sell_rows 0: the default storage (sliced ELL from one wave of
+    resident threads); 1: every level between the finest and the coarsest
+    sliced."""
     prob = CASES[name]()
     rp, rT, oracle_iters = reference(name)
     s = thermo.Solver.from_problem(prob)
     s.assemble(prob["p_k"], prob["T_k"], prob["p_n"], prob["T_n"], prob["dt"])
-    s.build(precision=precision)
+    s.build(precision=precision, sell_rows=sell_rows)
     xp, xT, info = s.solve(rtol=1e-8, maxit=600)
     assert info["status"] == 0, info
     full, ep, eT = errors(xp, xT, rp, rT)
-    print(f"{name} precision {precision}: {info['iters']} its (oracle at 1e-13: "
+    print(f"{name} precision {precision} sell_rows {sell_rows}: {info['iters']} its (oracle at 1e-13: "
           f"{oracle_iters}), scaled {info['rel_res']:.2e}, unscaled "
           f"{info['rel_res_unscaled']:.2e}, error {full:.2e} (p {ep:.2e}, T {eT:.2e})")
     assert full <= 1e-6 and ep <= 1e-6, (full, ep, eT)

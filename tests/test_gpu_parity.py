@@ -180,6 +180,93 @@ def test_amg_hierarchy_is_bit_exact_at_46080_cells(which, interp):
     g.close()
 
 
+def _grid48():
+    prob = make_problem("tiny", shape=(48, 48, 20), seed=6)
+    p, T = perturbed_state(prob, seed=9)
+    prob["p_n"] = prob["p_n"] + 5e4
+    return prob, p, T
+
+
+@pytest.mark.parametrize("name,which,interp", [("mid", "App", 1), ("mid", "S", 0),
+                                               ("grid48", "App", 1), ("grid48", "S", 0)])
+def test_sliced_ell_vcycle_matches_oracle(name, which, interp):
+    """sell_rows = 1 stores every level between the finest and the coarsest
+    as sliced ELL (rows sorted by length within windows of 256 rows, 32-row
+    slices padded to their longest row, the last window ragged) and sweeps it
+    one thread per row: the V-cycle still agrees with the oracle's to
+    rounding in FP64, and with the CSR path's to FP32 rounding in the FP32
+    and FP32 + BF16 hierarchies. sell_rows = -1 keeps CSR everywhere."""
+    prob, p, T = _grid48() if name == "grid48" else problem(name)
+    osys, _, _, oS = okry.assemble(prob, p, T)
+    A = osys.App if which == "App" else oS
+    iname = "ext+i" if interp == 1 else "classical"
+    oh = oamg.setup(A, theta=0.25, seed=12345, coarse_size=64, interp=iname, pmax=4)
+    b = np.random.default_rng(6).standard_normal(A[0].size - 1)
+    xo = oamg.vcycle(oh, b, 0, 3, 4)
+    kw = dict(interp=interp, seed=12345, pmax=4, coarse_size=64)
+    for precision, tol in ((0, 1e-11), (1, 1e-5), (2, 1e-5)):
+        g1 = thermo.AMG(*A, precision=precision, sell_rows=1, **kw)
+        g0 = thermo.AMG(*A, precision=precision, sell_rows=-1, **kw)
+        n, nnz = g1.info()
+        assert len(n) >= 3
+        for l in range(len(n)):
+            f1, e1 = g1.level_storage(l)
+            f0, _ = g0.level_storage(l)
+            assert f0 != 2
+            if 0 < l < len(n) - 1 and f0 == 0:
+                assert f1 == 2, l
+                # every slice holds 32 rows; padding at most to the longest row
+                rows = np.diff(g1.export_level(l)["A"][0])
+                assert e1 % 32 == 0 and nnz[l] <= e1 <= 32 * rows.max() * (-(-n[l] // 32))
+            else:
+                assert f1 == f0, l
+        x1, x0 = g1.vcycle(b), g0.vcycle(b)
+        if precision == 0:
+            assert np.max(np.abs(x1 - xo)) <= tol * np.max(np.abs(xo))
+            assert np.max(np.abs(x1 - x0)) <= 1e-12 * np.max(np.abs(x0))
+        else:
+            assert np.max(np.abs(x1 - x0)) <= tol * np.max(np.abs(x0)), precision
+        g0.close()
+        g1.close()
+
+
+def _sliced_levels(s):
+    """Levels of both hierarchies stored as sliced ELL."""
+    return sum(s.level_storage(w, l)[0] == 2 for w in (0, 1)
+               for l in range(len(s.hierarchy_info(w)[0])))
+
+
+def test_sliced_ell_preconditioner_and_refresh():
+    """The block preconditioner with sliced-ELL levels in both hierarchies
+    applies the same operator as with CSR levels; Newton with structure reuse
+    (values of the sliced copies refilled in place) ends where Newton with a
+    fresh setup per iteration does."""
+    prob, p, T = problem("mid")
+    s, _, _ = assemble_both(prob, p, T)
+    rng = np.random.default_rng(8)
+    vp, vT = rng.standard_normal(s.N), rng.standard_normal(s.N)
+    z = {}
+    for sell in (1, -1):
+        s.build(seed=7, sell_rows=sell)
+        assert (_sliced_levels(s) > 0) == (sell == 1)
+        z[sell] = s.apply_preconditioner(vp, vT)
+    for a, b in zip(z[1], z[-1]):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    s.close()
+    prob = make_problem("tiny", shape=(20, 16, 14), seed=5, dt_days=0.5)
+    out = []
+    for reuse, sell in ((False, -1), (True, 1)):
+        s = gpu_solver(prob)
+        p, T, info = s.newton_step(prob["p_n"], prob["T_n"], prob["dt"], max_newton=2,
+                                   tol_f=0.0, tol_dx=0.0, rtol=1e-12, reuse=reuse, sell_rows=sell)
+        assert info["last_linear_status"] == 0
+        assert (_sliced_levels(s) > 0) == (sell == 1)
+        out.append((p, T))
+        s.close()
+    assert np.linalg.norm(out[0][0] - out[1][0]) <= 1e-8 * np.linalg.norm(out[0][0] - prob["p_n"])
+    assert np.linalg.norm(out[0][1] - out[1][1]) <= 1e-8 * np.linalg.norm(out[0][1] - prob["T_n"])
+
+
 @pytest.mark.parametrize("name,degree,nu", [("iid16", 2, 1), ("mid", 2, 2), ("ragged", 3, 1),
                                              ("iid16", 1, 2)])
 def test_chebyshev_vcycle_matches_oracle(name, degree, nu):
