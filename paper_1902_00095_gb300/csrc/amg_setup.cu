@@ -1230,12 +1230,49 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_rows_warp(
   }
 }
 
-// rows with ex >= kSpCap: one 256-thread block per row with kSpBig entries of
-// dynamic shared memory (products staged by warp 0, the bitonic sort shared
-// by all threads); rows beyond that are summed serially
+// rows with ex >= kSpCap: one 512-thread block per row (one block per SM)
+// with kSpBig products in dynamic shared memory. Every warp stages the
+// products of its share of row i of A (lanes over the row of B, coalesced)
+// at their canonical sequence positions; a block bitonic sort orders the
+// (column, position) keys; a block scan lists the column runs, and one
+// thread per run adds it up in sequence order. Rows beyond kSpBig are summed
+// serially.
 constexpr int kSpBig = 8192;
-constexpr int kSpBigThreads = 256;
-constexpr size_t kSpBigSmem = (size_t)kSpBig * (sizeof(unsigned long long) + sizeof(double));
+constexpr int kSpBigThreads = 512;
+constexpr int kSpBigWarps = kSpBigThreads / 32;
+constexpr size_t kSpBigSmem =
+    (size_t)kSpBig * (sizeof(unsigned long long) + sizeof(double)) + (kSpBig + 1) * sizeof(int);
+
+// exclusive scan of x over the block; *total = the block's sum. s_w holds
+// kSpBigWarps + 1 ints; the block must not touch it between calls without a
+// barrier (the function ends with one).
+__device__ __forceinline__ int block_scan_excl(int x, int* s_w, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int v = lane < kSpBigWarps ? s_w[lane] : 0;
+    int iv = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, iv, o);
+      if (lane >= o) iv += y;
+    }
+    if (lane < kSpBigWarps) s_w[lane] = iv - v;
+    if (lane == 31) s_w[kSpBigWarps] = iv;
+  }
+  __syncthreads();
+  const int r = s_w[warp] + incl - x;
+  *total = s_w[kSpBigWarps];
+  __syncthreads();
+  return r;
+}
 
 __global__ void __launch_bounds__(kSpBigThreads) k_spgemm_rows_big(
     int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
@@ -1246,6 +1283,10 @@ __global__ void __launch_bounds__(kSpBigThreads) k_spgemm_rows_big(
   extern __shared__ unsigned long long s_big[];
   unsigned long long* key = s_big;
   double* val = reinterpret_cast<double*>(s_big + kSpBig);
+  int* start = reinterpret_cast<int*>(val + kSpBig);
+  __shared__ int s_w[kSpBigWarps + 1];
+  __shared__ int s_ak[kSpBigThreads], s_aoff[kSpBigThreads];
+  __shared__ double s_aa[kSpBigThreads];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = counts[1];
   for (int t = blockIdx.x; t < count; t += gridDim.x) {
@@ -1258,46 +1299,49 @@ __global__ void __launch_bounds__(kSpBigThreads) k_spgemm_rows_big(
       __syncthreads();
       continue;
     }
-    // 1. products in canonical order (warp 0)
-    if (warp == 0) {
-      const int a0 = Arp[i], a1 = Arp[i + 1];
-      int base = 0;
-      for (int e0 = a0; e0 < a1; e0 += 32) {
-        const int e = e0 + lane;
-        int k = 0, len = 0;
-        if (e < a1) {
-          k = Acol[e];
-          len = Brp[k + 1] - Brp[k];
-        }
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (e < a1) {
-          const double a = Aval[e];
-          const int fb = Brp[k];
-          int pidx = base + incl - len;
-          for (int t = 0; t < len; ++t, ++pidx) {
-            key[pidx] = ((unsigned long long)(unsigned)Bcol[fb + t] << 32) | (unsigned)pidx;
-            val[pidx] = __dmul_rn(a, Bval[fb + t]);
-          }
-        }
-        base += total;
+    // 1. products at their canonical positions (entry e of row i of A, then
+    // the row of B in order), kSpBigThreads entries of A at a time
+    const int a0 = Arp[i], a1 = Arp[i + 1];
+    int base = 0;
+    for (int c0 = a0; c0 < a1; c0 += kSpBigThreads) {
+      const int e = c0 + tid;
+      int k = 0, len = 0;
+      double a = 0.0;
+      if (e < a1) {
+        k = Acol[e];
+        a = Aval[e];
+        len = Brp[k + 1] - Brp[k];
       }
+      int total = 0;
+      const int ex_off = block_scan_excl(len, s_w, &total);
+      s_ak[tid] = k;
+      s_aa[tid] = a;
+      s_aoff[tid] = base + ex_off;
+      __syncthreads();
+      const int nc = min(kSpBigThreads, a1 - c0);
+      for (int q = warp; q < nc; q += kSpBigWarps) {
+        const int kk = s_ak[q];
+        const double aq = s_aa[q];
+        const int fb = Brp[kk], fe = Brp[kk + 1];
+        const int pb = s_aoff[q] - fb;
+        for (int f = fb + lane; f < fe; f += 32) {
+          const int pidx = pb + f;
+          key[pidx] = ((unsigned long long)(unsigned)Bcol[f] << 32) | (unsigned)pidx;
+          val[pidx] = __dmul_rn(aq, Bval[f]);
+        }
+      }
+      base += total;
+      __syncthreads();
     }
     int P = 1;
     while (P < ex) P <<= 1;
-    __syncthreads();
     for (int q = ex + tid; q < P; q += kSpBigThreads) key[q] = ~0ull;
     __syncthreads();
     // 2. block bitonic sort
     for (int size = 2; size <= P; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int t = tid; t < (P >> 1); t += kSpBigThreads) {
-          const int lo = 2 * stride * (t / stride) + (t % stride);
+        for (int u = tid; u < (P >> 1); u += kSpBigThreads) {
+          const int lo = 2 * stride * (u / stride) + (u % stride);
           const int hi = lo + stride;
           const bool up = (lo & size) == 0;
           const unsigned long long x = key[lo], y = key[hi];
@@ -1309,33 +1353,28 @@ __global__ void __launch_bounds__(kSpBigThreads) k_spgemm_rows_big(
         __syncthreads();
       }
     }
-    // 3. runs summed in sequence order (warp 0)
-    if (warp == 0) {
-      int nrun = 0;
-      for (int q0 = 0; q0 < ex; q0 += 32) {
-        const int q = q0 + lane;
-        int start = 0;
-        if (q < ex) start = (q == 0) || ((key[q] >> 32) != (key[q - 1] >> 32));
-        int incl = start;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (start) {
-          const unsigned col = (unsigned)(key[q] >> 32);
-          double sum = 0.0;
-          for (int r = q; r < ex && (unsigned)(key[r] >> 32) == col; ++r)
-            sum = __dadd_rn(sum, val[(unsigned)(key[r] & 0xffffffffu)]);
-          const int rid = nrun + incl - 1;
-          cc[rid] = (int)col;
-          cv[rid] = sum;
-        }
-        nrun += total;
-      }
-      if (lane == 0) cnt[i] = nrun;
+    // 3. the start of every column run
+    int nrun = 0;
+    for (int q0 = 0; q0 < ex; q0 += kSpBigThreads) {
+      const int q = q0 + tid;
+      int st = 0;
+      if (q < ex) st = (q == 0) || ((key[q] >> 32) != (key[q - 1] >> 32));
+      int total = 0;
+      const int r = block_scan_excl(st, s_w, &total);
+      if (st) start[nrun + r] = q;
+      nrun += total;
     }
+    if (tid == 0) start[nrun] = ex;
+    __syncthreads();
+    // 4. one thread per run, summed in sequence order
+    for (int r = tid; r < nrun; r += kSpBigThreads) {
+      const int q0 = start[r], q1 = start[r + 1];
+      double sum = 0.0;
+      for (int q = q0; q < q1; ++q) sum = __dadd_rn(sum, val[(unsigned)(key[q] & 0xffffffffu)]);
+      cc[r] = (int)(key[q0] >> 32);
+      cv[r] = sum;
+    }
+    if (tid == 0) cnt[i] = nrun;
     __syncthreads();
   }
 }
