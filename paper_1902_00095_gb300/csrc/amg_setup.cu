@@ -299,6 +299,30 @@ __global__ void k_classical_count(int n, const int* __restrict__ rp, const int* 
   cnt[i] = c;
 }
 
+// sign class of a_kk for opposite(): 0 when a_kk is zero or NaN (never
+// opposite), 1 positive, 2 negative (one byte per entry in shared memory
+// instead of the value)
+__device__ __forceinline__ unsigned char sign_class(double d) {
+  const unsigned long long ud = (unsigned long long)__double_as_longlong(d);
+  const unsigned long long md = ud & 0x7fffffffffffffffull;
+  if (md == 0 || md > 0x7ff0000000000000ull) return 0;
+  return (unsigned char)(1 + (ud >> 63));
+}
+
+// opposite(a, d) with d given by its sign class
+__device__ __forceinline__ bool opposite_class(double a, unsigned char dc) {
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ma = ua & 0x7fffffffffffffffull;
+  return dc != 0 && ma != 0 && ma <= 0x7ff0000000000000ull &&
+         (unsigned)(ua >> 63) != (unsigned)(dc - 1);
+}
+
+// an FP64 value is non-zero (either sign, or NaN), tested on its bits: FP64
+// compares would take the FP64 pipe
+__device__ __forceinline__ bool nonzero_bits(double v) {
+  return ((unsigned long long)__double_as_longlong(v) << 1) != 0;
+}
+
 // rows longer than kClsShort are filled by a warp (k_classical_fill_warp)
 constexpr int kClsShort = 8;
 constexpr int kClsWarps = 4;
@@ -343,7 +367,7 @@ __global__ void k_classical_fill(int n, const int* __restrict__ rp, const int* _
       if (opposite(val[f], akk) && is_strong_c(rp, col, strong, state, i, m))
         s = __dadd_rn(s, val[f]);
     }
-    if (s == 0.0) {
+    if (!nonzero_bits(s)) {
       denom = __dadd_rn(denom, val[e]);
       continue;
     }
@@ -426,7 +450,7 @@ __global__ void __launch_bounds__(32 * kClsWarps) k_classical_fill_warp(
         }
         if (m == 0u) continue;
       }
-      if (sk == 0.0) {
+      if (!nonzero_bits(sk)) {
         denom = __dadd_rn(denom, val[e]);
         continue;
       }
@@ -672,7 +696,7 @@ __device__ void extpi_fill_row_serial(int i, const int* __restrict__ rp, const i
           has_ki = true;
         }
       }
-      if (s == 0.0) {
+      if (!nonzero_bits(s)) {
         denom = __dadd_rn(denom, val[e]);
       } else {
         const double t = __ddiv_rn(val[e], s);
@@ -722,9 +746,9 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
     const int* __restrict__ cidx, const int* __restrict__ off, const int* __restrict__ buf,
     const int* __restrict__ Prp, int* __restrict__ Pcol, double* __restrict__ Pval) {
   __shared__ double s_t[kFillWarps][kFillMaxE];
-  __shared__ double s_akk[kFillWarps][kFillMaxE];
   __shared__ double s_term[kFillWarps][kFillMaxE];
   __shared__ unsigned char s_flag[kFillWarps][kFillMaxE];
+  __shared__ unsigned char s_akc[kFillWarps][kFillMaxE];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kFillWarps + w;
   if (i >= n) return;
@@ -747,36 +771,38 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
   const int* set = buf + off[i];
   const int ns = p1 - p0;
   double* t = s_t[w];
-  double* akk_e = s_akk[w];
   double* term = s_term[w];
   unsigned char* flag = s_flag[w];
+  unsigned char* akc = s_akc[w];
   // flags: 0 skip (diagonal or interpolated directly), 1 lump a_ie into the
   // denominator, 3 strong F neighbour with t_k (term = t_k ahat_ki or 0)
   for (int e = r0 + lane; e < r1; e += 32) {
     const int q = e - r0;
     const int k = col[e];
-    unsigned char fl = 0;
-    double tk = 0.0, tm = 0.0, ak = 0.0;
+    unsigned char fl = 0, kc = 0;
+    double tk = 0.0, tm = 0.0;
     if (k == i) {
       fl = 0;
     } else if (strong[e] && state[k] != kC) {
-      ak = val[dpos[k]];
+      kc = sign_class(val[dpos[k]]);
       double sk = 0.0, aki = 0.0;
       bool has_ki = false;
       for (int f = rp[k]; f < rp[k + 1]; ++f) {
         const int m = col[f];
-        if ((m == i || find_in(set, 0, ns, m) >= 0) && opposite(val[f], ak)) sk = __dadd_rn(sk, val[f]);
+        const double v = val[f];
+        // the sign test first: it skips most of the set searches
+        if (opposite_class(v, kc) && (m == i || find_in(set, 0, ns, m) >= 0)) sk = __dadd_rn(sk, v);
         if (m == i) {
-          aki = val[f];
+          aki = v;
           has_ki = true;
         }
       }
-      if (sk == 0.0) {
+      if (!nonzero_bits(sk)) {
         fl = 1;
       } else {
         fl = 3;
         tk = __ddiv_rn(val[e], sk);
-        if (has_ki && opposite(aki, ak)) tm = __dmul_rn(tk, aki);
+        if (has_ki && opposite_class(aki, kc)) tm = __dmul_rn(tk, aki);
       }
     } else if (find_in(set, 0, ns, k) >= 0) {
       fl = 0;
@@ -786,7 +812,7 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
     flag[q] = fl;
     t[q] = tk;
     term[q] = tm;
-    akk_e[q] = ak;
+    akc[q] = kc;
   }
   __syncwarp();
   double denom = 0.0;
@@ -795,7 +821,7 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
     for (int e = r0; e < r1; ++e) {
       const int q = e - r0;
       if (flag[q] == 1) denom = __dadd_rn(denom, val[e]);
-      else if (flag[q] == 3 && term[q] != 0.0) denom = __dadd_rn(denom, term[q]);
+      else if (flag[q] == 3 && nonzero_bits(term[q])) denom = __dadd_rn(denom, term[q]);
     }
   }
   denom = __shfl_sync(0xffffffffu, denom, 0);
@@ -808,7 +834,7 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_extpi_fill_warp(
       if (flag[q] != 3) continue;
       const int k = col[e];
       const int f = find_in(col, rp[k], rp[k + 1], m);
-      if (f >= 0 && opposite(val[f], akk_e[q])) num = __dadd_rn(num, __dmul_rn(t[q], val[f]));
+      if (f >= 0 && opposite_class(val[f], akc[q])) num = __dadd_rn(num, __dmul_rn(t[q], val[f]));
     }
     Pcol[p0 + sl] = cidx[m];
     Pval[p0 + sl] = __ddiv_rn(-num, denom);
