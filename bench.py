@@ -76,7 +76,7 @@ def parse():
                          "library's 3 and 4)")
     ap.add_argument("--sell-rows", type=int, default=None,
                     help="minimum rows of a level's sliced-ELL copy (default: the library's "
-                         "one wave of resident threads; -1 never, 1 every level between the "
+                         "half a wave of resident threads; -1 never, 1 every level between the "
                          "finest and the coarsest)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--sequence", type=int, default=0,
@@ -249,7 +249,7 @@ def arm_config(recipe, shape, args, world, precision="fp64 plain S~_T"):
             "grid": [nx, ny, nz], "unknowns": n2,
             "rtol": args.rtol, "solver": precision,
             "nu": args.nu if args.nu is not None else [3, 4], "restart": args.restart,
-            "sell_rows": args.sell_rows if args.sell_rows is not None else "one wave",
+            "sell_rows": args.sell_rows if args.sell_rows is not None else "half a wave",
             "l2": "flushed (512 MB write) before every timed step; inputs > L2",
             "parallelism": f"replicas{world}"}
 

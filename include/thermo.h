@@ -143,9 +143,9 @@ typedef struct {
                     /* operator (32-row slices, rows sorted by length within  */
                     /* windows of 256, each slice padded to its longest row)  */
                     /* for their l1-Jacobi sweeps and residuals, one thread   */
-                    /* per row; 0 (default): one wave of resident threads     */
-                    /* (SMs x maximum threads per SM); -1: never. The results */
-                    /* differ only in the order of the row sums               */
+                    /* per row; 0 (default): half a wave of resident threads  */
+                    /* (SMs x maximum threads per SM / 2); -1: never. The     */
+                    /* results differ only in the order of the row sums       */
 } tp_precond_opts;
 
 typedef struct {

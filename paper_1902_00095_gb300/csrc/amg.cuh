@@ -41,7 +41,7 @@ struct AmgOpts {
   int max_pmis_rounds = 64;
   int pmax = 0;          // interpolation truncation (0 = off)
   int tail_rows = 0;      // coarse levels with at most this many rows: one cluster kernel (0 off)
-  int sell_rows = 0;      // sliced-ELL copy from this many rows (0: one wave of threads, -1 off)
+  int sell_rows = 0;      // sliced-ELL copy from this many rows (0: half a wave of threads, -1 off)
   // vertical-line smoothing of the finest level: the level is the grid of
   // line_nxy columns x line_nz layers (cell c + line_nxy k); nu_line line
   // steps x <- x + T^-1 (b - A x) before and after the coarse correction,

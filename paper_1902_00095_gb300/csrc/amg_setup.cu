@@ -2162,13 +2162,13 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
     // sliced-ELL copy of the large levels below the finest: one thread per
     // row gives coalesced loads and no cross-lane reduction (the FP64 adds of
     // a split row's reduction compete with its multiply-adds for the FP64
-    // pipe). It needs a full wave of resident threads: on smaller levels the
-    // lane-split CSR sweep fills the machine better. Measured FP64 / FP32
-    // solve times (ms) without it, with it from one wave and with it on every
-    // level of 4096 rows or more: 256x256x64 layered 169.9 / 116.6,
-    // 154.6 / 107.4, 166.0 / 111.7; 128^2x64 channel 41.9 / 26.3,
-    // 40.7 / 25.1, 49.7 / 28.5.
-    const long long sell_min = opts.sell_rows == 0 ? resident_threads() : opts.sell_rows;
+    // pipe). It needs about half a wave of resident threads: on smaller
+    // levels the lane-split CSR sweep fills the machine better. Measured FP64
+    // / FP32 solve times (ms) without it; from 262,144 rows; from 131,072 or
+    // 200,000 rows; on every level of 4096 rows or more: 256x256x64 layered
+    // 169.9 / 116.6, 154.6 / 107.4, 151.3 / 107.4, 166.0 / 111.7; 128^2x64
+    // channel 41.9 / 26.3, 40.7 / 25.1, 39.8 / 25.3, 49.7 / 28.5.
+    const long long sell_min = opts.sell_rows == 0 ? resident_threads() / 2 : opts.sell_rows;
     if (allocate && opts.sell_rows >= 0 && l > 0 && v.ell_w == 0 && n >= sell_min &&
         l + 1 < L.size()) {
       const int windows = (n + kSellWindow - 1) / kSellWindow;

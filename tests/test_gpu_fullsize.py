@@ -78,7 +78,7 @@ def errors(xp, xT, rp, rT):
                          [(n, p, 0) for n in CASES for p in (0, 1)]
                          + [("layered64", 0, 1), ("layered64", 1, 1)])
 def test_solution_matches_stored_oracle_reference(name, precision, sell_rows):
-    """sell_rows 0: the default storage (sliced ELL from one wave of
+    """sell_rows 0: the default storage (sliced ELL from half a wave of
     resident threads); 1: every level between the finest and the coarsest
     sliced."""
     prob = CASES[name]()
