@@ -82,6 +82,10 @@ def parse():
     ap.add_argument("--sequence", type=int, default=0,
                     help="run this many backward-Euler steps with Newton (e.g. on "
                          "layered256) instead of the single-system benchmark")
+    ap.add_argument("--adaptive-days", type=float, default=0.0,
+                    help="--sequence mode with adaptive steps instead: simulate this many days, "
+                         "steps sized for about 4 Newton iterations (Sec. 4), at most the "
+                         "recipe's step, starting from it")
     ap.add_argument("--max-newton", type=int, default=4,
                     help="Newton iterations per time step in --sequence mode")
     ap.add_argument("--max-cuts", type=int, default=3,
@@ -625,11 +629,23 @@ def run_sequence(args, rank, world, local):
         opts = thermo.default_opts(precision=args.precision, **nu_kw(args))
     d = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
     p, T = d(prob["p_n"]), d(prob["T_n"])
-    from paper_1902_00095_gb300.timestep import advance
+    from paper_1902_00095_gb300.timestep import advance, simulate
     steps = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(args.sequence):
+    if args.adaptive_days > 0:
+        p, T, rec = simulate(s, p, T, args.adaptive_days * 86400.0, prob["dt"], dt_max=prob["dt"],
+                             target=4, max_cuts=args.max_cuts, max_newton=args.max_newton,
+                             tol_f=1e-8, tol_dx=1e-8, rtol=args.rtol, maxit=args.maxit,
+                             restart=args.restart, reuse=True, opts=opts)
+        for r in rec:
+            steps.append({"t_days": r["t"] / 86400.0, "dt_days": r["dt"] / 86400.0,
+                          "accepted": r["accepted"], "status": r["status"],
+                          "newton_iters": r.get("newton_iters", 0),
+                          "linear_iters": r.get("linear_iters", 0),
+                          "line_search_halvings": r.get("line_search_halvings", 0),
+                          "t_ms": r.get("t_ms", 0.0)})
+    for k in range(0 if args.adaptive_days > 0 else args.sequence):
         p, T, rec = advance(s, p, T, prob["dt"], max_cuts=args.max_cuts,
                             max_newton=args.max_newton, tol_f=1e-8, tol_dx=1e-8, rtol=args.rtol,
                             maxit=args.maxit, restart=args.restart, reuse=True, opts=opts)
@@ -644,6 +660,33 @@ def run_sequence(args, rank, world, local):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if rank != 0:
+        return
+    if args.adaptive_days > 0:
+        acc = [r for r in steps if r["accepted"]]
+        nacc = max(1, len(acc))
+        print(json.dumps({
+            "metric": "simulated days per second (adaptive backward-Euler steps, Newton + "
+                      "block-preconditioned FGMRES)",
+            "value": args.adaptive_days / wall, "unit": "days/s", "n_gpus": world,
+            "higher_is_better": True,
+            "dtype": "f64+f32" if (args.sequence_variant or args.precision) else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.config}: {WORKLOAD[args.config]}, "
+                                   f"{args.adaptive_days:g} days, adaptive steps",
+                       "unknowns": 2 * N, "max_newton": args.max_newton,
+                       "max_cuts": args.max_cuts, "dt_max_days": prob["dt"] / 86400.0,
+                       "solver": "fp32 hierarchy + learned S~" if args.sequence_variant else
+                                 ("fp32 hierarchy" if args.precision else "fp64 plain")},
+            "wall_s": wall, "steps_accepted": len(acc), "solves": len(steps),
+            "all_converged": all(r["status"] == 0 for r in acc),
+            "newton_per_step": sum(r["newton_iters"] for r in steps) / nacc,
+            "linear_per_newton": sum(r["linear_iters"] for r in steps) /
+                                 max(1, sum(r["newton_iters"] for r in steps)),
+            "steps_detail": steps,
+            "learned": (dict(train, fallback=s.learned_status()) if train else None),
+            "final_T_range": [float(T.min()), float(T.max())],
+            "final_p_range": [float(p.min()), float(p.max())],
+        }), flush=True)
         return
     print(json.dumps({
         "metric": "backward-Euler steps (Newton + block-preconditioned FGMRES) per second",
@@ -731,7 +774,7 @@ def main():
         run_reference(args, rank, world)
     elif args.single:
         run_single(args, rank, world, local)
-    elif args.sequence > 0:
+    elif args.sequence > 0 or args.adaptive_days > 0:
         run_sequence(args, rank, world, local)
     elif args.scaling2d:
         run_scaling2d(args, rank, world, local)
