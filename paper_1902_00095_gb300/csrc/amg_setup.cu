@@ -1152,47 +1152,116 @@ __device__ void spgemm_row_hash(int i, int ex, int lane, int tcap, const int* __
   int bits = 5;
   while ((1 << bits) < 2 * ex && (1 << bits) < tcap) ++bits;
   const int cap = 1 << bits;
+  const unsigned below = (1u << lane) - 1u;
   for (int q = lane; q < cap; q += 32) hkey[q] = -1;
   __syncwarp();
-  // 1. accumulate in canonical order
+  // 1. accumulate in canonical order: every column's sum starts at 0.0 and
+  // takes its products in ascending e. Rows of fewer than kSpMid products
+  // whose rows of B are short (fewer than 16 products per entry of A on
+  // average, as in A P; measured faster there, slower on the rows of
+  // kSpMid-kSpCap products of R (A P)) take the
+  // next 32 products of the row in sequence order per step (entry e of row i
+  // of A, then the row of B): lanes claim their column's slot, and lanes of
+  // one step that share a column (at most one product per entry e, so lane
+  // order is entry order) are added by the lowest of them in lane order onto
+  // the sum of the earlier steps. Other rows take one entry of A per step,
+  // its row of B split over the lanes (distinct columns).
+  for (int q = lane; q < cap; q += 32) hval[q] = 0.0;
+  __syncwarp();
+  double* sprod = reinterpret_cast<double*>(skey);  // 32 staged products
   const int a0 = Arp[i], a1 = Arp[i + 1];
-  for (int e0 = a0; e0 < a1; e0 += 32) {
-    const int e = e0 + lane;
-    double a = 0.0;
-    int fb = 0, fe = 0;
-    if (e < a1) {
-      const int k = Acol[e];
-      a = Aval[e];
-      fb = Brp[k];
-      fe = Brp[k + 1];
-    }
-    const int ne = min(32, a1 - e0);
-    for (int t = 0; t < ne; ++t) {
-      const double at = __shfl_sync(0xffffffffu, a, t);
-      const int f0 = __shfl_sync(0xffffffffu, fb, t);
-      const int f1 = __shfl_sync(0xffffffffu, fe, t);
-      for (int f = f0 + lane; f < f1; f += 32) {
-        const int j = Bcol[f];
-        const double prod = __dmul_rn(at, Bval[f]);
-        unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - bits);
-        for (int probe = 0; probe < cap; ++probe) {
-          const int prev = atomicCAS(&hkey[h], -1, j);
-          if (prev == -1) {
-            hval[h] = __dadd_rn(0.0, prod);
-            break;
-          }
-          if (prev == j) {
-            hval[h] = __dadd_rn(hval[h], prod);
-            break;
-          }
-          h = (h + 1) & (unsigned)(cap - 1);
-        }
+  if (tcap <= kSpMid && ex < 16 * (a1 - a0)) {
+    for (int e0 = a0; e0 < a1; e0 += 32) {
+      const int e = e0 + lane;
+      double a = 0.0;
+      int fb = 0, len = 0;
+      if (e < a1) {
+        const int k = Acol[e];
+        a = Aval[e];
+        fb = Brp[k];
+        len = Brp[k + 1] - fb;
       }
-      __syncwarp();
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int excl = incl - len;
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      for (int p0 = 0; p0 < total; p0 += 32) {
+        const int p = p0 + lane;
+        // the entry holding position p: the last lane with excl <= p
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = lo + step;
+          if (__shfl_sync(0xffffffffu, excl, cand) <= p) lo = cand;
+        }
+        const int se = __shfl_sync(0xffffffffu, excl, lo);
+        const int sf = __shfl_sync(0xffffffffu, fb, lo);
+        const double sa = __shfl_sync(0xffffffffu, a, lo);
+        int slot = -1 - lane;  // distinct for lanes without a product
+        double prod = 0.0;
+        if (p < total) {
+          const int f = sf + (p - se);
+          const int j = Bcol[f];
+          prod = __dmul_rn(sa, Bval[f]);
+          unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - bits);
+          for (int probe = 0; probe < cap; ++probe) {
+            const int prev = atomicCAS(&hkey[h], -1, j);
+            if (prev == -1 || prev == j) {
+              slot = (int)h;
+              break;
+            }
+            h = (h + 1) & (unsigned)(cap - 1);
+          }
+        }
+        sprod[lane] = prod;
+        const unsigned grp = __match_any_sync(0xffffffffu, slot);
+        __syncwarp();
+        if (slot >= 0 && (grp & below) == 0) {
+          double v = hval[slot];
+          for (unsigned g = grp; g; g &= g - 1u) v = __dadd_rn(v, sprod[__ffs(g) - 1]);
+          hval[slot] = v;
+        }
+        __syncwarp();
+      }
+    }
+  } else {
+    for (int e0 = a0; e0 < a1; e0 += 32) {
+      const int e = e0 + lane;
+      double a = 0.0;
+      int fb = 0, fe = 0;
+      if (e < a1) {
+        const int k = Acol[e];
+        a = Aval[e];
+        fb = Brp[k];
+        fe = Brp[k + 1];
+      }
+      const int ne = min(32, a1 - e0);
+      for (int t = 0; t < ne; ++t) {
+        const double at = __shfl_sync(0xffffffffu, a, t);
+        const int f0 = __shfl_sync(0xffffffffu, fb, t);
+        const int f1 = __shfl_sync(0xffffffffu, fe, t);
+        for (int f = f0 + lane; f < f1; f += 32) {
+          const int j = Bcol[f];
+          const double prod = __dmul_rn(at, Bval[f]);
+          unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - bits);
+          for (int probe = 0; probe < cap; ++probe) {
+            const int prev = atomicCAS(&hkey[h], -1, j);
+            if (prev == -1 || prev == j) {
+              hval[h] = __dadd_rn(hval[h], prod);
+              break;
+            }
+            h = (h + 1) & (unsigned)(cap - 1);
+          }
+        }
+        __syncwarp();
+      }
     }
   }
   // 2. compact the occupied slots as (column << 32 | slot) keys
-  const unsigned below = (1u << lane) - 1u;
   int d = 0;
   for (int q0 = 0; q0 < cap; q0 += 32) {
     const int q = q0 + lane;
