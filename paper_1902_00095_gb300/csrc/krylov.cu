@@ -62,12 +62,22 @@ __global__ void k_precond_in(int N, const double* __restrict__ vp, const double*
                              double* __restrict__ bT_s, double* __restrict__ hin) {
   pdl_wait();
   pdl_trigger();
+  // 1 / s_m and 1 / s_e once per block: an FP64 instruction occupies the
+  // GB300's FP64 pipe for the whole warp however few lanes run it, so a
+  // division per element (or per warp) would bound the kernel
+  __shared__ double rs[2];
+  if (threadIdx.x == 0) {
+    rs[0] = 1.0 / scales[0];
+    rs[1] = 1.0 / scales[1];
+  }
+  __syncthreads();
+  const double r0 = rs[0], r1 = rs[1];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const double a = vp[i] / scales[0];
+  const double a = vp[i] * r0;
   bp_s[i] = a;
   hin[i] = a;
-  bT_s[i] = vT[i] / scales[1];
+  bT_s[i] = vT[i] * r1;
 }
 
 // out = b - A x over the shared 7-point pattern (steps 2 and 4 of Sec. 3.2)
@@ -266,7 +276,8 @@ __global__ void __launch_bounds__(256) k_arnoldi(int j, int ldh, double* __restr
   Hj[j + 1] = 0.0;
   g[j + 1] = -sn[j] * g[j];
   g[j] = cs[j] * g[j];
-  *hn_out = hn;
+  hn_out[0] = hn;
+  hn_out[1] = 1.0 / hn;  // for k_normalize: one division here, not one per element
   est[0] = fabs(g[j + 1]);
   est[1] = hn;
   est[2] = den;
@@ -289,20 +300,24 @@ __global__ void __launch_bounds__(256) k_reorth_gate(int count, const double* __
   *gate = (2.0 * tot < tot + hh || !(tot == tot)) ? 1 : 0;
 }
 
+// v = w / h_{j+1,j} as w * (1 / h_{j+1,j}) (hn[1], written by k_arnoldi): an
+// FP64 division per element would keep the GB300's FP64 pipe busy for
+// longer than the vector takes to stream
 __global__ void k_normalize(long long n2, const double* __restrict__ w,
                             const double* __restrict__ hn, double* __restrict__ v) {
   pdl_wait();
   pdl_trigger();
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n2) v[i] = w[i] / hn[0];
+  if (i < n2) v[i] = w[i] * hn[1];
 }
 
-// first basis vector and Givens right-hand side: v0 = r / beta, g = beta e1
+// first basis vector and Givens right-hand side: v0 = r / beta (as r times
+// beta[1] = 1 / beta, from k_sqrt_inplace), g = beta e1
 __global__ void k_start_cycle(long long n2, const double* __restrict__ r,
                               const double* __restrict__ beta, double* __restrict__ v0,
                               double* __restrict__ g, int restart) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n2) v0[i] = r[i] / beta[0];
+  if (i < n2) v0[i] = r[i] * beta[1];
   if (i <= restart) g[i] = (i == 0) ? beta[0] : 0.0;
 }
 
@@ -407,8 +422,12 @@ __global__ void k_sum_to(const double* __restrict__ partials, int B, double* __r
   block_sum_store(v, out);
 }
 
+// v[0] = sqrt(v[0]), v[1] = 1 / v[0] (for k_start_cycle)
 __global__ void k_sqrt_inplace(double* v) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) v[0] = sqrt(v[0]);
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    v[0] = sqrt(v[0]);
+    v[1] = 1.0 / v[0];
+  }
 }
 
 void mdot_all(long long n2, const double* V, long long stride, int count, const double* w,
