@@ -277,6 +277,8 @@ int tp_create(tp_ctx** out, const tp_grid* grid, const tp_fluid* fluid, void* cu
                      &c->Tn, &c->rho, &c->lam, &c->lam_p, &c->lam_T, &c->Rm, &c->Re, &c->bp_s,
                      &c->bT_s, &c->tmpN, &c->io0, &c->io1, &c->io2, &c->io3})
     *f = P.alloc<double>(n);
+  c->Tf3 = P.alloc<double>(3 * n);
+  c->Tc3 = P.alloc<double>(3 * n);
   c->bval = P.alloc<double>(4 * nnzb);
   c->Sval = P.alloc<double>(nnzb);
   c->App = P.alloc<double>(nnzb);
@@ -352,6 +354,7 @@ int tp_set_fields(tp_ctx* c, const double* Kx, const double* Ky, const double* K
   if (f & 1) return TP_ENONFINITE;
   if (f & 2) return TP_EINVAL;
   tp::launch_mix_conductivity(c->N, c->phi, c->kTr, c->fluid, c->kT, s);
+  tp::launch_face_trans(c->grid, c->Kx, c->Ky, c->Kz, c->kT, c->Tf3, c->Tc3, s);
   TP_CUDA_TRY(cudaStreamSynchronize(s));
   c->fields_set = true;
   c->assembled = false;
@@ -1078,9 +1081,9 @@ int assemble_device(tp_ctx* c, double dt) {
   }
   if (read_flags(flags, s)) return TP_ENONFINITE;
   launch_cell_props(c->N, c->p, c->T, c->fluid, c->rho, c->lam, c->lam_p, c->lam_T, s);
-  launch_assemble(c->grid, c->fluid, c->rowptr, c->dpos, c->Kx, c->Ky, c->Kz, c->phi, c->kT, c->p,
-                  c->T, c->pn, c->Tn, c->rho, c->lam, c->lam_p, c->lam_T, dt, c->bval, c->Sval,
-                  c->Rm, c->Re, s);
+  launch_assemble(c->grid, c->fluid, c->rowptr, c->dpos, c->Tf3, c->Tc3, c->phi, c->p, c->T,
+                  c->pn, c->Tn, c->rho, c->lam, c->lam_p, c->lam_T, dt, c->bval, c->Sval, c->Rm,
+                  c->Re, s);
   launch_wells(c->grid, c->fluid, c->wells, c->dpos, c->Kx, c->Ky, c->p, c->T, c->rho, c->lam,
                c->lam_p, c->lam_T, c->bval, c->Sval, c->Rm, c->Re, s);
   TP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
@@ -1105,7 +1108,7 @@ void learned_features(tp_ctx* c) {
   launch_extract_blocks(c->nnzb, c->bval, c->App, c->ApT, c->ATp, c->ATT, s);
   launch_equation_scales(c->N, c->dpos, c->App, c->ATT, c->tmpN, c->partials, c->nparts,
                          c->scales, s);
-  launch_features(c->grid, c->fluid, c->dpos, c->Kx, c->Ky, c->Kz, c->phi, c->kT, c->p, c->T,
+  launch_features(c->grid, c->fluid, c->dpos, c->Tf3, c->Tc3, c->phi, c->p, c->T,
                   c->rho, c->lam, c->lam_p, c->lam_T, c->bval, c->Sval, c->scales, c->dt_last,
                   c->feat, s);
 }

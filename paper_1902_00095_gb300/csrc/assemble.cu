@@ -101,9 +101,43 @@ struct Face {
   bool up_lo;
 };
 
+// Face transmissibilities (Sec. 2.2, Eq. Fm, Eq. Fe): for cell lo and each
+// axis towards its upper neighbour hi, T_f = |e|/d 2 K_lo K_hi / (K_lo + K_hi)
+// and Tc_f the same for the mixture conductivity; axis-major [3][N], 0 on the
+// last layer of an axis. They depend on the fields only, so they are computed
+// when the fields are set, not at every assembly (two FP64 divisions per face
+// and side there).
+__global__ void k_face_trans(GridDev g, const double* __restrict__ Kx,
+                             const double* __restrict__ Ky, const double* __restrict__ Kz,
+                             const double* __restrict__ kT, double* __restrict__ Tf,
+                             double* __restrict__ Tc) {
+  const int N = g.nx * g.ny * g.nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int nxy = g.nx * g.ny;
+  const int x = i % g.nx, y = (i / g.nx) % g.ny, z = i / nxy;
+  const bool has[3] = {x < g.nx - 1, y < g.ny - 1, z < g.nz - 1};
+  const int step[3] = {1, g.nx, nxy};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    double tf = 0.0, tc = 0.0;
+    if (has[ax]) {
+      const int hi = i + step[ax];
+      const double area_over_d = ax == 0 ? (g.dy * g.dz) / g.dx
+                                 : ax == 1 ? (g.dx * g.dz) / g.dy
+                                           : (g.dx * g.dy) / g.dz;
+      const double* K = ax == 0 ? Kx : ax == 1 ? Ky : Kz;
+      const double Klo = K[i], Khi = K[hi], kTlo = kT[i], kThi = kT[hi];
+      tf = area_over_d * __ddiv_rn(__dmul_rn(__dmul_rn(2.0, Klo), Khi), __dadd_rn(Klo, Khi));
+      tc = area_over_d * __ddiv_rn(__dmul_rn(__dmul_rn(2.0, kTlo), kThi), __dadd_rn(kTlo, kThi));
+    }
+    Tf[(long long)ax * N + i] = tf;
+    Tc[(long long)ax * N + i] = tc;
+  }
+}
+
 // Face between cells lo < hi (quantities oriented lo -> hi).
-__device__ __forceinline__ void face_terms(int lo, int hi, double area_over_d, double Klo,
-                                           double Khi, double kTlo, double kThi, double dzf,
+__device__ __forceinline__ void face_terms(int lo, int hi, double Tf, double Tcf, double dzf,
                                            const double* __restrict__ p,
                                            const double* __restrict__ T,
                                            const double* __restrict__ rho,
@@ -111,8 +145,6 @@ __device__ __forceinline__ void face_terms(int lo, int hi, double area_over_d, d
                                            const double* __restrict__ lam_p,
                                            const double* __restrict__ lam_T,
                                            const FluidDev& f, double g, Face& o) {
-  const double Tf = area_over_d * __ddiv_rn(__dmul_rn(__dmul_rn(2.0, Klo), Khi), __dadd_rn(Klo, Khi));
-  const double Tcf = area_over_d * __ddiv_rn(__dmul_rn(__dmul_rn(2.0, kTlo), kThi), __dadd_rn(kTlo, kThi));
   const double rlo = rho[lo], rhi = rho[hi];
   const double rhobar = __dmul_rn(0.5, __dadd_rn(rlo, rhi));
   const double dphi = __dsub_rn(__dsub_rn(p[lo], p[hi]), __dmul_rn(__dmul_rn(rhobar, g), dzf));
@@ -143,8 +175,8 @@ __device__ __forceinline__ void face_terms(int lo, int hi, double area_over_d, d
 
 __global__ void __launch_bounds__(128) k_assemble(
     GridDev g, FluidDev f, const int* __restrict__ rowptr, const int* __restrict__ dpos,
-    const double* __restrict__ Kx, const double* __restrict__ Ky, const double* __restrict__ Kz,
-    const double* __restrict__ phi, const double* __restrict__ kT, const double* __restrict__ p,
+    const double* __restrict__ Tf3, const double* __restrict__ Tc3,
+    const double* __restrict__ phi, const double* __restrict__ p,
     const double* __restrict__ T, const double* __restrict__ p_n, const double* __restrict__ T_n,
     const double* __restrict__ rho, const double* __restrict__ lam,
     const double* __restrict__ lam_p, const double* __restrict__ lam_T, double dt,
@@ -170,14 +202,10 @@ __global__ void __launch_bounds__(128) k_assemble(
     const int j = nb[q];
     const int lo = i < j ? i : j, hi = i < j ? j : i;
     const int ax = axis[q];
-    const double area_over_d = ax == 0 ? (g.dy * g.dz) / g.dx
-                               : ax == 1 ? (g.dx * g.dz) / g.dy
-                                         : (g.dx * g.dy) / g.dz;
-    const double* K = ax == 0 ? Kx : ax == 1 ? Ky : Kz;
+    const long long fidx = (long long)ax * N + lo;
     const double dzf = ax == 2 ? g.dz : 0.0;
     Face o;
-    face_terms(lo, hi, area_over_d, K[lo], K[hi], kT[lo], kT[hi], dzf, p, T, rho, lam, lam_p,
-               lam_T, f, g.g, o);
+    face_terms(lo, hi, Tf3[fidx], Tc3[fidx], dzf, p, T, rho, lam, lam_p, lam_T, f, g.g, o);
     double* blk = bval + 4ll * e;
     if (i == lo) {
       rm += o.F;
@@ -208,13 +236,14 @@ __global__ void __launch_bounds__(128) k_assemble(
   const double rn = density(p_n[i], T_n[i], f);
   const double Tn = T_n[i];
   const double rock = (1.0 - ph) * f.rho_r * f.cr;
-  rm += V * ph * (r - rn) / dt;
-  re += V * (ph * f.cv * (r * Ti - rn * Tn) + rock * (Ti - Tn)) / dt;
-  J[0] += V * ph * rho_p / dt;
-  J[1] += V * ph * rho_T / dt;
-  J[2] += V * ph * f.cv * rho_p * Ti / dt;
-  J[3] += V * (ph * f.cv * (rho_T * Ti + r) + rock) / dt;
-  Sd += V * (ph * f.cv * r + rock) / dt;
+  const double vdt = V / dt;  // one FP64 division per cell, not seven
+  rm += vdt * (ph * (r - rn));
+  re += vdt * (ph * f.cv * (r * Ti - rn * Tn) + rock * (Ti - Tn));
+  J[0] += vdt * (ph * rho_p);
+  J[1] += vdt * (ph * rho_T);
+  J[2] += vdt * (ph * f.cv * rho_p * Ti);
+  J[3] += vdt * (ph * f.cv * (rho_T * Ti + r) + rock);
+  Sd += vdt * (ph * f.cv * r + rock);
   double* blk = bval + 4ll * d;
   blk[0] = J[0]; blk[1] = J[1]; blk[2] = J[2]; blk[3] = J[3];
   Sval[d] = Sd;
@@ -323,9 +352,9 @@ __global__ void k_scales(int N, const double* __restrict__ sums, double* __restr
 // diagonal, 20 log10(A_pp,ii s_m), 21 log10(A_TT,ii s_e),
 // 22 (A_TT,ii - S~_ii) / S~_ii, 23 accumulation / S~_ii.
 __global__ void __launch_bounds__(128) k_features(
-    GridDev g, FluidDev f, const int* __restrict__ dpos, const double* __restrict__ Kx,
-    const double* __restrict__ Ky, const double* __restrict__ Kz, const double* __restrict__ phi,
-    const double* __restrict__ kT, const double* __restrict__ p, const double* __restrict__ T,
+    GridDev g, FluidDev f, const int* __restrict__ dpos, const double* __restrict__ Tf3,
+    const double* __restrict__ Tc3, const double* __restrict__ phi,
+    const double* __restrict__ p, const double* __restrict__ T,
     const double* __restrict__ rho, const double* __restrict__ lam,
     const double* __restrict__ lam_p, const double* __restrict__ lam_T,
     const double* __restrict__ bval, const double* __restrict__ Sval,
@@ -352,16 +381,11 @@ __global__ void __launch_bounds__(128) k_features(
     const int j = nb[q];
     const int lo = i < j ? i : j, hi = i < j ? j : i;
     const int ax = axis[q];
-    const double area_over_d = ax == 0 ? (g.dy * g.dz) / g.dx
-                               : ax == 1 ? (g.dx * g.dz) / g.dy
-                                         : (g.dx * g.dy) / g.dz;
-    const double* K = ax == 0 ? Kx : ax == 1 ? Ky : Kz;
+    const long long fidx = (long long)ax * N + lo;
     const double dzf = ax == 2 ? g.dz : 0.0;
     Face o;
-    face_terms(lo, hi, area_over_d, K[lo], K[hi], kT[lo], kT[hi], dzf, p, T, rho, lam, lam_p,
-               lam_T, f, g.g, o);
-    const double Tf = area_over_d * (2.0 * K[lo] * K[hi] / (K[lo] + K[hi]));
-    out[q] = (float)log10(Tf / 1e-12);
+    face_terms(lo, hi, Tf3[fidx], Tc3[fidx], dzf, p, T, rho, lam, lam_p, lam_T, f, g.g, o);
+    out[q] = (float)log10(Tf3[fidx] / 1e-12);
     out[6 + q] = (float)log10(o.Tcf);
     out[13 + q] = (float)((i == lo ? o.adv : -o.adv) / Sd);
   }
@@ -378,15 +402,14 @@ __global__ void __launch_bounds__(128) k_features(
 
 }  // namespace
 
-void launch_features(const GridDev& g, const FluidDev& f, const int* dpos, const double* Kx,
-                     const double* Ky, const double* Kz, const double* phi, const double* kT,
-                     const double* p, const double* T, const double* rho, const double* lam,
-                     const double* lam_p, const double* lam_T, const double* bval,
-                     const double* Sval, const double* scales, double dt, float* F,
-                     cudaStream_t s) {
+void launch_features(const GridDev& g, const FluidDev& f, const int* dpos, const double* Tf3,
+                     const double* Tc3, const double* phi, const double* p, const double* T,
+                     const double* rho, const double* lam, const double* lam_p,
+                     const double* lam_T, const double* bval, const double* Sval,
+                     const double* scales, double dt, float* F, cudaStream_t s) {
   int N = g.nx * g.ny * g.nz;
-  k_features<<<grid_for(N, 128), 128, 0, s>>>(g, f, dpos, Kx, Ky, Kz, phi, kT, p, T, rho, lam,
-                                              lam_p, lam_T, bval, Sval, scales, dt, F);
+  k_features<<<grid_for(N, 128), 128, 0, s>>>(g, f, dpos, Tf3, Tc3, phi, p, T, rho, lam, lam_p,
+                                              lam_T, bval, Sval, scales, dt, F);
   TP_LAUNCH_CHECK();
 }
 
@@ -408,16 +431,21 @@ void launch_cell_props(int N, const double* p, const double* T, const FluidDev& 
   TP_LAUNCH_CHECK();
 }
 
+void launch_face_trans(const GridDev& g, const double* Kx, const double* Ky, const double* Kz,
+                       const double* kT, double* Tf3, double* Tc3, cudaStream_t s) {
+  const int N = g.nx * g.ny * g.nz;
+  k_face_trans<<<grid_for(N), kBlock, 0, s>>>(g, Kx, Ky, Kz, kT, Tf3, Tc3);
+  TP_LAUNCH_CHECK();
+}
+
 void launch_assemble(const GridDev& g, const FluidDev& f, const int* rowptr, const int* dpos,
-                     const double* Kx, const double* Ky, const double* Kz, const double* phi,
-                     const double* kT, const double* p, const double* T, const double* p_n,
-                     const double* T_n, const double* rho, const double* lam, const double* lam_p,
-                     const double* lam_T, double dt, double* bval, double* Sval, double* Rm,
-                     double* Re, cudaStream_t s) {
+                     const double* Tf3, const double* Tc3, const double* phi, const double* p,
+                     const double* T, const double* p_n, const double* T_n, const double* rho,
+                     const double* lam, const double* lam_p, const double* lam_T, double dt,
+                     double* bval, double* Sval, double* Rm, double* Re, cudaStream_t s) {
   int N = g.nx * g.ny * g.nz;
-  k_assemble<<<grid_for(N, 128), 128, 0, s>>>(g, f, rowptr, dpos, Kx, Ky, Kz, phi, kT, p, T, p_n,
-                                               T_n, rho, lam, lam_p, lam_T, dt, bval, Sval, Rm,
-                                               Re);
+  k_assemble<<<grid_for(N, 128), 128, 0, s>>>(g, f, rowptr, dpos, Tf3, Tc3, phi, p, T, p_n, T_n,
+                                               rho, lam, lam_p, lam_T, dt, bval, Sval, Rm, Re);
   TP_LAUNCH_CHECK();
 }
 

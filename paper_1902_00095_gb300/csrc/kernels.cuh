@@ -34,13 +34,16 @@ void launch_mix_conductivity(int N, const double* phi, const double* kTr, const 
                              double* kT, cudaStream_t s);
 void launch_cell_props(int N, const double* p, const double* T, const FluidDev& f,
                        double* rho, double* lam, double* lam_p, double* lam_T, cudaStream_t s);
+// Face transmissibilities T_f, Tc_f per cell and axis towards the upper
+// neighbour ([3][N], axis-major), from the fields.
+void launch_face_trans(const GridDev& g, const double* Kx, const double* Ky, const double* Kz,
+                       const double* kT, double* Tf3, double* Tc3, cudaStream_t s);
 // Jacobian (block-CSR, 4 doubles per block), residual and S~_T values.
 void launch_assemble(const GridDev& g, const FluidDev& f, const int* rowptr, const int* dpos,
-                     const double* Kx, const double* Ky, const double* Kz, const double* phi,
-                     const double* kT, const double* p, const double* T, const double* p_n,
-                     const double* T_n, const double* rho, const double* lam, const double* lam_p,
-                     const double* lam_T, double dt, double* bval, double* Sval, double* Rm,
-                     double* Re, cudaStream_t s);
+                     const double* Tf3, const double* Tc3, const double* phi, const double* p,
+                     const double* T, const double* p_n, const double* T_n, const double* rho,
+                     const double* lam, const double* lam_p, const double* lam_T, double dt,
+                     double* bval, double* Sval, double* Rm, double* Re, cudaStream_t s);
 void launch_wells(const GridDev& g, const FluidDev& f, const WellsDev& w, const int* dpos,
                   const double* Kx, const double* Ky, const double* p, const double* T,
                   const double* rho, const double* lam, const double* lam_p, const double* lam_T,
@@ -53,12 +56,11 @@ void launch_equation_scales(int N, const int* dpos, const double* App, const dou
                             cudaStream_t s);
 
 // learned-correction features (FP32 [N][24]) at the last assembly
-void launch_features(const GridDev& g, const FluidDev& f, const int* dpos, const double* Kx,
-                     const double* Ky, const double* Kz, const double* phi, const double* kT,
-                     const double* p, const double* T, const double* rho, const double* lam,
-                     const double* lam_p, const double* lam_T, const double* bval,
-                     const double* Sval, const double* scales, double dt, float* F,
-                     cudaStream_t s);
+void launch_features(const GridDev& g, const FluidDev& f, const int* dpos, const double* Tf3,
+                     const double* Tc3, const double* phi, const double* p, const double* T,
+                     const double* rho, const double* lam, const double* lam_p,
+                     const double* lam_T, const double* bval, const double* Sval,
+                     const double* scales, double dt, float* F, cudaStream_t s);
 
 // ------------------------------------------------------ sparse kernels
 // y = D A x for the block matrix; D = diag(scales[0], scales[1]) or identity

@@ -20,6 +20,7 @@ struct tp_ctx {
   // cell fields
   double *Kx = nullptr, *Ky = nullptr, *Kz = nullptr, *phi = nullptr, *kTr = nullptr,
          *kT = nullptr;
+  double *Tf3 = nullptr, *Tc3 = nullptr;  // face transmissibilities [3][N] (from the fields)
   bool fields_set = false;
   // wells
   tp::WellsDev wells;
