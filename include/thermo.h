@@ -317,8 +317,10 @@ int  tp_amg_export_level(tp_amg* amg, int level, int* rowptr, int* col,
                          int* P_nnz, int* P_rowptr, int* P_col, double* P_val);
 /* Storage of level `level`'s operator in its smoothing sweeps: format 0 CSR,
  * 1 ELL (column-major, padded to the longest row), 2 sliced ELL (see
- * tp_precond_opts.sell_rows); stored = entries held, padding included (CSR:
- * nnz). Host-only (no device work); TP_ESTATE before a build, TP_EINVAL for
+ * tp_precond_opts.sell_rows), 3 ELL by grid direction (the finest level of a
+ * context hierarchy whose operator is the grid's 7-point pattern, every grid
+ * extent >= 2: 7 values per row, 0 where a neighbour is absent, no column
+ * indices); stored = entries held, padding included (CSR: nnz). Host-only (no device work); TP_ESTATE before a build, TP_EINVAL for
  * a level out of range. tp_level_storage: a context hierarchy (which = 0
  * A_pp, 1 Schur). */
 int  tp_amg_level_storage(tp_amg* amg, int level, int* format, long long* stored);

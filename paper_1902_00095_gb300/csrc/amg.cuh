@@ -47,6 +47,10 @@ struct AmgOpts {
   // steps x <- x + T^-1 (b - A x) before and after the coarse correction,
   // T the tridiagonal part of A along each column (off when line_nz < 2)
   int line_nxy = 0, line_nz = 0, nu_line = 1;
+  // level 0 is the 7-point operator of this nx x ny x nz grid (cell x + nx y
+  // + nx ny z; 0: unknown): with every extent >= 2 its ELL copy is stored by
+  // grid direction, without column indices
+  int grid_nx = 0, grid_ny = 0, grid_nz = 0;
 };
 
 // Device descriptor of one level for the cluster kernel of the V-cycle's
@@ -128,6 +132,11 @@ struct Level {
   // ELL copy of A (slot-major: entry k of row i at k * n + i, padded with
   // column i and value 0) for levels whose rows have at most kEllMaxW entries
   int ell_w = 0;
+  // ell_nxy > 0: the slots are the grid directions (offsets -nxy, -nx, -1,
+  // 0, +1, +nx, +nxy: ascending columns), value 0 where a neighbour is
+  // absent, and ell_col is null: a slot's column is the row plus its offset,
+  // clamped to [0, n) (an absent neighbour's slot adds an exact zero)
+  int ell_nx = 0, ell_nxy = 0;
   int* ell_col = nullptr;
   double* ell_val = nullptr;
   float* ell_valf = nullptr;

@@ -1686,6 +1686,35 @@ __global__ void k_to_ell(int n, int w, const int* __restrict__ rp, const int* __
   }
 }
 
+// ELL copy by grid direction (the finest level of a grid's 7-point operator):
+// slot k of row i holds the entry at column i + (-nxy, -nx, -1, 0, +1, +nx,
+// +nxy)[k], 0 where the row has none; an entry at any other offset sets
+// bit 32 of *err (the level is not the grid's 7-point pattern)
+__global__ void k_to_stencil(int n, int nx, int nxy, const int* __restrict__ rp,
+                             const int* __restrict__ col, const double* __restrict__ val,
+                             double* __restrict__ eval, float* __restrict__ evalf,
+                             int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int d = col[e] - i;
+    const int k = d == -nxy ? 0 : d == -nx ? 1 : d == -1 ? 2 : d == 0 ? 3 : d == 1 ? 4
+                : d == nx ? 5 : d == nxy ? 6 : -1;
+    if (k < 0) {
+      atomicOr(err, 32);
+      continue;
+    }
+    v[k] = val[e];
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const long long q = (long long)k * n + i;
+    eval[q] = v[k];
+    if (evalf) evalf[q] = (float)v[k];
+  }
+}
+
 // ------------------------------------------------------------ coarsest level
 __global__ void k_to_dense(int n, const int* __restrict__ rp, const int* __restrict__ col,
                            const double* __restrict__ val, double* __restrict__ D) {
@@ -2209,8 +2238,20 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
         }
       }
     }
-    // ELL copy for short-row levels (the 7-point finest level)
-    if (allocate && n >= 4096) {
+    // ELL copy for short-row levels (the 7-point finest level); by grid
+    // direction when the level is a known grid's 7-point operator (the column
+    // indices, a third of an FP64 sweep's matrix bytes and half an FP32
+    // one's, are then implicit)
+    const bool stencil = l == 0 && opts.grid_nx > 1 && opts.grid_ny > 1 && opts.grid_nz > 1 &&
+                         (long long)opts.grid_nx * opts.grid_ny * opts.grid_nz == n;
+    if (allocate && stencil) {
+      v.ell_w = 7;
+      v.ell_nx = opts.grid_nx;
+      v.ell_nxy = opts.grid_nx * opts.grid_ny;
+      v.ell_col = nullptr;
+      v.ell_val = pool.alloc<double>((size_t)7 * n);
+      v.ell_valf = f32 ? pool.alloc<float>((size_t)7 * n) : nullptr;
+    } else if (allocate && n >= 4096) {
       TP_CUDA_TRY(cudaMemsetAsync(err + 1, 0, sizeof(int), s));
       k_max_row<<<grid_for(n), kBlock, 0, s>>>(n, v.A.rowptr, err + 1);
       TP_LAUNCH_CHECK();
@@ -2222,7 +2263,11 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
         v.ell_valf = f32 ? pool.alloc<float>((size_t)w * n) : nullptr;
       }
     }
-    if (v.ell_w > 0) {
+    if (v.ell_w > 0 && v.ell_nxy > 0) {
+      k_to_stencil<<<grid_for(n), kBlock, 0, s>>>(n, v.ell_nx, v.ell_nxy, v.A.rowptr, v.A.col,
+                                                  v.A.val, v.ell_val, v.ell_valf, err);
+      TP_LAUNCH_CHECK();
+    } else if (v.ell_w > 0) {
       k_to_ell<<<grid_for(n), kBlock, 0, s>>>(n, v.ell_w, v.A.rowptr, v.A.col, v.A.val,
                                               allocate ? v.ell_col : nullptr, v.ell_val,
                                               v.ell_valf);
@@ -2286,6 +2331,7 @@ void Hierarchy::finish_levels(cudaStream_t s, bool allocate) {
     if (e & 16)
       fail(TP_SETUP_FAILED,
            "AMG: vertical-line smoother needs both vertical neighbours and non-zero pivots");
+    if (e & 32) fail(TP_SETUP_FAILED, "AMG: level 0 is not the grid's 7-point pattern");
   }
   // coarsest level: explicit inverse by Gauss-Jordan with partial pivoting
   Level& cl = L.back();

@@ -629,7 +629,7 @@ static int level_storage(tp::Hierarchy* h, int level, int* format, long long* st
     f = 2;
     e = v.sell_entries;
   } else if (v.ell_w > 0) {
-    f = 1;
+    f = v.ell_nxy > 0 ? 3 : 1;
     e = (long long)v.ell_w * v.A.n;
   }
   if (format) *format = f;
@@ -1212,7 +1212,13 @@ void build_device(tp_ctx* c, const tp_precond_opts& o) {
   if (!c->hpp) c->hpp.reset(new Hierarchy());
   if (!c->hS) c->hS.reset(new Hierarchy());
   AmgOpts ao = amg_opts(o);
+  // A_pp (and S~ except S~_diag, whose pattern has 25 points) is the grid's
+  // 7-point operator: its finest ELL copy is stored by grid direction
+  ao.grid_nx = c->grid.nx;
+  ao.grid_ny = c->grid.ny;
+  ao.grid_nz = c->grid.nz;
   AmgOpts aS = ao;
+  if (o.schur == 3) aS.grid_nx = aS.grid_ny = aS.grid_nz = 0;
   if (o.interp_S >= 0) aS.interp = o.interp_S;
   if (o.max_levels_S > 0) aS.max_levels = o.max_levels_S;
   if (o.nu_S > 0) aS.nu_pre = aS.nu_post = o.nu_S;

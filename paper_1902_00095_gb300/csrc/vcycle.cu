@@ -171,22 +171,33 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
   if (valid && lane == 0) x[row] = d * bi + d * (bi - acc);
 }
 
+// column of slot k of row `row` in an ELL copy by grid direction (offsets
+// -nxy, -nx, -1, 0, +1, +nx, +nxy), clamped to [0, n): an absent neighbour's
+// slot holds 0, so any column in range adds an exact zero
+__device__ __forceinline__ int stencil_col(int k, int row, int n, int nx, int nxy) {
+  const int o = k == 0 ? -nxy : k == 1 ? -nx : k == 2 ? -1 : k == 3 ? 0 : k == 4 ? 1
+              : k == 5 ? nx : nxy;
+  const int c = row + o;
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
 // ELL forms (slot-major, one thread per row, coalesced over rows); a row's
-// slots are held in registers, loaded before the dependency wait
+// slots are held in registers, loaded before the dependency wait. ecol null:
+// the slots are the grid directions of an nx x ny x nz grid (nxy = nx ny)
 template <class TV>
 struct EllRow {
   int c[kEllMaxW];
   TV v[kEllMaxW];
 
   __device__ __forceinline__ void load(int n, int w, const int* __restrict__ ecol,
-                                       const TV* __restrict__ eval, int row) {
+                                       const TV* __restrict__ eval, int row, int nx, int nxy) {
 #pragma unroll
     for (int k = 0; k < kEllMaxW; ++k) {
       c[k] = 0;
       v[k] = TV(0);
       if (k < w) {
         const long long q = (long long)k * n + row;
-        c[k] = ecol[q];
+        c[k] = ecol ? ecol[q] : stencil_col(k, row, n, nx, nxy);
         v[k] = eval[q];
       }
     }
@@ -203,7 +214,7 @@ struct EllRow {
 };
 
 template <class TV, class TB, class TO>
-__global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __restrict__ ecol,
+__global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __restrict__ ecol, int snx, int snxy,
                                                     const TV* __restrict__ eval,
                                                     const TV* __restrict__ dinv,
                                                     const TB* __restrict__ b,
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __r
   EllRow<TV> a;
   TV di = TV(0);
   if (row < n) {
-    a.load(n, w, ecol, eval, row);
+    a.load(n, w, ecol, eval, row, snx, snxy);
     di = dinv[row];
   }
   pdl_wait();
@@ -225,14 +236,14 @@ __global__ void __launch_bounds__(256) k_jacobi_ell(int n, int w, const int* __r
 }
 
 template <class TV, class TB>
-__global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* __restrict__ ecol,
+__global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* __restrict__ ecol, int snx, int snxy,
                                                       const TV* __restrict__ eval,
                                                       const TB* __restrict__ b,
                                                       const TV* __restrict__ x,
                                                       TV* __restrict__ r) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   EllRow<TV> a;
-  if (row < n) a.load(n, w, ecol, eval, row);
+  if (row < n) a.load(n, w, ecol, eval, row, snx, snxy);
   pdl_wait();
   pdl_trigger();
   if (row >= n) return;
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* _
 }
 
 template <class TV, class TB>
-__global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* __restrict__ ecol,
+__global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* __restrict__ ecol, int snx, int snxy,
                                                       const TV* __restrict__ eval,
                                                       const TV* __restrict__ dinv,
                                                       const TB* __restrict__ b,
@@ -253,7 +264,7 @@ __global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* _
 #pragma unroll
   for (int k = 0; k < kEllMaxW; ++k) dj[k] = TV(0);
   if (row < n) {
-    a.load(n, w, ecol, eval, row);
+    a.load(n, w, ecol, eval, row, snx, snxy);
     d = dinv[row];
 #pragma unroll
     for (int k = 0; k < kEllMaxW; ++k)
@@ -361,7 +372,8 @@ __global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __rest
 // so every plane is read and written coalesced.
 template <class TV, class TB, class TO>
 __global__ void __launch_bounds__(128) k_line_sweep(
-    int nxy, int nz, int n, int ell_w, const int* __restrict__ ecol, const TV* __restrict__ eval,
+    int nxy, int nz, int n, int ell_w, const int* __restrict__ ecol, int snx, int snxy,
+    const TV* __restrict__ eval,
     const int* __restrict__ rp, const int* __restrict__ col, const TV* __restrict__ val,
     const TV* __restrict__ lo, const TV* __restrict__ minv, const TV* __restrict__ cp,
     const TB* __restrict__ b, const TV* __restrict__ xin, TO* __restrict__ xout) {
@@ -381,7 +393,7 @@ __global__ void __launch_bounds__(128) k_line_sweep(
         for (int q = 0; q < kEllMaxW; ++q)
           if (q < ell_w) {
             const long long e = (long long)q * n + i;
-            ax += eval[e] * xin[ecol[e]];
+            ax += eval[e] * xin[ecol ? ecol[e] : stencil_col(q, i, n, snx, snxy)];
           }
       } else {
         for (int e = rp[i]; e < rp[i + 1]; ++e) ax += val[e] * xin[col[e]];
@@ -676,7 +688,7 @@ void level_sweep(const Level& v, const TV* dinv, const TB* b, const TV* xin, TO*
                v.sell_perm, v.sell_col, Vals<TV>::S(v), dinv, b, xin, xout);
   } else if (v.ell_w > 0) {
     launch_pdl(k_jacobi_ell<TV, TB, TO>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
-               Vals<TV>::E(v), dinv, b, xin, xout);
+               v.ell_nx, v.ell_nxy, Vals<TV>::E(v), dinv, b, xin, xout);
   } else {
     jacobi<TV, TB, TO>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, xin, xout, s);
   }
@@ -690,7 +702,7 @@ void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_
                v.sell_perm, v.sell_col, Vals<TV>::S(v), b, x, r);
   } else if (v.ell_w > 0) {
     launch_pdl(k_residual_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
-               Vals<TV>::E(v), b, x, r);
+               v.ell_nx, v.ell_nxy, Vals<TV>::E(v), b, x, r);
   } else {
     residual<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), b, x, r, s);
   }
@@ -706,7 +718,7 @@ void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV*
                v.sell_perm, v.sell_col, Vals<TV>::S(v), dinv, b, x, first);
   } else if (v.ell_w > 0) {
     launch_pdl(k_jacobi2z_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
-               Vals<TV>::E(v), dinv, b, x, first);
+               v.ell_nx, v.ell_nxy, Vals<TV>::E(v), dinv, b, x, first);
   } else {
     jacobi2z<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, x, first, s);
   }
@@ -714,9 +726,13 @@ void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV*
 
 // algorithmic bytes of one sweep x_out = x_in + dinv (b - A x_in)
 template <class TV, class TB, class TO>
-double sweep_bytes(const DevCSR& A) {
-  return (double)A.nnz * (sizeof(TV) + sizeof(int)) + 4.0 * (A.n + 1) +
-         (double)A.n * (2 * sizeof(TV) + sizeof(TB) + sizeof(TO));
+double sweep_bytes(const Level& v) {
+  const DevCSR& A = v.A;
+  // an ELL copy by grid direction holds values only (7 per row, zeros at
+  // the boundary included): its column indices are implicit
+  const double amat = v.ell_nxy > 0 ? (double)A.n * v.ell_w * sizeof(TV)
+                                    : (double)A.nnz * (sizeof(TV) + sizeof(int)) + 4.0 * (A.n + 1);
+  return amat + (double)A.n * (2 * sizeof(TV) + sizeof(TB) + sizeof(TO));
 }
 
 template <class TV, class TB, class TO>
@@ -724,7 +740,7 @@ void sweep_probed(Probe* pr, const Level& v, const TV* dinv, const TB* b, const 
                   TO* xout, cudaStream_t s) {
   if (pr) pr->before(s);
   level_sweep<TV, TB, TO>(v, dinv, b, xin, xout, s);
-  if (pr) pr->after(s, sweep_bytes<TV, TB, TO>(v.A));
+  if (pr) pr->after(s, sweep_bytes<TV, TB, TO>(v));
 }
 
 // smoother selection of one V-cycle: 0 l1-Jacobi, 1 Chebyshev of `degree`;
@@ -746,7 +762,7 @@ double line_bytes(const Level& v, bool from_zero) {
   double bytes = n * (3 * sizeof(TV) + sizeof(TB) + sizeof(TO));
   if (!from_zero) {
     bytes += n * sizeof(TV);
-    if (v.ell_w > 0) bytes += n * v.ell_w * (sizeof(int) + sizeof(TV));
+    if (v.ell_w > 0) bytes += n * v.ell_w * ((v.ell_nxy > 0 ? 0 : sizeof(int)) + sizeof(TV));
     else bytes += (double)v.A.nnz * (sizeof(int) + sizeof(TV)) + 4.0 * (n + 1);
   }
   return bytes;
@@ -760,7 +776,8 @@ void line_step(const Smooth& sm, const Level& v, const TB* b, const TV* xin, TO*
   const int threads = sm.line_nxy >= 152 * 128 * 2 ? 128 : 32;
   const int grid = (sm.line_nxy + threads - 1) / threads;
   launch_pdl(k_line_sweep<TV, TB, TO>, grid, threads, s, sm.line_nxy, sm.line_nz, v.A.n,
-             v.ell_w, v.ell_col, Vals<TV>::E(v), v.A.rowptr, v.A.col, Vals<TV>::A(v),
+             v.ell_w, v.ell_col, v.ell_nx, v.ell_nxy, Vals<TV>::E(v), v.A.rowptr, v.A.col,
+             Vals<TV>::A(v),
              Vals<TV>::lo(v), Vals<TV>::minv(v), Vals<TV>::cp(v), b, xin, xout);
 }
 
@@ -873,12 +890,12 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   for (int k = 1; k <= nu_post; ++k) {
     if (k == nu_post && final_out) {
       smooth_step<TV, TB, TO>(sm, nullptr, v, dinv, b, cur, final_out, s);
-      span_bytes += sweep_bytes<TV, TB, TO>(v.A);
+      span_bytes += sweep_bytes<TV, TB, TO>(v);
       if (span) span->after(s, span_bytes, nu_post);
       return nullptr;
     }
     smooth_step<TV, TB, TV>(sm, nullptr, v, dinv, b, cur, oth, s);
-    span_bytes += sweep_bytes<TV, TB, TV>(v.A);
+    span_bytes += sweep_bytes<TV, TB, TV>(v);
     std::swap(cur, oth);
   }
   if (span) span->after(s, span_bytes, nu_post);
@@ -927,7 +944,7 @@ double Hierarchy::vcycle_bytes() const {
       total += n * n * 8.0 + n * sb + n * (l == 0 ? 8.0 : sv);
       break;
     }
-    const double amat = v.ell_w > 0 ? n * v.ell_w * (4.0 + sv)
+    const double amat = v.ell_w > 0 ? n * v.ell_w * ((v.ell_nxy > 0 ? 0.0 : 4.0) + sv)
                                     : (double)v.A.nnz * (4.0 + sv) + 4.0 * (n + 1);
     const double sweep = amat + n * (sv /*dinv*/ + sb + sv /*x in*/ + sv /*x out*/);
     const double resid = amat + n * (sb + sv + sv);
