@@ -230,6 +230,27 @@ def test_sliced_ell_vcycle_matches_oracle(name, which, interp):
         g1.close()
 
 
+def test_finest_level_storage_by_grid_direction():
+    """A context hierarchy whose finest operator is the grid's 7-point
+    pattern (every extent >= 2) keeps its ELL copy by grid direction: format
+    3, 7 values per row, no column indices, at any size. S~_diag (25
+    points) and grids with an extent of 1 do not (ELL with columns from 4096
+    rows, CSR below: these grids have fewer)."""
+    for name, want in (("ragged", 3), ("thin", 0)):
+        prob, p, T = problem(name)
+        s, _, _ = assemble_both(prob, p, T)
+        s.build(seed=7)
+        for which in (0, 1):
+            f, e = s.level_storage(which, 0)
+            assert f == want, (name, which, f)
+            if f == 3:
+                assert e == 7 * s.N
+        if name == "ragged":
+            s.build(seed=7, schur=3)
+            assert s.level_storage(0, 0)[0] == 3 and s.level_storage(1, 0)[0] == 0
+        s.close()
+
+
 def _sliced_levels(s):
     """Levels of both hierarchies stored as sliced ELL."""
     return sum(s.level_storage(w, l)[0] == 2 for w in (0, 1)
