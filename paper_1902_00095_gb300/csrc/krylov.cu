@@ -444,6 +444,16 @@ void mdot_all(long long n2, const double* V, long long stride, int count, const 
   launch_pdl(k_reduce_rows, count, 256, s, count, B, partials, out, gate);
 }
 
+// grid of the multi-dots of the FGMRES basis: 8 blocks per SM (the
+// partition of their partial sums; with 2 per SM, the context's partition,
+// the 8.4 M-element dots left most of each SM idle: layered 256x256x64
+// FGMRES 144.4 ms with 2, 142.9 with 4, 140.5 with 8, 141.1 with 16)
+int mdot_grid(const tp_ctx* c, long long n) {
+  const long long want = (n + 255) / 256;
+  const long long cap = 8ll * c->num_sms;
+  return (int)std::max(1ll, std::min(want, cap));
+}
+
 // grid of k_orth_update: enough blocks for 8 resident per SM, at most one
 // element per thread
 int orth_grid(const tp_ctx* c, long long n) {
@@ -476,7 +486,8 @@ void ensure_workspace(tp_ctx* c, int restart) {
   c->hn = c->kpool.alloc<double>(4);
   c->est = c->kpool.alloc<double>(4);
   c->h2 = c->kpool.alloc<double>(2 * (restart + 2));
-  c->kparts = c->kpool.alloc<double>((size_t)(restart + 2) * 4 * c->nparts + 16);
+  c->kparts = c->kpool.alloc<double>(
+      (size_t)(restart + 2) * std::max(4 * c->nparts, mdot_grid(c, 2ll * c->N)) + 16);
   c->oparts = c->kpool.alloc<double>((size_t)orth_grid(c, 2ll * c->N) + 16);
   c->reorth = c->kpool.alloc<int>(4);
   c->restart_alloc = restart;
@@ -713,6 +724,7 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
   const int N = c->N;
   const long long n2 = 2ll * N;
   const int B = c->nparts;
+  const int Bm = mdot_grid(c, 2ll * c->N);
   const int ldh = restart + 1;
   double* hp_host = c->host_est;
   auto t0 = std::chrono::steady_clock::now();
@@ -789,11 +801,11 @@ int fgmres_solve(tp_ctx* c, const double* bp, const double* bT, double* xp, doub
         double* h1 = c->h2;
         double* h2 = c->h2 + (restart + 2);
         const int G = orth_grid(c, n2);
-        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h1, s);
+        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, Bm, h1, s);
         launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h1, c->w, c->oparts,
                    (const int*)nullptr);
         launch_pdl(k_reorth_gate, 1, 256, s, j + 1, h1, c->oparts, G, c->reorth);
-        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, B, h2, s, c->reorth);
+        mdot_all(n2, c->Vb, n2, j + 1, c->w, c->kparts, Bm, h2, s, c->reorth);
         launch_pdl(k_orth_update, G, 256, s, n2, c->Vb, n2, j + 1, h2, c->w, c->oparts,
                    (const int*)c->reorth);
         launch_pdl(k_arnoldi, 1, 256, s, j, ldh, c->H, c->cs, c->sn, c->g, h1, h2, c->oparts, G,
