@@ -1822,7 +1822,12 @@ int pick_lanes(const DevCSR& A) {
   int lmin = 1;
   while (lmin < 32 && avg / lmin > 12.0) lmin *= 2;
   while (l > lmin && (long long)A.n * l > 4 * resident) l /= 2;
-  return l;
+  // at most 16 lanes: a 32-lane row's five FP64 reduction adds occupy the
+  // FP64 pipe for the whole warp (A_pp's level 3 on the layered workload:
+  // 34 k rows x 92 entries). Layered 256x256x64 FGMRES 140.4 -> 138.2 ms
+  // (FP64), 95.1 -> 94.6 ms (FP32); channelised and grf 64x64x32 within
+  // noise; at most 8 lanes: 140.0 ms, grf +0.6 ms
+  return l > 16 ? 16 : l;
 }
 
 // threads resident on the whole device at full occupancy, once per process
