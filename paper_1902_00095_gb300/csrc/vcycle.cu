@@ -134,16 +134,31 @@ __global__ void k_jacobi0(int n, const TV* __restrict__ dinv, const TB* __restri
   if (i < n) x[i] = d * (TV)b[i];
 }
 
-// two sweeps from a zero guess in one pass:
-// x = d b + d (b - A d b)  (x1 = d b is recomputed for every neighbour)
+// y = d b (rounded as in the sweeps): the first sweep from a zero guess,
+// read by the fused two-sweep kernels below instead of forming d_j b_j for
+// every matrix entry (two FP64 operations per entry on a pipe that bounds
+// these sweeps). first: the kernel opens a V-cycle (waits before any read).
+template <class TV, class TB>
+__global__ void k_scale_db(int n, const TV* __restrict__ dinv, const TB* __restrict__ b,
+                           TV* __restrict__ y, int first) {
+  if (first) pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const TV d = i < n ? dinv[i] : TV(0);
+  pdl_wait();
+  pdl_trigger();
+  if (i < n) y[i] = d * (TV)b[i];
+}
+
+// two sweeps from a zero guess in one pass, y = d b from k_scale_db:
+// x = d b + d (b - A y)
 template <int LANES, class TV, class TB>
 __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__ rp,
                                                   const int* __restrict__ col,
                                                   const TV* __restrict__ val,
                                                   const TV* __restrict__ dinv,
-                                                  const TB* __restrict__ b, TV* __restrict__ x,
-                                                  int first) {
-  if (first) pdl_wait();
+                                                  const TB* __restrict__ b,
+                                                  const TV* __restrict__ y,
+                                                  TV* __restrict__ x) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
@@ -152,9 +167,6 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
   TV d = TV(0);
   if (valid && lane == 0) d = dinv[row];
   constexpr int K = RowPre<LANES, TV>::K;
-  TV dj[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) dj[k] = (a.e + k * LANES < a.e1) ? dinv[a.c[k]] : TV(0);
   pdl_wait();
   pdl_trigger();
   TV bi = TV(0);
@@ -162,11 +174,8 @@ __global__ void __launch_bounds__(256) k_jacobi2z(int n, const int* __restrict__
   TV acc = TV(0);
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (a.e + k * LANES < a.e1) acc += a.v[k] * (dj[k] * (TV)b[a.c[k]]);
-  for (int q = a.e + K * LANES; q < a.e1; q += LANES) {
-    const int j = col[q];
-    acc += val[q] * (dinv[j] * (TV)b[j]);
-  }
+    if (a.e + k * LANES < a.e1) acc += a.v[k] * y[a.c[k]];
+  for (int q = a.e + K * LANES; q < a.e1; q += LANES) acc += val[q] * y[col[q]];
   acc = group_sum<LANES>(acc);
   if (valid && lane == 0) x[row] = d * bi + d * (bi - acc);
 }
@@ -252,23 +261,19 @@ __global__ void __launch_bounds__(256) k_residual_ell(int n, int w, const int* _
 }
 
 template <class TV, class TB>
-__global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* __restrict__ ecol, int snx, int snxy,
+__global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* __restrict__ ecol,
+                                                      int snx, int snxy,
                                                       const TV* __restrict__ eval,
                                                       const TV* __restrict__ dinv,
                                                       const TB* __restrict__ b,
-                                                      TV* __restrict__ x, int first) {
-  if (first) pdl_wait();
+                                                      const TV* __restrict__ y,
+                                                      TV* __restrict__ x) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   EllRow<TV> a;
-  TV d = TV(0), dj[kEllMaxW];
-#pragma unroll
-  for (int k = 0; k < kEllMaxW; ++k) dj[k] = TV(0);
+  TV d = TV(0);
   if (row < n) {
     a.load(n, w, ecol, eval, row, snx, snxy);
     d = dinv[row];
-#pragma unroll
-    for (int k = 0; k < kEllMaxW; ++k)
-      if (k < w) dj[k] = dinv[a.c[k]];
   }
   pdl_wait();
   pdl_trigger();
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(256) k_jacobi2z_ell(int n, int w, const int* _
   TV acc = TV(0);
 #pragma unroll
   for (int k = 0; k < kEllMaxW; ++k)
-    if (k < w) acc += a.v[k] * (dj[k] * (TV)b[a.c[k]]);
+    if (k < w) acc += a.v[k] * y[a.c[k]];
   x[row] = d * bi + d * (bi - acc);
 }
 
@@ -537,7 +542,7 @@ __global__ void __launch_bounds__(256) k_sell_residual(int nslots, const int* __
   r[a.row] = bi - a.dot(col, val, x);
 }
 
-// two sweeps from a zero guess: x = d b + d (b - A d b)
+// two sweeps from a zero guess, y = d b from k_scale_db: x = d b + d (b - A y)
 template <class TV, class TB>
 __global__ void __launch_bounds__(256) k_sell_jacobi2z(int nslots, const int* __restrict__ ptr,
                                                        const int* __restrict__ perm,
@@ -545,8 +550,8 @@ __global__ void __launch_bounds__(256) k_sell_jacobi2z(int nslots, const int* __
                                                        const TV* __restrict__ val,
                                                        const TV* __restrict__ dinv,
                                                        const TB* __restrict__ b,
-                                                       TV* __restrict__ x, int first) {
-  if (first) pdl_wait();
+                                                       const TV* __restrict__ y,
+                                                       TV* __restrict__ x) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   SellRow<TV> a;
   a.load(nslots, ptr, perm, col, val, t);
@@ -559,11 +564,8 @@ __global__ void __launch_bounds__(256) k_sell_jacobi2z(int nslots, const int* __
   constexpr int K = SellRow<TV>::K;
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (k < a.w) acc += a.v[k] * (dinv[a.c[k]] * (TV)b[a.c[k]]);
-  for (int k = K; k < a.w; ++k) {
-    const int j = col[a.q0 + 32 * k];
-    acc += val[a.q0 + 32 * k] * (dinv[j] * (TV)b[j]);
-  }
+    if (k < a.w) acc += a.v[k] * y[a.c[k]];
+  for (int k = K; k < a.w; ++k) acc += val[a.q0 + 32 * k] * y[col[a.q0 + 32 * k]];
   x[a.row] = d * bi + d * (bi - acc);
 }
 
@@ -584,14 +586,14 @@ void jacobi(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB*
 }
 
 template <class TV, class TB>
-void jacobi2z(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b, TV* x,
-              int first, cudaStream_t s) {
+void jacobi2z(int lanes, const DevCSR& A, const TV* val, const TV* dinv, const TB* b,
+              const TV* y, TV* x, cudaStream_t s) {
   const int g = grid_for((long long)A.n * lanes);
   switch (lanes) {
 #define TP_CASE(L)                                                                         \
   case L:                                                                                  \
-    launch_pdl(k_jacobi2z<L, TV, TB>, g, kBlock, s, A.n, A.rowptr, A.col, val, dinv, b, x, \
-               first);                                                                     \
+    launch_pdl(k_jacobi2z<L, TV, TB>, g, kBlock, s, A.n, A.rowptr, A.col, val, dinv, b, y, \
+               x);                                                                         \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -708,19 +710,21 @@ void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_
   }
 }
 
-// first: the kernel opens a V-cycle (waits before reading the level operator)
+// y: work vector of the level (holds d b); first: the sweeps open a V-cycle
+// (the first kernel waits before any read)
 template <class TV, class TB>
-void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* x, int first,
-                                cudaStream_t s) {
+void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* y, TV* x,
+                                int first, cudaStream_t s) {
+  launch_pdl(k_scale_db<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, dinv, b, y, first);
   if (v.sell_slices > 0) {
     const int nslots = v.sell_slices * 32;
     launch_pdl(k_sell_jacobi2z<TV, TB>, grid_for(nslots), kBlock, s, nslots, v.sell_ptr,
-               v.sell_perm, v.sell_col, Vals<TV>::S(v), dinv, b, x, first);
+               v.sell_perm, v.sell_col, Vals<TV>::S(v), dinv, b, (const TV*)y, x);
   } else if (v.ell_w > 0) {
     launch_pdl(k_jacobi2z_ell<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, v.ell_w, v.ell_col,
-               v.ell_nx, v.ell_nxy, Vals<TV>::E(v), dinv, b, x, first);
+               v.ell_nx, v.ell_nxy, Vals<TV>::E(v), dinv, b, (const TV*)y, x);
   } else {
-    jacobi2z<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, x, first, s);
+    jacobi2z<TV, TB>(v.lanes_A, v.A, Vals<TV>::A(v), dinv, b, y, x, s);
   }
 }
 
@@ -862,7 +866,7 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     smooth_step<TV, TB, TV>(sm, nullptr, v, dinv, b, (const TV*)nullptr, x, s);
   } else if (nu_pre >= 2) {
     // the first two l1-Jacobi sweeps from a zero guess fused
-    level_two_sweeps_from_zero<TV, TB>(v, dinv, b, x, l == 0 ? 1 : 0, s);
+    level_two_sweeps_from_zero<TV, TB>(v, dinv, b, t, x, l == 0 ? 1 : 0, s);
     done = 2;
   } else {
     launch_pdl(k_jacobi0<TV, TB>, grid_for(n), kBlock, s, n, dinv, b, x, l == 0 ? 1 : 0);
