@@ -975,8 +975,69 @@ __global__ void k_spgemm_ub(int n, const int* __restrict__ Arp, const int* __res
 // Row i of C: products a_ik * b_kj in ascending k (row i of A) then ascending
 // j (row k of B); each column's sum starts at 0.0 and adds them in that
 // order. Columns kept sorted by insertion. This thread-per-row form takes
-// the rows with at most kSpShort products; k_spgemm_rows_warp the others.
+// the rows with at most kSpShort products and more than kSpMerge entries of
+// A (k_spgemm_rows_merge the rows with fewer, k_spgemm_rows_warp the rows
+// with more products).
 constexpr int kSpShort = 96;
+constexpr int kSpMerge = 8;  // rows of A with at most this many entries: k-way merge
+
+// The rows of k_spgemm_rows whose row of A has at most kSpMerge entries (a
+// 7-point operator times P): a merge of the (sorted) rows of B of the row's
+// entries, heads in registers. Each column comes out once, in order, its
+// products added in ascending entry order from 0.0 (the canonical order),
+// with no sorted-list insertion in memory. A kernel of its own: its
+// registers would cost the insertion form occupancy.
+__global__ void k_spgemm_rows_merge(int n, const int* __restrict__ Arp,
+                                    const int* __restrict__ Acol, const double* __restrict__ Aval,
+                                    const int* __restrict__ Brp, const int* __restrict__ Bcol,
+                                    const double* __restrict__ Bval, const int* __restrict__ off,
+                                    const int* __restrict__ ub, int* __restrict__ ccol,
+                                    double* __restrict__ cval, int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || ub[i] > kSpShort) return;
+  const int a0 = Arp[i], na = Arp[i + 1] - a0;
+  if (na > kSpMerge) return;
+  int* cc = ccol + off[i];
+  double* cv = cval + off[i];
+  // a merge of the (sorted) rows of B of the row's entries, heads in
+  // registers: each column comes out once, in order, its products added
+  // in ascending entry order from 0.0 (the canonical order), with no
+  // sorted-list insertion in memory (rows of a 7-point operator times P)
+  int f[kSpMerge], fe[kSpMerge], hc[kSpMerge];
+  double av[kSpMerge];
+#pragma unroll
+  for (int k = 0; k < kSpMerge; ++k) {
+    f[k] = fe[k] = 0;
+    hc[k] = 0x7fffffff;
+    av[k] = 0.0;
+    if (k < na) {
+      const int kk = Acol[a0 + k];
+      av[k] = Aval[a0 + k];
+      f[k] = Brp[kk];
+      fe[k] = Brp[kk + 1];
+      if (f[k] < fe[k]) hc[k] = Bcol[f[k]];
+    }
+  }
+  int u = 0;
+  while (true) {
+    int m = 0x7fffffff;
+#pragma unroll
+    for (int k = 0; k < kSpMerge; ++k) m = min(m, hc[k]);
+    if (m == 0x7fffffff) break;
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < kSpMerge; ++k)
+      if (hc[k] == m) {
+        sum = __dadd_rn(sum, __dmul_rn(av[k], Bval[f[k]]));
+        ++f[k];
+        hc[k] = f[k] < fe[k] ? Bcol[f[k]] : 0x7fffffff;
+      }
+    cc[u] = m;
+    cv[u] = sum;
+    ++u;
+  }
+  cnt[i] = u;
+}
 
 __global__ void k_spgemm_rows(int n, const int* __restrict__ Arp, const int* __restrict__ Acol,
                               const double* __restrict__ Aval, const int* __restrict__ Brp,
@@ -988,6 +1049,7 @@ __global__ void k_spgemm_rows(int n, const int* __restrict__ Arp, const int* __r
   if (i >= n || ub[i] > kSpShort) return;
   int* cc = ccol + off[i];
   double* cv = cval + off[i];
+  if (Arp[i + 1] - Arp[i] <= kSpMerge) return;  // k_spgemm_rows_merge
   int u = 0;
   for (int e = Arp[i]; e < Arp[i + 1]; ++e) {
     const int k = Acol[e];
@@ -1891,6 +1953,9 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
         n, B.m, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, ccol, cval, cnt);
     TP_LAUNCH_CHECK();
   } else {
+  k_spgemm_rows_merge<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr,
+                                                       B.col, B.val, off, ub, ccol, cval, cnt);
+  TP_LAUNCH_CHECK();
   k_spgemm_rows<<<grid_for(n, 128), 128, 0, s>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col,
                                                  B.val, off, ub, ccol, cval, cnt);
   TP_LAUNCH_CHECK();
