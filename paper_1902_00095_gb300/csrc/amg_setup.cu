@@ -1608,6 +1608,30 @@ __global__ void k_to_bf16(long long n, const double* __restrict__ a,
 // elimination without pivoting on a tridiagonal matrix): m_0 = d_0,
 // m_k = d_k - l_k (u_{k-1} / m_{k-1}); stores l_k, 1 / m_k and u_k / m_k.
 // Correctly rounded operations in the oracle's order (no FMA contraction).
+// Twisted factorisation of each column's tridiagonal part (diagonal d_k,
+// lower l_k, upper u_k; layer k of column c is cell c + nxy k), so that two
+// threads can solve a column from both ends at once (k_line_sweep). With
+// mid = nz / 2: the top rows k < mid are eliminated downwards (m_k = d_k -
+// l_k cp_{k-1}, cp_k = u_k / m_k), the bottom rows k > mid upwards (q_k =
+// d_k - u_k cq_{k+1}, cq_k = l_k / q_k), and the middle row takes both sides
+// (pivot d - l cp_{mid-1} - u cq_{mid+1}). Stored per cell: lo = the
+// coupling to the row eliminated before it (l_k on top, u_k below, l_mid in
+// the middle), minv = 1 / pivot, cp = cp_k on top, cq_k below, u_mid in the
+// middle.
+__device__ __forceinline__ void line_row(int i, int nxy, const int* __restrict__ rp,
+                                         const int* __restrict__ col,
+                                         const double* __restrict__ val, double& d, double& l,
+                                         double& u, bool& has_lo, bool& has_up) {
+  d = l = u = 0.0;
+  has_lo = has_up = false;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int j = col[e];
+    if (j == i) d = val[e];
+    else if (j == i - nxy) { l = val[e]; has_lo = true; }
+    else if (j == i + nxy) { u = val[e]; has_up = true; }
+  }
+}
+
 __global__ void k_line_factor(int nxy, int nz, const int* __restrict__ rp,
                               const int* __restrict__ col, const double* __restrict__ val,
                               double* __restrict__ lo, double* __restrict__ minv,
@@ -1616,36 +1640,59 @@ __global__ void k_line_factor(int nxy, int nz, const int* __restrict__ rp,
                               int* __restrict__ err) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nxy) return;
-  double cprev = 0.0;
-  for (int k = 0; k < nz; ++k) {
-    const int i = c + k * nxy;
-    double d = 0.0, l = 0.0, u = 0.0;
-    bool has_lo = false, has_up = false;
-    for (int e = rp[i]; e < rp[i + 1]; ++e) {
-      const int j = col[e];
-      if (j == i) d = val[e];
-      else if (j == i - nxy) { l = val[e]; has_lo = true; }
-      else if (j == i + nxy) { u = val[e]; has_up = true; }
+  const int mid = nz >> 1;
+  auto store = [&](int i, double a, double mi, double q) {
+    lo[i] = a;
+    minv[i] = mi;
+    cp[i] = q;
+    if (lof) {
+      lof[i] = (float)a;
+      minvf[i] = (float)mi;
+      cpf[i] = (float)q;
     }
+  };
+  auto pivot_ok = [&](double m) {
+    const bool ok = m != 0.0 && isfinite(m);
+    if (!ok) atomicOr(err, 16);
+    return ok;
+  };
+  double d, l, u;
+  bool has_lo, has_up;
+  double cprev = 0.0;  // top: cp_{k-1}
+  for (int k = 0; k < mid; ++k) {
+    const int i = c + k * nxy;
+    line_row(i, nxy, rp, col, val, d, l, u, has_lo, has_up);
     if (has_lo != (k > 0) || has_up != (k < nz - 1)) atomicOr(err, 16);
     const double m = __dsub_rn(d, __dmul_rn(l, cprev));
-    double mi = 0.0, cpk = 0.0;
-    if (m == 0.0 || !isfinite(m)) {
-      atomicOr(err, 16);
-    } else {
+    double mi = 0.0, q = 0.0;
+    if (pivot_ok(m)) {
       mi = __ddiv_rn(1.0, m);
-      cpk = __ddiv_rn(u, m);
+      q = __ddiv_rn(u, m);
     }
-    lo[i] = l;
-    minv[i] = mi;
-    cp[i] = cpk;
-    if (lof) {
-      lof[i] = (float)l;
-      minvf[i] = (float)mi;
-      cpf[i] = (float)cpk;
-    }
-    cprev = cpk;
+    store(i, l, mi, q);
+    cprev = q;
   }
+  double cnext = 0.0;  // bottom: cq_{k+1}
+  for (int k = nz - 1; k > mid; --k) {
+    const int i = c + k * nxy;
+    line_row(i, nxy, rp, col, val, d, l, u, has_lo, has_up);
+    if (has_lo != (k > 0) || has_up != (k < nz - 1)) atomicOr(err, 16);
+    const double m = __dsub_rn(d, __dmul_rn(u, cnext));
+    double mi = 0.0, q = 0.0;
+    if (pivot_ok(m)) {
+      mi = __ddiv_rn(1.0, m);
+      q = __ddiv_rn(l, m);
+    }
+    store(i, u, mi, q);
+    cnext = q;
+  }
+  const int i = c + mid * nxy;
+  line_row(i, nxy, rp, col, val, d, l, u, has_lo, has_up);
+  if (has_lo != (mid > 0) || has_up != (mid < nz - 1)) atomicOr(err, 16);
+  const double m = __dsub_rn(__dsub_rn(d, __dmul_rn(l, cprev)), __dmul_rn(u, cnext));
+  double mi = 0.0;
+  if (pivot_ok(m)) mi = __ddiv_rn(1.0, m);
+  store(i, l, mi, u);
 }
 
 void line_setup(Level& v, int nxy, int nz, Pool& pool, bool f32, int* err, bool allocate,

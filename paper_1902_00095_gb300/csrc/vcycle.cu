@@ -369,12 +369,16 @@ __global__ void k_coarse(int n, const double* __restrict__ inv, const TB* __rest
 }
 
 // Vertical-line step x_out = x_in + T^-1 (b - A x_in) (x_in null: x_out =
-// T^-1 b), one thread per column c of the nxy x nz grid (cell c + nxy k):
-// forward elimination g_k = (r_k - l_k g_{k-1}) / m_k with the residual row
-// r_k formed on the way up (ELL slots when the level has them, else the CSR
-// row), g_k parked in x_out, then back substitution e_k = g_k - (u_k / m_k)
-// e_{k+1} from the top down. Consecutive threads own consecutive columns,
-// so every plane is read and written coalesced.
+// T^-1 b) with the twisted factorisation of k_line_factor: two threads per
+// column c of the nxy x nz grid (cell c + nxy k), adjacent lanes. With mid =
+// nz / 2 the even lane eliminates the top rows downwards and the odd lane
+// the bottom rows upwards, in the same instructions (the stored coefficients
+// make the two recurrences one: g = (r - lo g_prev) minv), each forming its
+// residual rows on the way (ELL slots when the level has them, else the CSR
+// row) and parking g in x_out. The even lane then solves the middle row with
+// the odd lane's last g (a shuffle), and both substitute back towards their
+// ends, e = g - cp e_prev. Half the serial chain of a one-thread Thomas
+// solve, twice the threads.
 template <class TV, class TB, class TO>
 __global__ void __launch_bounds__(128) k_line_sweep(
     int nxy, int nz, int n, int ell_w, const int* __restrict__ ecol, int snx, int snxy,
@@ -384,12 +388,12 @@ __global__ void __launch_bounds__(128) k_line_sweep(
     const TB* __restrict__ b, const TV* __restrict__ xin, TO* __restrict__ xout) {
   pdl_wait();
   pdl_trigger();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nxy) return;
-  TV gprev = TV(0);
-#pragma unroll 2
-  for (int k = 0; k < nz; ++k) {
-    const int i = c + k * nxy;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = t >> 1, role = t & 1;  // role 0: top rows, 1: bottom rows
+  const bool act = c < nxy;
+  const int mid = nz >> 1;
+  const int nsteps = role ? nz - 1 - mid : mid;
+  auto rrow = [&](int i) -> TV {
     TV r = (TV)b[i];
     if (xin) {
       TV ax = TV(0);
@@ -405,17 +409,37 @@ __global__ void __launch_bounds__(128) k_line_sweep(
       }
       r -= ax;
     }
-    const TV g = (r - lo[i] * gprev) * minv[i];
-    xout[i] = (TO)g;
-    gprev = g;
-  }
-  TV enext = TV(0);
+    return r;
+  };
+  TV gprev = TV(0);
 #pragma unroll 2
-  for (int k = nz - 1; k >= 0; --k) {
-    const int i = c + k * nxy;
-    const TV e = (TV)xout[i] - cp[i] * enext;
-    xout[i] = (TO)(xin ? xin[i] + e : e);
-    enext = e;
+  for (int s = 0; s < mid; ++s) {
+    if (act && s < nsteps) {
+      const int i = c + (role ? nz - 1 - s : s) * nxy;
+      const TV g = (rrow(i) - lo[i] * gprev) * minv[i];
+      xout[i] = (TO)g;
+      gprev = g;
+    }
+  }
+  // middle row: the top lane takes the bottom lane's last g
+  const TV gb = __shfl_down_sync(0xffffffffu, gprev, 1);
+  TV xm = TV(0);
+  if (act && role == 0) {
+    const int i = c + mid * nxy;
+    const TV gt = mid > 0 ? gprev : TV(0);
+    const TV gu = mid + 1 < nz ? gb : TV(0);
+    xm = (rrow(i) - lo[i] * gt - cp[i] * gu) * minv[i];
+    xout[i] = (TO)(xin ? xin[i] + xm : xm);
+  }
+  TV enext = __shfl_sync(0xffffffffu, xm, (threadIdx.x & 31) & ~1);
+#pragma unroll 2
+  for (int s = 0; s < mid; ++s) {
+    if (act && s < nsteps) {
+      const int i = c + (role ? mid + 1 + s : mid - 1 - s) * nxy;
+      const TV e = (TV)xout[i] - cp[i] * enext;
+      xout[i] = (TO)(xin ? xin[i] + e : e);
+      enext = e;
+    }
   }
 }
 
@@ -775,10 +799,11 @@ double line_bytes(const Level& v, bool from_zero) {
 template <class TV, class TB, class TO>
 void line_step(const Smooth& sm, const Level& v, const TB* b, const TV* xin, TO* xout,
                cudaStream_t s) {
-  // one thread per column; small blocks spread a few thousand columns over
+  // two threads per column; small blocks spread a few thousand columns over
   // every SM
-  const int threads = sm.line_nxy >= 152 * 128 * 2 ? 128 : 32;
-  const int grid = (sm.line_nxy + threads - 1) / threads;
+  const long long lanes = 2ll * sm.line_nxy;
+  const int threads = lanes >= 152 * 128 * 2 ? 128 : 32;
+  const int grid = (int)((lanes + threads - 1) / threads);
   launch_pdl(k_line_sweep<TV, TB, TO>, grid, threads, s, sm.line_nxy, sm.line_nz, v.A.n,
              v.ell_w, v.ell_col, v.ell_nx, v.ell_nxy, Vals<TV>::E(v), v.A.rowptr, v.A.col,
              Vals<TV>::A(v),
