@@ -1556,16 +1556,21 @@ __global__ void k_spgemm_numeric(int n, const int* __restrict__ Arp, const int* 
   }
 }
 
+// rows of C from their slots at off[i] to the compact CSR: L lanes per row
+// (about two entries per lane on average), so that a warp's copies are a
+// few contiguous runs rather than 32 scattered rows
+template <int L>
 __global__ void k_spgemm_compact(int n, const int* __restrict__ off,
                                  const int* __restrict__ ccol, const double* __restrict__ cval,
                                  const int* __restrict__ Crp, int* __restrict__ Ccol,
                                  double* __restrict__ Cval) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(t / L), lane = (int)(t % L);
   if (i >= n) return;
-  const int o = off[i];
-  for (int e = Crp[i]; e < Crp[i + 1]; ++e) {
-    Ccol[e] = ccol[o + (e - Crp[i])];
-    Cval[e] = cval[o + (e - Crp[i])];
+  const int o = off[i], c0 = Crp[i], len = Crp[i + 1] - c0;
+  for (int e = lane; e < len; e += L) {
+    Ccol[c0 + e] = ccol[o + e];
+    Cval[c0 + e] = cval[o + e];
   }
 }
 
@@ -2048,7 +2053,20 @@ DevCSR spgemm(const DevCSR& A, const DevCSR& B, Pool& pool, Pool& scratch, cudaS
   C.nnz = (int)nnz;
   C.col = pool.alloc<int>(nnz + 1);
   C.val = pool.alloc<double>(nnz + 1);
-  k_spgemm_compact<<<grid_for(n), kBlock, 0, s>>>(n, off, ccol, cval, C.rowptr, C.col, C.val);
+  {
+    const double avg = n > 0 ? (double)nnz / n : 1.0;
+    int L = 1;
+    while (L < 32 && 2.0 * L < avg) L *= 2;
+    const int g = grid_for((long long)n * L);
+    switch (L) {
+#define TP_CASE(LL)                                                                          \
+  case LL:                                                                                   \
+    k_spgemm_compact<LL><<<g, kBlock, 0, s>>>(n, off, ccol, cval, C.rowptr, C.col, C.val); \
+    break;
+      TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
+#undef TP_CASE
+    }
+  }
   TP_LAUNCH_CHECK();
   return C;
 }
