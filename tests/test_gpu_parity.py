@@ -528,7 +528,7 @@ def test_errors_are_status_codes_not_faults():
 @pytest.mark.parametrize("cfg", ["grf64", "channel128"])
 def test_full_size_recipes_reach_the_tolerance(cfg):
     """At the full sizes the oracle's own assembly (vectorised, seconds) is
-    the checker: the GPU solution must give relative residual <= 1e-8 on
+    the reference: the GPU solution must give relative residual <= 1e-8 on
     the oracle's matrix, and sampled rows of the GPU matrix must match the
     oracle's rows."""
     prob = make_problem(cfg)
