@@ -415,7 +415,7 @@ class Solver:
 
     def level_storage(self, which, level):
         """(format, stored entries) of a level's operator: format 0 CSR,
-        1 ELL, 2 sliced ELL."""
+        1 ELL, 2 sliced ELL, 3 ELL by grid direction (no column indices)."""
         f, e = C.c_int(), C.c_longlong()
         _check(self._lib.tp_level_storage(self._h, which, level, C.byref(f), C.byref(e)),
                "tp_level_storage")
@@ -558,7 +558,7 @@ class AMG:
 
     def level_storage(self, level):
         """(format, stored entries) of a level's operator: format 0 CSR,
-        1 ELL, 2 sliced ELL."""
+        1 ELL, 2 sliced ELL, 3 ELL by grid direction (no column indices)."""
         f, e = C.c_int(), C.c_longlong()
         _check(self._lib.tp_amg_level_storage(self._h, level, C.byref(f), C.byref(e)),
                "tp_amg_level_storage")
