@@ -308,19 +308,28 @@ __global__ void __launch_bounds__(256) k_residual(int n, const int* __restrict__
 
 // y = R x (restriction; R values of type TP)
 template <int LANES, class TP, class TV>
+// y = A x (the restriction); with dsc, also ysc = dsc y, rounded as in the
+// coarse level's first sweep from zero (d b: its k_jacobi0 result or the y of
+// its fused two sweeps), which then needs no kernel of its own
 __global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
                                               const int* __restrict__ col,
                                               const TP* __restrict__ val,
-                                              const TV* __restrict__ x, TV* __restrict__ y) {
+                                              const TV* __restrict__ x, TV* __restrict__ y,
+                                              const TV* __restrict__ dsc,
+                                              TV* __restrict__ ysc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = t / LANES, lane = t % LANES;
   const bool valid = row < n;
   RowPre<LANES, TP> a;
   a.load(rp, col, val, row, valid, lane);
+  const TV d = (dsc && valid && lane == 0) ? dsc[row] : TV(0);
   pdl_wait();
   pdl_trigger();
   TV ax = a.template dot<TV, TV>(col, val, x);
-  if (valid && lane == 0) y[row] = ax;
+  if (valid && lane == 0) {
+    y[row] = ax;
+    if (dsc) ysc[row] = d * ax;
+  }
 }
 
 // x += P e (prolongation; P values of type TP)
@@ -639,12 +648,13 @@ void residual(int lanes, const DevCSR& A, const TV* val, const TB* b, const TV* 
 }
 
 template <class TP, class TV>
-void spmv(int lanes, const DevCSR& A, const TP* val, const TV* x, TV* y, cudaStream_t s) {
+void spmv(int lanes, const DevCSR& A, const TP* val, const TV* x, TV* y, cudaStream_t s,
+          const TV* dsc = nullptr, TV* ysc = nullptr) {
   const int g = grid_for((long long)A.n * lanes);
   switch (lanes) {
-#define TP_CASE(L)                                                                  \
-  case L:                                                                           \
-    launch_pdl(k_spmv<L, TP, TV>, g, kBlock, s, A.n, A.rowptr, A.col, val, x, y);   \
+#define TP_CASE(L)                                                                           \
+  case L:                                                                                    \
+    launch_pdl(k_spmv<L, TP, TV>, g, kBlock, s, A.n, A.rowptr, A.col, val, x, y, dsc, ysc);  \
     break;
     TP_CASE(1) TP_CASE(2) TP_CASE(4) TP_CASE(8) TP_CASE(16) TP_CASE(32)
 #undef TP_CASE
@@ -738,8 +748,9 @@ void level_residual(const Level& v, const TB* b, const TV* x, TV* r, cudaStream_
 // (the first kernel waits before any read)
 template <class TV, class TB>
 void level_two_sweeps_from_zero(const Level& v, const TV* dinv, const TB* b, TV* y, TV* x,
-                                int first, cudaStream_t s) {
-  launch_pdl(k_scale_db<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, dinv, b, y, first);
+                                int first, cudaStream_t s, bool y_ready = false) {
+  if (!y_ready)
+    launch_pdl(k_scale_db<TV, TB>, grid_for(v.A.n), kBlock, s, v.A.n, dinv, b, y, first);
   if (v.sell_slices > 0) {
     const int nslots = v.sell_slices * 32;
     launch_pdl(k_sell_jacobi2z<TV, TB>, grid_for(nslots), kBlock, s, nslots, v.sell_ptr,
@@ -821,10 +832,27 @@ void smooth_step(const Smooth& sm, Probe* pr, const Level& v, const TV* dinv, co
   }
 }
 
+// bc = R r for level l + 1. When that level smooths with l1-Jacobi by the
+// per-kernel path (not the coarsest, not the cluster tail) the restriction
+// also writes its first sweep from zero, d b: into t for the fused two
+// sweeps, into x for a single one. Returns whether it did.
+template <class TV>
+bool restrict_to(std::vector<Level>& L, size_t l, const Smooth& sm, int nu_pre, const TV* r,
+                 TV* bc, cudaStream_t s) {
+  Level& v = L[l];
+  Level& c = L[l + 1];
+  const bool fuse = sm.kind == 0 && l + 2 < L.size() && (int)(l + 1) != sm.tail_first;
+  const TV* dsc = fuse ? Vals<TV>::dinv(c) : nullptr;
+  TV* ysc = fuse ? static_cast<TV*>(nu_pre >= 2 ? c.t : c.x) : nullptr;
+  if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s, dsc, ysc);
+  else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s, dsc, ysc);
+  return fuse;
+}
+
 template <class TV, class TB, class TO>
 TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, TO* final_out,
               int nu_pre, int nu_post, const Smooth& sm, cudaStream_t s,
-              Probe* probe = nullptr) {
+              Probe* probe = nullptr, bool pre_done = false) {
   Level& v = L[l];
   const int n = v.A.n;
   TV* x = static_cast<TV*>(v.x);
@@ -863,10 +891,9 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     level_residual<TV, TB>(v, b, cur, r, s);
     Level& c = L[l + 1];
     TV* bc = static_cast<TV*>(c.b);
-    if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s);
-    else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
+    const bool fuse = restrict_to<TV>(L, l, sm, nu_pre, r, bc, s);
     TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s,
-                                   probe);
+                                   probe, fuse);
     if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
     else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
     double span_bytes = 0.0;
@@ -890,10 +917,11 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
     // pre-smoothing from a zero guess
     smooth_step<TV, TB, TV>(sm, nullptr, v, dinv, b, (const TV*)nullptr, x, s);
   } else if (nu_pre >= 2) {
-    // the first two l1-Jacobi sweeps from a zero guess fused
-    level_two_sweeps_from_zero<TV, TB>(v, dinv, b, t, x, l == 0 ? 1 : 0, s);
+    // the first two l1-Jacobi sweeps from a zero guess fused (y = d b in t,
+    // written by the restriction when pre_done)
+    level_two_sweeps_from_zero<TV, TB>(v, dinv, b, t, x, l == 0 ? 1 : 0, s, pre_done);
     done = 2;
-  } else {
+  } else if (!pre_done) {
     launch_pdl(k_jacobi0<TV, TB>, grid_for(n), kBlock, s, n, dinv, b, x, l == 0 ? 1 : 0);
   }
   for (int k = done; k < nu_pre; ++k) {
@@ -905,10 +933,9 @@ TV* run_level(std::vector<Level>& L, const double* cinv, size_t l, const TB* b, 
   level_residual<TV, TB>(v, b, cur, r, s);
   Level& c = L[l + 1];
   TV* bc = static_cast<TV*>(c.b);
-  if (v.Rh) spmv<__nv_bfloat16, TV>(v.lanes_R, v.R, v.Rh, r, bc, s);
-  else spmv<TV, TV>(v.lanes_R, v.R, Vals<TV>::R(v), r, bc, s);
+  const bool fuse = restrict_to<TV>(L, l, sm, nu_pre, r, bc, s);
   TV* ec = run_level<TV, TV, TV>(L, cinv, l + 1, bc, (TV*)nullptr, nu_pre, nu_post, sm, s,
-                                 probe);
+                                 probe, fuse);
   if (v.Ph) prolong<__nv_bfloat16, TV>(v.lanes_P, v.P, v.Ph, ec, cur, s);
   else prolong<TV, TV>(v.lanes_P, v.P, Vals<TV>::P(v), ec, cur, s);
   // post-smoothing; on the probed level one event pair spans all sweeps
