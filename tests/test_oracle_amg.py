@@ -453,3 +453,58 @@ def test_line_smoothed_vcycle_solves_vertical_transport_fast():
         res[line is not None] = np.linalg.norm(b - amg.spmv(A, x)) / np.linalg.norm(b)
     assert res[True] <= 0.05 ** 4
     assert res[False] >= 0.1 ** 4
+
+
+def _twisted_solve(l, d, u, r):
+    """The twisted elimination of the GPU's vertical-line step, restated:
+    with mid = n // 2 the top rows are eliminated downwards (m_k = d_k -
+    l_k cp_{k-1}, cp_k = u_k / m_k, g_k = (r_k - l_k g_{k-1}) / m_k), the
+    bottom rows upwards (q_k = d_k - u_k cq_{k+1}, cq_k = l_k / q_k, h_k =
+    (r_k - u_k h_{k+1}) / q_k), the middle row takes both sides, and each
+    half substitutes back towards its end."""
+    n = d.size
+    mid = n // 2
+    x = np.zeros(n)
+    cp = np.zeros(n)
+    g = np.zeros(n)
+    for k in range(mid):
+        m = d[k] - (l[k] * cp[k - 1] if k > 0 else 0.0)
+        cp[k] = u[k] / m
+        g[k] = (r[k] - (l[k] * g[k - 1] if k > 0 else 0.0)) / m
+    for k in range(n - 1, mid, -1):
+        q = d[k] - (u[k] * cp[k + 1] if k < n - 1 else 0.0)
+        cp[k] = l[k] / q
+        g[k] = (r[k] - (u[k] * g[k + 1] if k < n - 1 else 0.0)) / q
+    ct = cp[mid - 1] if mid > 0 else 0.0
+    gt = g[mid - 1] if mid > 0 else 0.0
+    cb = cp[mid + 1] if mid + 1 < n else 0.0
+    gb = g[mid + 1] if mid + 1 < n else 0.0
+    x[mid] = (r[mid] - l[mid] * gt - u[mid] * gb) / (d[mid] - l[mid] * ct - u[mid] * cb)
+    for k in range(mid - 1, -1, -1):
+        x[k] = g[k] - cp[k] * x[k + 1]
+    for k in range(mid + 1, n):
+        x[k] = g[k] - cp[k] * x[k - 1]
+    return x
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 7, 64, 65])
+def test_twisted_elimination_matches_the_banded_solver(n):
+    """The two-ended elimination of the GPU line step solves the same
+    tridiagonal system as the oracle's Thomas algorithm (LAPACK's banded
+    solver as the reference), on non-symmetric, diagonally dominant columns
+    of odd and even height, down to two cells."""
+    import scipy.linalg
+    rng = np.random.default_rng(n)
+    l = rng.uniform(-1.0, 0.2, n)
+    u = rng.uniform(-3.0, 0.1, n)  # strong one-sided (downward-transport-like) coupling
+    l[0] = 0.0
+    u[-1] = 0.0
+    d = np.abs(l) + np.abs(u) + rng.uniform(0.5, 1.5, n)
+    r = rng.standard_normal(n)
+    ab = np.zeros((3, n))
+    ab[0, 1:] = u[:-1]
+    ab[1] = d
+    ab[2, :-1] = l[1:]
+    ref = scipy.linalg.solve_banded((1, 1), ab, r)
+    x = _twisted_solve(l, d, u, r)
+    assert np.max(np.abs(x - ref)) <= 1e-13 * np.max(np.abs(ref))
